@@ -1,0 +1,171 @@
+/*
+ * pa.h - C ABI of the GB300 privacy-amplification hash library (libpa_gb300.so).
+ *
+ * The library computes the modular-arithmetic universal_2 hash of
+ * arXiv 1910.04429 (Sec. 2.3, Definition 5, Eq. 6 and Eq. 7):
+ *
+ *     g_{c,d}(x) = floor( ((c * x + d) mod 2^n) / 2^(n - m) )
+ *
+ * which compresses an n-bit reconciled key x to an m-bit final key using the
+ * public seed (c, d) (Sec. 2.2: Alice and Bob publicly pick one g from the
+ * family and apply it to their identical strings). Here c is called seed_a
+ * and d seed_b. The product is exact: an NTT over the Goldilocks prime
+ * 2^64 - 2^32 + 1 on 16-bit digits (Algorithm 1, Sec. 3.2.2, with GF(p) in
+ * place of GMP's Fermat ring), then carry resolve, + d, mod 2^n and
+ * extraction of the m most significant bits of the n-bit field (Sec. 3.2.3-
+ * 3.2.5).
+ *
+ * Data layout (all entry points): an integer of w bits is an array of
+ * ceil(w/64) uint64_t limbs, least significant limb first; integer bit i is bit
+ * (i mod 64) of limb floor(i/64) (the least-significant-word-first import of
+ * Sec. 3.2.1). Input bits at positions >= n are ignored (operands are elements
+ * of Z_{2^n}); output bits at positions >= m are written as zero.
+ *
+ * Ownership: every buffer passed in is owned by the caller and must stay
+ * valid until the work queued on `stream` has finished. Device pointers must
+ * point to memory of the current CUDA device. The library owns its transform
+ * workspace (stream-ordered allocations from its own memory pool) and its
+ * twiddle tables (one set per device and transform size, kept until
+ * pa_shutdown or process exit).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ * default stream. Calls are asynchronous unless stated otherwise. The first
+ * call for a new transform size on a device builds that size's twiddle tables
+ * with a synchronous upload, so make that first call (or pa_prepare) before
+ * any stream capture.
+ *
+ * Errors: every entry point returns an int status. On PA_EINVAL nothing has
+ * been queued. A CUDA error while queueing returns PA_ECUDA (the message is
+ * available from pa_last_error()).
+ */
+#ifndef PA_GB300_H
+#define PA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_OK 0
+#define PA_EINVAL (-1)   /* bad size, null pointer, m > n, or n beyond PA_MAX_BITS */
+#define PA_ENOMEM (-2)   /* device or host allocation failed */
+#define PA_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define PA_EAGAIN (-4)   /* serving: not admitted now / result not ready */
+#define PA_ETIMEOUT (-5) /* serving: a bounded wait expired */
+
+/* Largest key length: 2^31 bits (transform length 2^28, two 2 GiB buffers). */
+#define PA_MAX_BITS (1ull << 31)
+
+/*
+ * pa_hash: out = floor(((seed_a * key + seed_b) mod 2^n) / 2^(n-m)).
+ *   key, seed_a, seed_b : device pointers, ceil(n/64) limbs each (read only)
+ *   n                   : key length in bits, 1 <= n <= PA_MAX_BITS
+ *   m                   : output length in bits, 1 <= m <= n (the final-key
+ *                         length r of Sec. 2.2 Eq. 1 and Sec. 3.2.5)
+ *   out                 : device pointer, ceil(m/64) limbs (written)
+ *   stream              : cudaStream_t or NULL
+ * seed_a need not be odd: the formula is evaluated for any value (the family
+ * of Eq. 6 draws odd c; that is the caller's choice of seed).
+ * Returns PA_OK once all kernels are queued (asynchronous).
+ */
+int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
+            uint64_t m, uint64_t* out, void* stream);
+
+/*
+ * pa_hash_host: pa_hash on HOST buffers (same shapes). Copies the inputs to
+ * the device, hashes, copies the result back and waits for the stream, so it
+ * returns with `out` filled. Pinned host memory gives asynchronous copies;
+ * pageable memory also works. Device staging buffers come from the library's
+ * pool.
+ */
+int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
+                 uint64_t n, uint64_t m, uint64_t* out, void* stream);
+
+/*
+ * pa_convolve16: the digit product of Algorithm 1 steps 1-5 (zero fill,
+ * split into 16-bit digits, forward NTTs, pointwise product, inverse NTT),
+ * before any carry:
+ *   coef[k] = sum_{i+j=k} x_i a_j,  k < L = ceil(n/16),
+ * where x_i, a_j are the 16-bit digits of key and seed_a reduced mod 2^n.
+ *   key, seed_a : device, ceil(n/64) limbs;  coef : device, L words (written)
+ * Each coef[k] < L * 2^32 < 2^64.
+ */
+int pa_convolve16(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t* coef,
+                  void* stream);
+
+/*
+ * pa_carry_extract: Algorithm 1 steps 6-7 plus Sec. 3.2.2-3.2.5 on given
+ * digits: out = floor(((sum_{k<L} coef[k] 2^(16k) + seed_b) mod 2^n) / 2^(n-m)).
+ *   coef : device, L words, each < 2^64, digit k weighing 2^(16k); digits at
+ *          k >= L count as zero (L = ceil(n/16) covers every digit below 2^n)
+ *   L    : number of words in coef (may be smaller than ceil(n/16))
+ *   seed_b : device, ceil(n/64) limbs;  out : device, ceil(m/64) limbs
+ */
+int pa_carry_extract(const uint64_t* coef, uint64_t L, const uint64_t* seed_b, uint64_t n,
+                     uint64_t m, uint64_t* out, void* stream);
+
+/* One hash problem for the batched call (all pointers device pointers). */
+typedef struct {
+    const uint64_t* key;
+    const uint64_t* seed_a;
+    const uint64_t* seed_b;
+    uint64_t n;
+    uint64_t m;
+    uint64_t* out;
+} pa_block;
+
+/*
+ * pa_hash_batched: hash `count` independent blocks of any sizes on `stream`.
+ * `blocks` is a host array read during the call only. Each result equals the
+ * result of pa_hash on that block alone. All blocks are validated before any
+ * work is queued (PA_EINVAL if any is invalid).
+ */
+int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream);
+
+/*
+ * pa_prepare: build the twiddle tables for transforms that serve keys of up
+ * to n bits on the current device (synchronous). Optional: pa_hash does this
+ * lazily. Call it before capturing a stream into a CUDA graph.
+ */
+int pa_prepare(uint64_t n);
+
+/* pa_workspace_bytes: device workspace one pa_hash of n bits draws from the pool. */
+uint64_t pa_workspace_bytes(uint64_t n);
+
+/* Per-kernel device time, aggregated by kernel name (see pa_profile). */
+typedef struct {
+    char name[32];
+    uint32_t launches;
+    double total_ms;
+} pa_kernel_stat;
+
+/*
+ * pa_profile: on != 0 starts recording a CUDA event pair around every kernel
+ * launch the library queues (on the launching stream); 0 stops recording.
+ * Recording adds two event records per launch.
+ */
+int pa_profile(int on);
+
+/*
+ * pa_profile_collect: wait for the recorded events, aggregate the elapsed
+ * time per kernel name into stats[0 .. cap), clear the records, and return the
+ * number of entries written (or a negative status).
+ */
+int pa_profile_collect(pa_kernel_stat* stats, int cap);
+
+/* pa_shutdown: free tables and pooled memory of all devices (no work may be in flight). */
+int pa_shutdown(void);
+
+/* Human-readable text of the last error on the calling thread ("" if none). */
+const char* pa_last_error(void);
+
+/* Library version string. */
+const char* pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_GB300_H */

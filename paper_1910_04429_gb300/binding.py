@@ -1,0 +1,202 @@
+"""Thin ctypes binding of libpa_gb300.so (the C ABI of include/pa.h).
+
+Argument marshalling only: every step of the hash runs in the library's CUDA
+kernels. Device operands are torch CUDA tensors of dtype int64 (or uint64)
+holding little-endian 64-bit limbs; host operands are numpy uint64 arrays.
+There is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_EAGAIN, PA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+PA_MAX_BITS = 1 << 31
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "pa_hash": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
+                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "pa_hash_batched": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
+    "pa_prepare": ([ctypes.c_uint64], ctypes.c_int),
+    "pa_workspace_bytes": ([ctypes.c_uint64], ctypes.c_uint64),
+    "pa_shutdown": ([], ctypes.c_int),
+    "pa_profile": ([ctypes.c_int], ctypes.c_int),
+    "pa_profile_collect": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "pa_last_error": ([], ctypes.c_char_p),
+    "pa_version": ([], ctypes.c_char_p),
+}
+
+
+class PaBlock(ctypes.Structure):
+    """Mirror of ``pa_block`` in include/pa.h."""
+
+    _fields_ = [("key", ctypes.c_void_p), ("seed_a", ctypes.c_void_p), ("seed_b", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("m", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
+class PaKernelStat(ctypes.Structure):
+    """Mirror of ``pa_kernel_stat`` in include/pa.h."""
+
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
+
+
+class PaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it from csrc/ if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(path):
+                raise PaError(PA_ECUDA, f"CUDA library {path} is missing; run build()")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != PA_OK:
+        raise PaError(rc, f"{what}: {load().pa_last_error().decode()}")
+
+
+def _dev_ptr(t, limbs: int, name: str):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int64/uint64 tensor")
+    if t.numel() < limbs:
+        raise ValueError(f"{name} has {t.numel()} limbs, needs {limbs}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def limbs(bits: int) -> int:
+    return (bits + 63) // 64
+
+
+def hash(key, seed_a, seed_b, n: int, m: int, out=None, stream=None):
+    """out = floor(((seed_a*key + seed_b) mod 2^n) / 2^(n-m)) on the GPU (asynchronous)."""
+    import torch
+
+    L = limbs(n)
+    if out is None:
+        out = torch.empty(limbs(m), dtype=torch.int64, device=key.device)
+    args = [_dev_ptr(key, L, "key"), _dev_ptr(seed_a, L, "seed_a"), _dev_ptr(seed_b, L, "seed_b")]
+    _check(load().pa_hash(*args, n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)), "pa_hash")
+    return out
+
+
+def hash_host(key: np.ndarray, seed_a: np.ndarray, seed_b: np.ndarray, n: int, m: int,
+              out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    """pa_hash_host: host arrays in, host array out (synchronous)."""
+    L = limbs(n)
+    arrs = []
+    for name, v in (("key", key), ("seed_a", seed_a), ("seed_b", seed_b)):
+        if v.dtype != np.uint64 or not v.flags.c_contiguous or v.size < L:
+            raise ValueError(f"{name} must be a contiguous uint64 array of >= {L} limbs")
+        arrs.append(ctypes.c_void_p(v.ctypes.data))
+    if out is None:
+        out = np.zeros(limbs(m), dtype=np.uint64)
+    st = ctypes.c_void_p(0) if stream is None else _stream_ptr(stream)
+    _check(load().pa_hash_host(*arrs, n, m, ctypes.c_void_p(out.ctypes.data), st), "pa_hash_host")
+    return out
+
+
+def convolve16(key, seed_a, n: int, coef=None, stream=None):
+    """Digit product coef[k] = sum_{i+j=k} x_i a_j, k < ceil(n/16) (no carry)."""
+    import torch
+
+    L16 = (n + 15) // 16
+    if coef is None:
+        coef = torch.empty(L16, dtype=torch.int64, device=key.device)
+    _check(load().pa_convolve16(_dev_ptr(key, limbs(n), "key"), _dev_ptr(seed_a, limbs(n), "seed_a"),
+                                n, _dev_ptr(coef, L16, "coef"), _stream_ptr(stream)), "pa_convolve16")
+    return coef
+
+
+def carry_extract(coef, seed_b, n: int, m: int, out=None, stream=None):
+    import torch
+
+    if out is None:
+        out = torch.empty(limbs(m), dtype=torch.int64, device=seed_b.device)
+    L = coef.numel()
+    _check(load().pa_carry_extract(_dev_ptr(coef, L, "coef"), L, _dev_ptr(seed_b, limbs(n), "seed_b"),
+                                   n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)),
+           "pa_carry_extract")
+    return out
+
+
+def hash_batched(blocks, stream=None):
+    """blocks: sequence of (key, seed_a, seed_b, n, m, out) with CUDA tensors."""
+    arr = (PaBlock * len(blocks))()
+    for i, (k, a, b, n, m, o) in enumerate(blocks):
+        L = limbs(n)
+        arr[i] = PaBlock(_dev_ptr(k, L, "key").value, _dev_ptr(a, L, "seed_a").value,
+                         _dev_ptr(b, L, "seed_b").value, n, m, _dev_ptr(o, limbs(m), "out").value)
+    _check(load().pa_hash_batched(arr, len(blocks), _stream_ptr(stream)), "pa_hash_batched")
+
+
+def prepare(n: int):
+    _check(load().pa_prepare(n), "pa_prepare")
+
+
+def workspace_bytes(n: int) -> int:
+    return int(load().pa_workspace_bytes(n))
+
+
+def profile(on: bool):
+    _check(load().pa_profile(1 if on else 0), "pa_profile")
+
+
+def profile_collect() -> dict:
+    """{kernel name: (launches, total_ms)} recorded since pa_profile(1)."""
+    cap = 64
+    arr = (PaKernelStat * cap)()
+    n = load().pa_profile_collect(ctypes.cast(arr, ctypes.c_void_p), cap)
+    if n < 0:
+        _check(n, "pa_profile_collect")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n)}
+
+
+def version() -> str:
+    return load().pa_version().decode()
+
+
+def raw():
+    """The loaded ctypes library (for status-code tests)."""
+    return load()

@@ -1,0 +1,156 @@
+// Goldilocks prime field GF(p), p = 2^64 - 2^32 + 1.
+//
+// The exact multiply of the G_{c,d} hash (arXiv 1910.04429, Sec. 3.2.2,
+// Algorithm 1) is done here with a number-theoretic transform over this prime
+// instead of GMP's Fermat-ring Schonhage-Strassen. Reduction uses the shape of p:
+// 2^64 = 2^32 - 1 (mod p) and 2^96 = -1 (mod p), so 2 is a 192-th root of unity
+// and 8 = 2^3 a primitive 64-th root: DFTs of length <= 64 need no general
+// multiplies, only the shift-multiplies below.
+//
+// All values are kept canonical (in [0, p)).
+#pragma once
+#include <stdint.h>
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+#if defined(__CUDACC__)
+#define GL_HD __host__ __device__ __forceinline__
+#else
+#define GL_HD inline
+#endif
+
+namespace gl {
+
+constexpr u64 P = 0xFFFFFFFF00000001ull;
+constexpr u64 EPS = 0xFFFFFFFFull;  // 2^64 mod p
+
+GL_HD u64 add(u64 a, u64 b) {
+    u64 s = a + b;
+    if (s < a) s += EPS;  // wrapped: s + 2^64 = s + EPS (mod p); cannot wrap again
+    if (s >= P) s -= P;
+    return s;
+}
+
+GL_HD u64 sub(u64 a, u64 b) {
+    u64 d = a - b;
+    if (a < b) d += P;  // a - b + p, computed mod 2^64
+    return d;
+}
+
+GL_HD u64 neg(u64 a) { return a ? P - a : 0; }
+
+// (hi:lo) mod p for any 128-bit value, using 2^64 = EPS and 2^96 = -1.
+GL_HD u64 reduce128(u64 lo, u64 hi) {
+    u64 h0 = hi & 0xFFFFFFFFull, h1 = hi >> 32;
+    u64 t = lo - h1;                // lo - h1*2^96 -> lo - h1
+    if (lo < h1) t -= EPS;          // borrow of 2^64 = EPS
+    u64 u = (h0 << 32) - h0;        // h0 * 2^64 -> h0 * EPS
+    u64 r = t + u;
+    if (r < u) r += EPS;            // carry of 2^64 = EPS; cannot carry again
+    if (r >= P) r -= P;
+    return r;
+}
+
+GL_HD u64 mul(u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+    return reduce128(a * b, __umul64hi(a, b));
+#else
+    unsigned __int128 t = (unsigned __int128)a * b;
+    return reduce128((u64)t, (u64)(t >> 64));
+#endif
+}
+
+// x * 2^S mod p for a compile-time S in [0, 192).
+template <int S>
+GL_HD u64 shl(u64 x) {
+    static_assert(S >= 0 && S < 192, "shift out of range");
+    if constexpr (S >= 96) {
+        return neg(shl<S - 96>(x));         // 2^96 = -1
+    } else if constexpr (S == 0) {
+        return x;
+    } else if constexpr (S < 64) {
+        return reduce128(x << S, x >> (64 - S));
+    } else if constexpr (S == 64) {
+        return reduce128(0, x);
+    } else {
+        // x * 2^S = (x * 2^(S-64)) * 2^64, the inner product below 2^96
+        return reduce128(0, reduce128(x << (S - 64), x >> (128 - S)));
+    }
+}
+
+GL_HD u64 pow(u64 b, u64 e) {
+    u64 r = 1;
+    while (e) {
+        if (e & 1) r = mul(r, b);
+        b = mul(b, b);
+        e >>= 1;
+    }
+    return r;
+}
+
+}  // namespace gl
+
+namespace gl {
+
+// x * 2^s mod p for a run-time s in [0, 192). Inside fully unrolled loops s
+// is a constant and the branches fold away; where s varies it is uniform
+// across a warp in every caller, so the branches do not diverge.
+GL_HD u64 shl_v(u64 x, int s) {
+    bool negate = s >= 96;
+    if (negate) s -= 96;
+    u64 r;
+    if (s == 0) r = x;
+    else if (s < 64) r = reduce128(x << s, x >> (64 - s));
+    else if (s == 64) r = reduce128(0, x);
+    else r = reduce128(0, reduce128(x << (s - 64), x >> (128 - s)));
+    return negate ? neg(r) : r;
+}
+
+// Shift for w^e where w = 2^(192/R) is the R-th root of unity used by every
+// radix-R DFT here (R | 64); INV selects w^-e.
+template <int R, bool INV>
+GL_HD int root_shift(int e) {
+    int s = ((192 / R) * e) % 192;
+    return INV ? (192 - s) % 192 : s;
+}
+
+// In-register DFT of length R in {1, 2, 4, 8}, natural order in and out:
+// v[k] <- sum_j v[j] w^(jk), w = 2^(192/R) (or its inverse), no 1/R scaling.
+template <int R, bool INV>
+GL_HD void dft(u64* v) {
+    if constexpr (R == 1) {
+        (void)v;
+    } else if constexpr (R == 2) {
+        u64 a = v[0], b = v[1];
+        v[0] = add(a, b);
+        v[1] = sub(a, b);
+    } else if constexpr (R == 4) {
+        // w = 2^48 (forward); w^2 = -1
+        u64 a = add(v[0], v[2]), b = sub(v[0], v[2]);
+        u64 c = add(v[1], v[3]);
+        u64 d = shl_v(sub(v[1], v[3]), root_shift<4, INV>(1));
+        v[0] = add(a, c);
+        v[2] = sub(a, c);
+        v[1] = add(b, d);
+        v[3] = sub(b, d);
+    } else if constexpr (R == 8) {
+        // one radix-2 decimation-in-frequency step, then two length-4 DFTs:
+        // X[2k] = DFT4(v_i + v_{i+4}), X[2k+1] = DFT4((v_i - v_{i+4}) w^i)
+        u64 s[4], t[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            s[i] = add(v[i], v[i + 4]);
+            t[i] = shl_v(sub(v[i], v[i + 4]), root_shift<8, INV>(i));
+        }
+        dft<4, INV>(s);
+        dft<4, INV>(t);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[2 * k] = s[k];
+            v[2 * k + 1] = t[k];
+        }
+    }
+}
+
+}  // namespace gl

@@ -1,0 +1,275 @@
+// Per-thread phases of the NTT tile kernels.
+//
+// The exact product of Algorithm 1 (Sec. 3.2.2: zero fill and split, evaluate
+// by NTT, pointwise multiply, interpolate by inverse NTT) is computed with a
+// length-N transform over GF(p), N = 2^k. The transform is factored
+// (Cooley-Tukey, decimation in frequency) into passes; each pass works on
+// independent tiles of 4096 elements held by one 512-thread CTA:
+//
+//  * a strided pass of radix R (2..64) over stride S: for every column j < S of
+//    a sub-problem of size M = R*S, a length-R DFT down the column, then the
+//    inter-pass twiddle w_M^(j*k) on output k (in place, k replacing the digit);
+//  * one contiguous pass over 4096 consecutive elements (64 x 64 tile: column
+//    DFTs, the twiddle w_4096^(c*k), row DFTs).
+// Every length-64 DFT is 8 x 8 with in-register length-8 DFTs; all their
+// roots are powers of 2 (w_64 = 8), so only shift-multiplies occur inside.
+// The spectrum ends up in a fixed digit-reversed order, identical for both
+// operands, and the inverse passes run the same steps mirrored, so the
+// pointwise product needs no reordering.
+//
+// Each phase is a function of (thread or work item, registers) so that the
+// kernels are plain sequences of phases separated by __syncthreads().
+#pragma once
+#include "gl.cuh"
+
+namespace pa {
+
+constexpr int TILE = 4096;
+constexpr int NT = 512;  // threads per tile CTA
+
+// ---------------------------------------------------------------------------
+// twiddles
+// ---------------------------------------------------------------------------
+struct Twiddles {
+    const u64* w4096;   // w_4096^t, t < 4096
+    const u64* w4096i;  // w_4096^-t
+    const u64* wlo;     // w_N^t, t < 4096
+    const u64* wloi;
+    const u64* whi;     // w_N^(4096 t), t < N / 4096
+    const u64* whii;
+};
+
+template <bool INV>
+GL_HD u64 omega_n(const Twiddles& tw, u64 e) {  // w_N^(+-e), e < N
+    const u64* lo = INV ? tw.wloi : tw.wlo;
+    const u64* hi = INV ? tw.whii : tw.whi;
+    return gl::mul(lo[e & 4095], hi[e >> 12]);
+}
+
+// ---------------------------------------------------------------------------
+// key digits: the 16-bit coefficients of Algorithm 1's split step
+// ---------------------------------------------------------------------------
+struct Digits {
+    const uint16_t* src;  // little-endian limbs viewed as 16-bit digits
+    u64 L;                // live digits: ceil(n / 16)
+    uint16_t top_mask;    // mask of digit L-1 (bits >= n cleared)
+};
+
+GL_HD u64 digit_at(const Digits& d, u64 pos) {
+    if (pos >= d.L) return 0;  // zero fill (Algorithm 1, step 1)
+    uint16_t v = d.src[pos];
+    if (pos == d.L - 1) v &= d.top_mask;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// strided pass, radix R = RA * RB, tile = R rows x C columns
+// ---------------------------------------------------------------------------
+struct StridedGeom {
+    u64 N, M, S;  // transform length, sub-problem size, stride (= M / R)
+};
+
+template <int RA, int RB>
+struct Strided {
+    static constexpr int R = RA * RB;
+    static constexpr int C = TILE / R;
+
+    // global position of (digit d, column c) in tile t
+    static GL_HD u64 pos(const StridedGeom& g, u64 t, int c, int d, u64* jlow) {
+        u64 tpb = g.S / C;
+        u64 b = t / tpb, cg = t % tpb;
+        *jlow = cg * C + c;
+        return b * g.M + *jlow + g.S * (u64)d;
+    }
+
+    // forward, step 1: length-RB DFT over j1 of digits j0 + RA*j1, twiddle w_R^(j0 kr)
+    template <bool PACK>
+    static GL_HD void fwd_a(const StridedGeom& g, u64 t, int it, const u64* buf,
+                            const Digits& dig, u64* sm) {
+        int j0 = it / C, c = it % C;
+        u64 v[RB];
+        u64 jl;
+#pragma unroll
+        for (int j1 = 0; j1 < RB; j1++) {
+            u64 p = pos(g, t, c, j0 + RA * j1, &jl);
+            v[j1] = PACK ? digit_at(dig, p) : buf[p];
+        }
+        gl::dft<RB, false>(v);
+#pragma unroll
+        for (int kr = 0; kr < RB; kr++) {
+            u64 w = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
+            sm[(kr * RA + j0) * C + c] = w;
+        }
+    }
+
+    // forward, step 2: length-RA DFT over j0, inter-pass twiddle, store digit k = RB ks + kr
+    static GL_HD void fwd_b(const StridedGeom& g, u64 t, int it, u64* buf, const u64* sm,
+                            const Twiddles& tw) {
+        int kr = it / C, c = it % C;
+        u64 w[RA];
+#pragma unroll
+        for (int j0 = 0; j0 < RA; j0++) w[j0] = sm[(kr * RA + j0) * C + c];
+        gl::dft<RA, false>(w);
+        u64 step = g.N / g.M;
+#pragma unroll
+        for (int ks = 0; ks < RA; ks++) {
+            int k = RB * ks + kr;
+            u64 jl;
+            u64 p = pos(g, t, c, k, &jl);
+            buf[p] = gl::mul(w[ks], omega_n<false>(tw, step * jl * (u64)k));
+        }
+    }
+
+    // inverse, mirror of fwd_b
+    static GL_HD void inv_b(const StridedGeom& g, u64 t, int it, const u64* buf, u64* sm,
+                            const Twiddles& tw) {
+        int kr = it / C, c = it % C;
+        u64 w[RA];
+        u64 step = g.N / g.M;
+#pragma unroll
+        for (int ks = 0; ks < RA; ks++) {
+            int k = RB * ks + kr;
+            u64 jl;
+            u64 p = pos(g, t, c, k, &jl);
+            w[ks] = gl::mul(buf[p], omega_n<true>(tw, step * jl * (u64)k));
+        }
+        gl::dft<RA, true>(w);
+#pragma unroll
+        for (int j0 = 0; j0 < RA; j0++) sm[(kr * RA + j0) * C + c] = w[j0];
+    }
+
+    // inverse, mirror of fwd_a; LAST keeps only positions < keep
+    template <bool LAST>
+    static GL_HD void inv_a(const StridedGeom& g, u64 t, int it, u64* buf, const u64* sm,
+                            u64 keep) {
+        int j0 = it / C, c = it % C;
+        u64 v[RB];
+#pragma unroll
+        for (int kr = 0; kr < RB; kr++)
+            v[kr] = gl::shl_v(sm[(kr * RA + j0) * C + c], gl::root_shift<R, true>(j0 * kr));
+        gl::dft<RB, true>(v);
+#pragma unroll
+        for (int j1 = 0; j1 < RB; j1++) {
+            u64 jl;
+            u64 p = pos(g, t, c, j0 + RA * j1, &jl);
+            if (!LAST || p < keep) buf[p] = v[j1];
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// contiguous 4096-element pass: 64 x 64 tile, element (r, c) at offset 64 r + c
+// ---------------------------------------------------------------------------
+GL_HD int sidx(int r, int c) { return r * 64 + (c ^ (r & 15)); }  // bank-conflict-free swizzle
+
+struct Lane {
+    int u;    // warp & 7: j0 or kr of the current step (uniform in a warp)
+    int idx;  // 32 * (warp >> 3) + lane: the column (or row) this thread owns
+};
+GL_HD Lane lane_of(int t) { return Lane{(t >> 5) & 7, 32 * (t >> 8) + (t & 31)}; }
+
+// F1: column c = idx, digits u + 8 j1: length-8 DFT, twiddle w_64^(u kr) -> smem row kr*8+u
+template <bool PACK>
+GL_HD void c_fwd_col_a(int t, const u64* src, const Digits& dig, u64 base, u64* sm) {
+    Lane ln = lane_of(t);
+    u64 v[8];
+#pragma unroll
+    for (int j1 = 0; j1 < 8; j1++) {
+        int off = (ln.u + 8 * j1) * 64 + ln.idx;
+        v[j1] = PACK ? digit_at(dig, base + off) : src[off];
+    }
+    gl::dft<8, false>(v);
+#pragma unroll
+    for (int kr = 0; kr < 8; kr++)
+        sm[sidx(kr * 8 + ln.u, ln.idx)] = gl::shl_v(v[kr], gl::root_shift<64, false>(ln.u * kr));
+}
+
+// F3: kr = u: length-8 DFT over j0, twiddle w_4096^(c k) with k = 8 ks + kr (regs only)
+GL_HD void c_fwd_col_b_load(int t, const u64* sm, const Twiddles& tw, u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0++) v[j0] = sm[sidx(ln.u * 8 + j0, ln.idx)];
+    gl::dft<8, false>(v);
+#pragma unroll
+    for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(v[ks], tw.w4096[ln.idx * (8 * ks + ln.u)]);
+}
+// F4: row k of the tile receives column c's output k
+GL_HD void c_fwd_col_b_store(int t, u64* sm, const u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int ks = 0; ks < 8; ks++) sm[sidx(8 * ks + ln.u, ln.idx)] = v[ks];
+}
+// F5: row r = idx, columns u + 8 j1: length-8 DFT, twiddle w_64^(u kr)
+GL_HD void c_fwd_row_a_load(int t, const u64* sm, u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int j1 = 0; j1 < 8; j1++) v[j1] = sm[sidx(ln.idx, ln.u + 8 * j1)];
+    gl::dft<8, false>(v);
+#pragma unroll
+    for (int kr = 0; kr < 8; kr++) v[kr] = gl::shl_v(v[kr], gl::root_shift<64, false>(ln.u * kr));
+}
+// F6
+GL_HD void c_fwd_row_a_store(int t, u64* sm, const u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int kr = 0; kr < 8; kr++) sm[sidx(ln.idx, kr * 8 + ln.u)] = v[kr];
+}
+// F7: kr = u: length-8 DFT over j0; v[ks] is the spectrum at (r, 8 ks + kr)
+GL_HD void c_fwd_row_b_load(int t, const u64* sm, u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0++) v[j0] = sm[sidx(ln.idx, ln.u * 8 + j0)];
+    gl::dft<8, false>(v);
+}
+
+// I1: inverse of F7
+GL_HD void c_inv_row_b_store(int t, u64* sm, u64* v) {
+    Lane ln = lane_of(t);
+    gl::dft<8, true>(v);
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0++) sm[sidx(ln.idx, ln.u * 8 + j0)] = v[j0];
+}
+// I2: inverse of F5 (j0 = u)
+GL_HD void c_inv_row_a_load(int t, const u64* sm, u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int kr = 0; kr < 8; kr++)
+        v[kr] = gl::shl_v(sm[sidx(ln.idx, kr * 8 + ln.u)], gl::root_shift<64, true>(ln.u * kr));
+    gl::dft<8, true>(v);
+}
+// I3
+GL_HD void c_inv_row_a_store(int t, u64* sm, const u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int j1 = 0; j1 < 8; j1++) sm[sidx(ln.idx, ln.u + 8 * j1)] = v[j1];
+}
+// I4: inverse of F3 (kr = u)
+GL_HD void c_inv_col_b_load(int t, const u64* sm, const Twiddles& tw, u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int ks = 0; ks < 8; ks++)
+        v[ks] = gl::mul(sm[sidx(8 * ks + ln.u, ln.idx)], tw.w4096i[ln.idx * (8 * ks + ln.u)]);
+    gl::dft<8, true>(v);
+}
+// I5
+GL_HD void c_inv_col_b_store(int t, u64* sm, const u64* v) {
+    Lane ln = lane_of(t);
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0++) sm[sidx(ln.u * 8 + j0, ln.idx)] = v[j0];
+}
+// I6: inverse of F1 (j0 = u): rows u + 8 j1 of column c go back to global
+GL_HD void c_inv_col_a(int t, const u64* sm, u64* dst, u64 base, u64 keep) {
+    Lane ln = lane_of(t);
+    u64 v[8];
+#pragma unroll
+    for (int kr = 0; kr < 8; kr++)
+        v[kr] = gl::shl_v(sm[sidx(kr * 8 + ln.u, ln.idx)], gl::root_shift<64, true>(ln.u * kr));
+    gl::dft<8, true>(v);
+#pragma unroll
+    for (int j1 = 0; j1 < 8; j1++) {
+        int off = (ln.u + 8 * j1) * 64 + ln.idx;
+        if (base + off < keep) dst[off] = v[j1];
+    }
+}
+
+}  // namespace pa

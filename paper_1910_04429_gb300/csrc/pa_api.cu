@@ -1,0 +1,365 @@
+// C ABI of the library (declared in include/pa.h): argument checks, plan and
+// twiddle-table cache, stream-ordered workspace, and the launch sequence of
+// the G_{c,d} hash (Sec. 2.3 Eq. 7; pipeline of Sec. 3.2).
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/pa.h"
+#include "pa_internal.h"
+
+using namespace pa;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA;
+}
+
+struct Device {
+    cudaMemPool_t pool = nullptr;
+    std::unordered_map<int, u64*> tables;  // logN -> device twiddle tables
+};
+
+std::mutex g_mu;
+std::unordered_map<int, Device> g_dev;
+
+int current_device(int* dev) {
+    cudaError_t e = cudaGetDevice(dev);
+    return e == cudaSuccess ? PA_OK : cuda_fail(e, "cudaGetDevice");
+}
+
+// Pool with no release threshold: freed workspace stays reserved for reuse.
+int get_pool(int dev, cudaMemPool_t* out) {
+    Device& d = g_dev[dev];
+    if (!d.pool) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&d.pool, &props);
+        if (e != cudaSuccess) { d.pool = nullptr; return cuda_fail(e, "cudaMemPoolCreate"); }
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = d.pool;
+    return PA_OK;
+}
+
+int get_tables(int dev, int logN, Twiddles* tw) {
+    Device& d = g_dev[dev];
+    auto it = d.tables.find(logN);
+    u64* p = nullptr;
+    if (it == d.tables.end()) {
+        std::vector<u64> host;
+        make_tables(logN, host);
+        cudaError_t e = cudaMalloc(&p, host.size() * sizeof(u64));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(twiddles)");
+        e = cudaMemcpy(p, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(p); return cuda_fail(e, "cudaMemcpy(twiddles)"); }
+        d.tables[logN] = p;
+    } else {
+        p = it->second;
+    }
+    u64 nh = (1ull << logN) >> 12;
+    tw->w4096 = p;
+    tw->w4096i = p + 4096;
+    tw->wlo = p + 8192;
+    tw->wloi = p + 12288;
+    tw->whi = p + 16384;
+    tw->whii = p + 16384 + nh;
+    return PA_OK;
+}
+
+struct Scratch {
+    cudaStream_t st;
+    cudaMemPool_t pool;
+    std::vector<void*> ptrs;
+    Scratch(cudaStream_t s, cudaMemPool_t p) : st(s), pool(p) {}
+    int get(size_t bytes, void** out) {
+        cudaError_t e = cudaMallocFromPoolAsync(out, bytes ? bytes : 16, pool, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync");
+        ptrs.push_back(*out);
+        return PA_OK;
+    }
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+bool check_sizes(uint64_t n, uint64_t m) { return n >= 1 && m >= 1 && m <= n && n <= PA_MAX_BITS; }
+
+int logn_for_bits(uint64_t n) { return logn_for_digits((n + 15) / 16); }
+
+uint16_t top_digit_mask(uint64_t n) {
+    return (n & 15) ? (uint16_t)((1u << (n & 15)) - 1) : (uint16_t)0xFFFF;
+}
+
+// Queue steps 1-5 of Algorithm 1; on success *coef points at the digits (k < L).
+int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, cudaStream_t st,
+                      Scratch& scr, int dev, u64** coef) {
+    u64 L = (n + 15) / 16;
+    int logN = logn_for_bits(n);
+    NttJob j;
+    j.geom = make_geom(logN);
+    j.L = L;
+    int rc = get_tables(dev, logN, &j.tw);
+    if (rc) return rc;
+    void *bx, *ba;
+    if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
+    if ((rc = scr.get(j.geom.N * sizeof(u64), &ba))) return rc;
+    j.buf_x = (u64*)bx;
+    j.buf_a = (u64*)ba;
+    j.ahat = (u64*)ba;  // each tile is read completely before it is overwritten
+    uint16_t top = top_digit_mask(n);
+    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top};
+    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top};
+    cudaError_t e = launch_convolution(j, st);
+    if (e != cudaSuccess) return cuda_fail(e, "NTT launch");
+    *coef = j.buf_x;
+    return PA_OK;
+}
+
+int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint64_t m,
+                uint64_t* out, cudaStream_t st, Scratch& scr) {
+    u64 tiles = carry_tiles(n);
+    void *agg, *cin;
+    int rc;
+    if ((rc = scr.get(tiles, &agg))) return rc;
+    if ((rc = scr.get(tiles, &cin))) return rc;
+    CarryJob c{coef, L, seed_b, n, m, out, (uint8_t*)agg, (uint8_t*)cin};
+    cudaError_t e = launch_carry(c, st);
+    if (e != cudaSuccess) return cuda_fail(e, "carry launch");
+    return PA_OK;
+}
+
+int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
+                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool) {
+    Scratch scr(st, pool);
+    u64* coef = nullptr;
+    int rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef);
+    if (rc) return rc;
+    return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr);
+}
+
+int setup(int* dev, cudaMemPool_t* pool) {
+    int rc = current_device(dev);
+    if (rc) return rc;
+    return get_pool(*dev, pool);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// per-kernel CUDA-event profiling
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+}  // namespace
+
+namespace pa {
+void prof_begin(cudaStream_t st, const char* name) {
+    if (!g_prof_on) return;
+    ProfRec r{name, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess) return;
+    if (cudaEventCreate(&r.b) != cudaSuccess) { cudaEventDestroy(r.a); return; }
+    cudaEventRecord(r.a, st);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(r);
+}
+void prof_end(cudaStream_t st) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof.empty()) cudaEventRecord(g_prof.back().b, st);
+}
+}  // namespace pa
+
+extern "C" {
+
+int pa_profile(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return PA_OK;
+}
+
+int pa_profile_collect(pa_kernel_stat* stats, int cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<pa_kernel_stat> agg;
+    int rc = PA_OK;
+    for (ProfRec& r : g_prof) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) rc = cuda_fail(e, "profile event");
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        pa_kernel_stat* s = nullptr;
+        for (auto& x : agg)
+            if (!strncmp(x.name, r.name, sizeof(x.name))) s = &x;
+        if (!s) {
+            agg.push_back(pa_kernel_stat{});
+            s = &agg.back();
+            strncpy(s->name, r.name, sizeof(s->name) - 1);
+        }
+        s->launches += 1;
+        s->total_ms += ms;
+    }
+    g_prof.clear();
+    if (rc) return rc;
+    int n = (int)agg.size() < cap ? (int)agg.size() : cap;
+    for (int i = 0; i < n; i++) stats[i] = agg[i];
+    return n;
+}
+
+int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
+            uint64_t m, uint64_t* out, void* stream) {
+    if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_hash: need 1 <= m <= n <= PA_MAX_BITS");
+    if (!key || !seed_a || !seed_b || !out) return fail(PA_EINVAL, "pa_hash: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    return hash_device(key, seed_a, seed_b, n, m, out, (cudaStream_t)stream, dev, pool);
+}
+
+int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
+                 uint64_t n, uint64_t m, uint64_t* out, void* stream) {
+    if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_hash_host: need 1 <= m <= n <= PA_MAX_BITS");
+    if (!key || !seed_a || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_host: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        int dev;
+        cudaMemPool_t pool;
+        if ((rc = setup(&dev, &pool))) return rc;
+        Scratch scr(st, pool);
+        size_t in_bytes = ((n + 63) / 64) * sizeof(u64), out_bytes = ((m + 63) / 64) * sizeof(u64);
+        void *dx, *da, *db, *dout;
+        if ((rc = scr.get(in_bytes, &dx)) || (rc = scr.get(in_bytes, &da)) ||
+            (rc = scr.get(in_bytes, &db)) || (rc = scr.get(out_bytes, &dout)))
+            return rc;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(dx, key, in_bytes, cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(da, seed_a, in_bytes, cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(db, seed_b, in_bytes, cudaMemcpyHostToDevice, st)))
+            return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+        rc = hash_device((const u64*)dx, (const u64*)da, (const u64*)db, n, m, (u64*)dout, st, dev,
+                         pool);
+        if (rc) return rc;
+        if ((e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st)))
+            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return PA_OK;
+}
+
+int pa_convolve16(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t* coef,
+                  void* stream) {
+    if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_convolve16: need 1 <= n <= PA_MAX_BITS");
+    if (!key || !seed_a || !coef) return fail(PA_EINVAL, "pa_convolve16: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch scr(st, pool);
+    u64* c = nullptr;
+    if ((rc = queue_convolution(key, seed_a, n, st, scr, dev, &c))) return rc;
+    cudaError_t e = cudaMemcpyAsync(coef, c, ((n + 15) / 16) * sizeof(u64),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2D)");
+    return PA_OK;
+}
+
+int pa_carry_extract(const uint64_t* coef, uint64_t L, const uint64_t* seed_b, uint64_t n,
+                     uint64_t m, uint64_t* out, void* stream) {
+    if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_carry_extract: need 1 <= m <= n <= PA_MAX_BITS");
+    if ((!coef && L) || !seed_b || !out) return fail(PA_EINVAL, "pa_carry_extract: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch scr(st, pool);
+    u64 Lmax = (n + 15) / 16;
+    return queue_carry(coef, L < Lmax ? L : Lmax, seed_b, n, m, out, st, scr);
+}
+
+int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream) {
+    if (count && !blocks) return fail(PA_EINVAL, "pa_hash_batched: null block array");
+    for (uint32_t i = 0; i < count; i++) {
+        const pa_block& b = blocks[i];
+        if (!check_sizes(b.n, b.m) || !b.key || !b.seed_a || !b.seed_b || !b.out)
+            return fail(PA_EINVAL, "pa_hash_batched: invalid block " + std::to_string(i));
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    for (uint32_t i = 0; i < count; i++) {
+        const pa_block& b = blocks[i];
+        rc = hash_device(b.key, b.seed_a, b.seed_b, b.n, b.m, b.out, (cudaStream_t)stream, dev, pool);
+        if (rc) return rc;
+    }
+    return PA_OK;
+}
+
+int pa_prepare(uint64_t n) {
+    if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_prepare: need 1 <= n <= PA_MAX_BITS");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    Twiddles tw;
+    return get_tables(dev, logn_for_bits(n), &tw);
+}
+
+uint64_t pa_workspace_bytes(uint64_t n) {
+    if (n < 1 || n > PA_MAX_BITS) return 0;
+    uint64_t N = 1ull << logn_for_bits(n);
+    return 2 * N * sizeof(u64) + 2 * carry_tiles(n);
+}
+
+int pa_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    for (auto& kv : g_dev) {
+        cudaSetDevice(kv.first);
+        for (auto& t : kv.second.tables) cudaFree(t.second);
+        if (kv.second.pool) cudaMemPoolDestroy(kv.second.pool);
+    }
+    g_dev.clear();
+    if (prev >= 0) cudaSetDevice(prev);
+    return PA_OK;
+}
+
+const char* pa_last_error(void) { return g_err.c_str(); }
+
+const char* pa_version(void) { return "pa_gb300 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

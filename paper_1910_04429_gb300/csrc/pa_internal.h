@@ -1,0 +1,48 @@
+// Internal interfaces between the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ntt_tile.cuh"
+#include "plan.h"
+
+namespace pa {
+
+// One operand pair's transform work: the key x (operand 0) and the seed a
+// (operand 1), both N-element GF(p) buffers.
+struct NttJob {
+    Geom geom;
+    Twiddles tw;
+    u64* buf_x;   // N words: transform of x, then the product digits
+    u64* buf_a;   // N words: transform of a (strided passes)
+    u64* ahat;    // N words: spectrum of a in tile register order, times N^-1
+    Digits dx, da;
+    u64 L;        // live product digits kept by the last inverse pass
+};
+
+// Launches: digits of x and a -> convolution digits c_k (k < L) in buf_x.
+cudaError_t launch_convolution(const NttJob& job, cudaStream_t st);
+
+// Carry resolve, + b, mod 2^n and extraction of bits [n-m, n) (Algorithm 1
+// steps 6-7, Sec. 3.2.2-3.2.5).
+struct CarryJob {
+    const u64* coef;  // convolution digits, coefficient k weighs 2^(16k)
+    u64 L;            // digits present (coef[k] = 0 for k >= L)
+    const u64* b;     // addend limbs, ceil(n/64)
+    u64 n, m;
+    u64* out;         // ceil(m/64) limbs
+    uint8_t* agg;     // per-tile carry aggregates (scratch)
+    uint8_t* cin;     // per-tile carry-in (scratch)
+};
+constexpr int CARRY_THREADS = 256;
+constexpr int CARRY_LIMBS = 4;  // limbs per thread
+constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
+inline u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
+cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
+
+// Per-kernel timing with CUDA events on the launching stream (off unless
+// pa_profile(1) was called). prof_begin/prof_end bracket one launch.
+void prof_begin(cudaStream_t st, const char* name);
+void prof_end(cudaStream_t st);
+
+}  // namespace pa

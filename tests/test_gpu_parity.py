@@ -1,0 +1,212 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work: the bar is exact equality of every output limb.
+"""
+import hashlib
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_04429_gb300 import binding, inputs
+from tests.gpu_util import dev, gpu_hash, host
+from tests.intutil import from_int, to_int
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    binding.load()
+    yield
+
+
+def _check_block(blk, threads=None):
+    got = gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m)
+    want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m,
+                          threads=threads or oracle.default_threads())
+    assert got.shape == want.shape
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"n={blk.n} m={blk.m}: {bad.size} limbs differ, first at {bad[:5]}"
+
+
+# sizes spanning every pass layout (transform lengths 2^12 .. 2^21), ragged
+# digit and limb tails, and the single-tile / multi-tile boundary
+SIZES = [1, 2, 3, 15, 16, 17, 63, 64, 65, 100, 127, 128, 129, 1000, 4095, 4097,
+         32767, 32768, 32769, 65536 + 5, 100_003, 131_072, 262_144 + 1, 524_287,
+         1_000_000, 2_097_152 + 16, 4_194_304 + 33, 8_388_609, 16_777_000]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_parity_sizes(n):
+    for m in sorted({1, max(1, n // 4), n}):
+        _check_block(inputs.make_block(n, m, seed=n + m))
+
+
+def test_parity_config1():
+    """n = 10^6 key, m = 250,000 output bits, seed 1."""
+    _check_block(inputs.make_block(1_000_000, 250_000, seed=1))
+
+
+def test_parity_every_residue_mod_64():
+    for r in range(64):
+        n = 64 * 700 + r if r else 64 * 701
+        m = [1, n // 3, n - 1, n][r % 4] or 1
+        _check_block(inputs.make_block(n, m, seed=1000 + r))
+
+
+@pytest.mark.parametrize("m_off", [1, 63, 64, 65, 127, 128])
+def test_parity_output_lengths(m_off):
+    n = 200_000 + 37
+    for m in (m_off, n - m_off):
+        _check_block(inputs.make_block(n, m, seed=m))
+
+
+@pytest.mark.parametrize("n", [1, 17, 64, 1000, 32769, 1_000_000, 3_000_017])
+def test_closed_forms(n):
+    """x = 0, a = 1, a = 2^k, a = -1, and the all-propagate carry (y = 0)."""
+    L = (n + 63) // 64
+    mask = (1 << n) - 1
+    m = max(1, n // 4)
+    sh = n - m
+    blk = inputs.make_block(n, m, seed=7)
+    x, b = to_int(blk.x), to_int(blk.b)
+    zero, one, ones = from_int(0, L), from_int(1, L), from_int(mask, L)
+
+    def run(X, A, B, mm=m):
+        return to_int(gpu_hash(binding, X, A, B, n, mm))
+
+    assert run(zero, blk.a, blk.b) == b >> sh
+    assert run(blk.x, one, blk.b) == ((x + b) & mask) >> sh
+    for k in sorted({0, 1, 17, n // 2, n - 1}):
+        if k < n:
+            assert run(blk.x, from_int(1 << k, L), blk.b) == (((x << k) + b) & mask) >> sh
+    assert run(blk.x, ones, blk.b) == ((b - x) & mask) >> sh
+    assert run(ones, one, one) == 0
+    assert run(ones, one, zero, n) == mask
+    assert run(ones, ones, zero, n) == 1  # (2^n - 1)^2 = 1 mod 2^n
+
+
+def test_inputs_above_n_are_ignored():
+    n, m = 1000, 300
+    L = (n + 63) // 64
+    rng = random.Random(3)
+    x, a, b = (from_int(rng.getrandbits(64 * L), L) for _ in range(3))
+    got = gpu_hash(binding, x, a, b, n, m)
+    want = oracle.pa_hash(x, a, b, n, m)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_convolve16_matches_digit_convolution():
+    import torch
+
+    for n in (16, 1000, 65_536, 160_000 - 5, 300_000):
+        blk = inputs.make_block(n, n, seed=n)
+        L = (n + 15) // 16
+        xd = blk.x.view(np.uint16)[:L].astype(np.int64)
+        ad = blk.a.view(np.uint16)[:L].astype(np.int64)
+        if n % 16:
+            xd[-1] &= (1 << (n % 16)) - 1
+            ad[-1] &= (1 << (n % 16)) - 1
+        want = np.convolve(xd, ad)[:L]
+        coef = binding.convolve16(dev(blk.x), dev(blk.a), n)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(coef).astype(np.int64), want)
+
+
+def _carry_ref(coef, b_int, n, m):
+    y = sum(int(c) << (16 * k) for k, c in enumerate(coef)) + b_int
+    return (y & ((1 << n) - 1)) >> (n - m)
+
+
+@pytest.mark.parametrize("pattern", ["random64", "all_ffff", "propagate", "max"])
+def test_carry_extract(pattern):
+    """Carry chains inside and across carry tiles (1024 limbs per tile)."""
+    import torch
+
+    n = 64 * 1024 * 5 + 48
+    m = n // 2 + 3
+    L = (n + 15) // 16
+    rng = np.random.default_rng(5)
+    if pattern == "random64":
+        coef = rng.integers(0, 2**63, size=L, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+        b = rng.integers(0, 2**63, size=(n + 63) // 64, dtype=np.uint64)
+    elif pattern == "all_ffff":
+        coef = np.full(L, 0xFFFF, dtype=np.uint64)          # y = 2^(16L) - 1 before + b
+        b = np.zeros((n + 63) // 64, dtype=np.uint64)
+        b[0] = 1                                            # + 1 ripples through every limb
+    elif pattern == "propagate":
+        coef = np.zeros(L, dtype=np.uint64)
+        coef[::4] = np.uint64(0xFFFFFFFFFFFFFFFF)           # each limb sum = 2^64 - 1 + carry
+        b = np.zeros((n + 63) // 64, dtype=np.uint64)
+    else:
+        coef = np.full(L, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64)
+        b = np.full((n + 63) // 64, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64)
+    out = binding.carry_extract(dev(coef), dev(b), n, m)
+    torch.cuda.synchronize()
+    assert to_int(host(out)) == _carry_ref(coef, to_int(b), n, m)
+
+
+def test_hash_host_buffers():
+    blk = inputs.make_block(3_000_000, 700_001, seed=11)
+    got = binding.hash_host(blk.x, blk.a, blk.b, blk.n, blk.m)
+    want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m, threads=oracle.default_threads())
+    np.testing.assert_array_equal(got, want)
+
+
+def test_nondefault_streams_and_repeat():
+    import torch
+
+    blks = [inputs.make_block(n, n // 5, seed=n) for n in (500_000, 1_200_000, 77_777)]
+    streams = [torch.cuda.Stream() for _ in blks]
+    outs = []
+    for blk, st in zip(blks, streams):
+        with torch.cuda.stream(st):
+            tx, ta, tb = dev(blk.x), dev(blk.a), dev(blk.b)
+            outs.append((binding.hash(tx, ta, tb, blk.n, blk.m, stream=st),
+                         binding.hash(tx, ta, tb, blk.n, blk.m, stream=st), (tx, ta, tb)))
+    torch.cuda.synchronize()
+    for blk, (o1, o2, _) in zip(blks, outs):
+        want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m)
+        np.testing.assert_array_equal(host(o1), want)
+        np.testing.assert_array_equal(host(o2), want)
+
+
+def test_batched_mixed_sizes():
+    import torch
+
+    blks = inputs.make_batch(24, 1_000, 3_000_000, seed=21)
+    tensors = [(dev(b.x), dev(b.a), dev(b.b)) for b in blks]
+    outs = [torch.empty((b.m + 63) // 64, dtype=torch.int64, device="cuda") for b in blks]
+    binding.hash_batched([(t[0], t[1], t[2], b.n, b.m, o) for b, t, o in zip(blks, tensors, outs)])
+    torch.cuda.synchronize()
+    for b, o in zip(blks, outs):
+        np.testing.assert_array_equal(host(o), oracle.pa_hash(b.x, b.a, b.b, b.n, b.m))
+
+
+def test_parity_config2_full_size():
+    """n = 10^8, m = 2.5 * 10^7, seed 1: the plain single-launch workload."""
+    _check_block(inputs.make_block(100_000_000, 25_000_000, seed=1))
+
+
+def test_parity_config5_digest():
+    """n = 10^9, m = 2.5 * 10^8, seed 1, against the stored oracle digest."""
+    path = os.path.join(GOLDEN, "oracle_digest_n1000000000_m250000000_seed1.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle digest for n = 10^9 not generated")
+    with open(path) as f:
+        rec = json.load(f)
+    blk = inputs.make_block(rec["n"], rec["m"], rec["seed"])
+    got = gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m)
+    assert got.size == rec["out_limbs"]
+    assert [f"{int(v):016x}" for v in got[:4]] == rec["first_limbs"]
+    assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == rec["sha256"]
