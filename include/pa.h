@@ -155,6 +155,39 @@ int pa_profile(int on);
  */
 int pa_profile_collect(pa_kernel_stat* stats, int cap);
 
+/* Largest key pa_hash_noalloc accepts: 2^20 bits (its fixed scratch size). */
+#define PA_NOALLOC_MAX_BITS (1ull << 20)
+
+/*
+ * pa_hash_noalloc: the same result as pa_hash, for callers that cannot
+ * allocate device memory (this entry point has no counterpart in the paper;
+ * it exists for integration). Some callers must not let a library call
+ * cudaMalloc, or allocate from a stream-ordered pool: code that builds CUDA
+ * graphs without allocation nodes, real-time post-processing loops that
+ * reserve all device memory up front and may not stall in an allocator, and
+ * programs whose device memory belongs to another framework's allocator.
+ * This entry point calls no cudaMalloc, cudaFree or other allocating routine:
+ * its device scratch (two transform buffers, twiddle tables for every
+ * transform size it serves, carry-scan bytes; about 3 MB) is a set of
+ * fixed-size arrays compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   key, seed_a, seed_b, n, m, out, stream: as for pa_hash (device pointers,
+ *   caller-owned), with n <= PA_NOALLOC_MAX_BITS.
+ * Returns PA_EINVAL (nothing queued) if n > PA_NOALLOC_MAX_BITS, for bad
+ * sizes or null pointers; PA_ECUDA if set-up or a launch fails. The message
+ * is available from pa_last_error().
+ * The first call on a device does the set-up: it looks up the arrays' device
+ * addresses, fills the twiddle tables on `stream` and waits for them. Make that
+ * first call before any stream capture. Later calls only queue kernels.
+ * All calls share the one scratch area and it keeps the previous call's
+ * contents (every word is rewritten before it is read, so nothing needs
+ * clearing). Calls whose work overlaps on the GPU (different streams, or
+ * unordered use from several threads) race on the scratch and give wrong
+ * results: order them on one stream or with events.
+ */
+int pa_hash_noalloc(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
+                    uint64_t n, uint64_t m, uint64_t* out, void* stream);
+
 /* pa_shutdown: free tables and pooled memory of all devices (no work may be in flight). */
 int pa_shutdown(void);
 

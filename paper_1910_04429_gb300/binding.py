@@ -23,6 +23,7 @@ _lib = None
 
 _SIGS = {
     "pa_hash": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_hash_noalloc": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
@@ -118,6 +119,20 @@ def hash(key, seed_a, seed_b, n: int, m: int, out=None, stream=None):
         out = torch.empty(limbs(m), dtype=torch.int64, device=key.device)
     args = [_dev_ptr(key, L, "key"), _dev_ptr(seed_a, L, "seed_a"), _dev_ptr(seed_b, L, "seed_b")]
     _check(load().pa_hash(*args, n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)), "pa_hash")
+    return out
+
+
+def hash_noalloc(key, seed_a, seed_b, n: int, m: int, out=None, stream=None):
+    """pa_hash_noalloc: the hash using only the library's fixed device scratch
+    (n <= 2^20 bits), for callers that cannot allocate device memory."""
+    import torch
+
+    L = limbs(n)
+    if out is None:
+        out = torch.empty(limbs(m), dtype=torch.int64, device=key.device)
+    args = [_dev_ptr(key, L, "key"), _dev_ptr(seed_a, L, "seed_a"), _dev_ptr(seed_b, L, "seed_b")]
+    _check(load().pa_hash_noalloc(*args, n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)),
+           "pa_hash_noalloc")
     return out
 
 

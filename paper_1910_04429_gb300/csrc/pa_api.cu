@@ -175,6 +175,8 @@ std::vector<ProfRec> g_prof;
 }  // namespace
 
 namespace pa {
+void set_error(const char* msg) { g_err = msg; }
+
 void prof_begin(cudaStream_t st, const char* name) {
     if (!g_prof_on) return;
     ProfRec r{name, nullptr, nullptr};

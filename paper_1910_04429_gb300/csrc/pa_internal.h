@@ -45,4 +45,7 @@ cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
 void prof_begin(cudaStream_t st, const char* name);
 void prof_end(cudaStream_t st);
 
+// Sets the text pa_last_error() returns on the calling thread.
+void set_error(const char* msg);
+
 }  // namespace pa

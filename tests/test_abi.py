@@ -98,6 +98,10 @@ def test_argument_checks_without_gpu():
     assert lib.pa_hash_batched(blocks, 2, null) == binding.PA_EINVAL
     assert b"block 1" in lib.pa_last_error()
     assert lib.pa_prepare(0) == binding.PA_EINVAL
+    # the fixed-scratch entry point refuses keys beyond its scratch size
+    assert lib.pa_hash_noalloc(p, p, p, (1 << 20) + 1, 1, p, null) == binding.PA_EINVAL
+    assert b"PA_NOALLOC_MAX_BITS" in lib.pa_last_error()
+    assert lib.pa_hash_noalloc(p, p, p, 10, 11, p, null) == binding.PA_EINVAL
 
 
 @pytest.mark.parametrize("n,N", [(1, 4096), (32768, 4096), (32769, 8192), (1_000_000, 1 << 17),
