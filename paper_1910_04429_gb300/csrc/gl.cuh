@@ -25,36 +25,104 @@ namespace gl {
 constexpr u64 P = 0xFFFFFFFF00000001ull;
 constexpr u64 EPS = 0xFFFFFFFFull;  // 2^64 mod p
 
+// Values are kept in [0, p]: p itself may stand for 0 inside a transform
+// (neg(0) = p); add, sub, mul and the shifts accept and return that range, and
+// canon() maps p to 0 where an exact integer leaves the field.
 GL_HD u64 add(u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+    // s = a + b (65 bits); s >= p iff s + EPS carries out of 64 bits
+    u64 s, t;
+    u32 c;
+    asm("add.cc.u64 %0, %3, %4;\n\t"
+        "addc.u32 %2, 0, 0;\n\t"
+        "add.cc.u64 %1, %0, 4294967295;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=l"(s), "=l"(t), "=r"(c)
+        : "l"(a), "l"(b));
+    return c ? t : s;
+#else
     u64 s = a + b;
-    if (s < a) s += EPS;  // wrapped: s + 2^64 = s + EPS (mod p); cannot wrap again
-    if (s >= P) s -= P;
-    return s;
+    bool c1 = s < a;
+    u64 t = s + EPS;
+    bool c2 = t < s;
+    return (c1 || c2) ? t : s;
+#endif
 }
 
 GL_HD u64 sub(u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+    // a - b; on borrow the wrapped value is 2^64 too large and 2^64 = EPS + p
+    u64 d;
+    u32 m;
+    asm("sub.cc.u64 %0, %2, %3;\n\t"
+        "subc.u32 %1, 0, 0;"
+        : "=l"(d), "=r"(m)
+        : "l"(a), "l"(b));
+    return d - (u64)m;
+#else
     u64 d = a - b;
-    if (a < b) d += P;  // a - b + p, computed mod 2^64
+    if (a < b) d -= EPS;
     return d;
+#endif
 }
 
-GL_HD u64 neg(u64 a) { return a ? P - a : 0; }
+GL_HD u64 neg(u64 a) { return P - a; }
 
-// (hi:lo) mod p for any 128-bit value, using 2^64 = EPS and 2^96 = -1.
+GL_HD u64 canon(u64 a) { return a == P ? 0 : a; }
+
+// (hi:lo) mod p for any 128-bit value, using 2^64 = EPS and 2^96 = -1;
+// result in [0, p).
 GL_HD u64 reduce128(u64 lo, u64 hi) {
+#if defined(__CUDA_ARCH__)
+    u32 h0 = (u32)hi, h1 = (u32)(hi >> 32);
+    u64 t, r, q;
+    u32 m, c, c2;
+    asm("sub.cc.u64 %0, %2, %3;\n\t"
+        "subc.u32 %1, 0, 0;"
+        : "=l"(t), "=r"(m)
+        : "l"(lo), "l"((u64)h1));
+    t -= (u64)m;                                   // lo - h1 (borrow of 2^64 = EPS)
+    u64 u;
+    asm("mul.wide.u32 %0, %1, 4294967295;" : "=l"(u) : "r"(h0));  // h0 * EPS
+    asm("add.cc.u64 %0, %2, %3;\n\t"
+        "addc.u32 %1, 0, 0;"
+        : "=l"(r), "=r"(c)
+        : "l"(t), "l"(u));
+    r += (u64)(0u - c);                            // carry of 2^64 = EPS; cannot carry again
+    asm("add.cc.u64 %0, %2, 4294967295;\n\t"
+        "addc.u32 %1, 0, 0;"
+        : "=l"(q), "=r"(c2)
+        : "l"(r));
+    return c2 ? q : r;                             // r - p when r >= p
+#else
     u64 h0 = hi & 0xFFFFFFFFull, h1 = hi >> 32;
-    u64 t = lo - h1;                // lo - h1*2^96 -> lo - h1
-    if (lo < h1) t -= EPS;          // borrow of 2^64 = EPS
-    u64 u = (h0 << 32) - h0;        // h0 * 2^64 -> h0 * EPS
+    u64 t = lo - h1;
+    if (lo < h1) t -= EPS;
+    u64 u = (h0 << 32) - h0;
     u64 r = t + u;
-    if (r < u) r += EPS;            // carry of 2^64 = EPS; cannot carry again
+    if (r < u) r += EPS;
     if (r >= P) r -= P;
     return r;
+#endif
 }
 
 GL_HD u64 mul(u64 a, u64 b) {
 #if defined(__CUDA_ARCH__)
-    return reduce128(a * b, __umul64hi(a, b));
+    // 64 x 64 -> 128 from four 32 x 32 products with one carry chain
+    u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+    u32 r0, r1, r2, r3;
+    asm("mul.lo.u32 %0, %4, %6;\n\t"
+        "mul.hi.u32 %1, %4, %6;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.u32 %2, %4, %7, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, 0;\n\t"
+        "mad.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "=&r"(r0), "=&r"(r1), "=&r"(r2), "=&r"(r3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    return reduce128(((u64)r1 << 32) | r0, ((u64)r3 << 32) | r2);
 #else
     unsigned __int128 t = (unsigned __int128)a * b;
     return reduce128((u64)t, (u64)(t >> 64));

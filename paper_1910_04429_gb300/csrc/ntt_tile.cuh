@@ -66,82 +66,87 @@ GL_HD u64 digit_at(const Digits& d, u64 pos) {
 // strided pass, radix R = RA * RB, tile = R rows x C columns
 // ---------------------------------------------------------------------------
 struct StridedGeom {
-    u64 N, M, S;  // transform length, sub-problem size, stride (= M / R)
+    u64 N, M, S;    // transform length, sub-problem size, stride (= M / R)
+    int log_tpb;    // log2 of the tiles per sub-problem, (S / C)
+};
+
+// Where tile t of a strided pass sits: sub-problem b, first column jl0.
+struct TilePos {
+    u64 base;  // b * M + jl0: position of (column 0, digit 0)
+    u64 jl0;   // first column of the tile within its sub-problem
 };
 
 template <int RA, int RB>
 struct Strided {
     static constexpr int R = RA * RB;
     static constexpr int C = TILE / R;
+    static constexpr int ITEMS_A = TILE / RB / NT;  // phase-A items per thread
+    static constexpr int ITEMS_B = TILE / RA / NT;  // phase-B items per thread
 
-    // global position of (digit d, column c) in tile t
-    static GL_HD u64 pos(const StridedGeom& g, u64 t, int c, int d, u64* jlow) {
-        u64 tpb = g.S / C;
-        u64 b = t / tpb, cg = t % tpb;
-        *jlow = cg * C + c;
-        return b * g.M + *jlow + g.S * (u64)d;
+    static GL_HD TilePos tile(const StridedGeom& g, u64 t) {
+        u64 b = t >> g.log_tpb, cg = t & ((1ull << g.log_tpb) - 1);
+        return TilePos{b * g.M + cg * C, cg * C};
     }
 
     // forward, step 1: length-RB DFT over j1 of digits j0 + RA*j1, twiddle w_R^(j0 kr)
     template <bool PACK>
-    static GL_HD void fwd_a(const StridedGeom& g, u64 t, int it, const u64* buf,
+    static GL_HD void fwd_a(const StridedGeom& g, const TilePos& tp, int it, const u64* buf,
                             const Digits& dig, u64* sm) {
         int j0 = it / C, c = it % C;
         u64 v[RB];
-        u64 jl;
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {
-            u64 p = pos(g, t, c, j0 + RA * j1, &jl);
+            u64 p = tp.base + c + g.S * (u64)(j0 + RA * j1);
             v[j1] = PACK ? digit_at(dig, p) : buf[p];
         }
         gl::dft<RB, false>(v);
 #pragma unroll
-        for (int kr = 0; kr < RB; kr++) {
-            u64 w = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
-            sm[(kr * RA + j0) * C + c] = w;
-        }
+        for (int kr = 0; kr < RB; kr++)
+            sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
     }
 
-    // forward, step 2: length-RA DFT over j0, inter-pass twiddle, store digit k = RB ks + kr
-    static GL_HD void fwd_b(const StridedGeom& g, u64 t, int it, u64* buf, const u64* sm,
-                            const Twiddles& tw) {
+    // inter-pass twiddles w_M^(jl k) of one phase-B item, k = RB ks + kr
+    static GL_HD void twiddles(const StridedGeom& g, const TilePos& tp, int it, const Twiddles& tw,
+                               u64* w) {
         int kr = it / C, c = it % C;
-        u64 w[RA];
+        u64 e = (g.N / g.M) * (tp.jl0 + c);
 #pragma unroll
-        for (int j0 = 0; j0 < RA; j0++) w[j0] = sm[(kr * RA + j0) * C + c];
-        gl::dft<RA, false>(w);
-        u64 step = g.N / g.M;
+        for (int ks = 0; ks < RA; ks++) w[ks] = omega_n<false>(tw, e * (u64)(RB * ks + kr));
+    }
+
+    // forward, step 2: length-RA DFT over j0, times the twiddles, store digit k = RB ks + kr
+    static GL_HD void fwd_b(const StridedGeom& g, const TilePos& tp, int it, u64* buf,
+                            const u64* sm, const u64* w) {
+        int kr = it / C, c = it % C;
+        u64 v[RA];
 #pragma unroll
-        for (int ks = 0; ks < RA; ks++) {
-            int k = RB * ks + kr;
-            u64 jl;
-            u64 p = pos(g, t, c, k, &jl);
-            buf[p] = gl::mul(w[ks], omega_n<false>(tw, step * jl * (u64)k));
-        }
+        for (int j0 = 0; j0 < RA; j0++) v[j0] = sm[(kr * RA + j0) * C + c];
+        gl::dft<RA, false>(v);
+#pragma unroll
+        for (int ks = 0; ks < RA; ks++)
+            buf[tp.base + c + g.S * (u64)(RB * ks + kr)] = gl::mul(v[ks], w[ks]);
     }
 
     // inverse, mirror of fwd_b
-    static GL_HD void inv_b(const StridedGeom& g, u64 t, int it, const u64* buf, u64* sm,
+    static GL_HD void inv_b(const StridedGeom& g, const TilePos& tp, int it, const u64* buf, u64* sm,
                             const Twiddles& tw) {
         int kr = it / C, c = it % C;
         u64 w[RA];
-        u64 step = g.N / g.M;
+        u64 e = (g.N / g.M) * (tp.jl0 + c);
 #pragma unroll
         for (int ks = 0; ks < RA; ks++) {
-            int k = RB * ks + kr;
-            u64 jl;
-            u64 p = pos(g, t, c, k, &jl);
-            w[ks] = gl::mul(buf[p], omega_n<true>(tw, step * jl * (u64)k));
+            u64 k = RB * ks + kr;
+            w[ks] = gl::mul(buf[tp.base + c + g.S * k], omega_n<true>(tw, e * k));
         }
         gl::dft<RA, true>(w);
 #pragma unroll
         for (int j0 = 0; j0 < RA; j0++) sm[(kr * RA + j0) * C + c] = w[j0];
     }
 
-    // inverse, mirror of fwd_a; LAST keeps only positions < keep
+    // inverse, mirror of fwd_a; LAST keeps only positions < keep, as exact digits
     template <bool LAST>
-    static GL_HD void inv_a(const StridedGeom& g, u64 t, int it, u64* buf, const u64* sm,
-                            u64 keep) {
+    static GL_HD void inv_a(const StridedGeom& g, const TilePos& tp, int it, u64* buf,
+                            const u64* sm, u64 keep) {
         int j0 = it / C, c = it % C;
         u64 v[RB];
 #pragma unroll
@@ -150,9 +155,9 @@ struct Strided {
         gl::dft<RB, true>(v);
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {
-            u64 jl;
-            u64 p = pos(g, t, c, j0 + RA * j1, &jl);
-            if (!LAST || p < keep) buf[p] = v[j1];
+            u64 p = tp.base + c + g.S * (u64)(j0 + RA * j1);
+            if (!LAST) buf[p] = v[j1];
+            else if (p < keep) buf[p] = gl::canon(v[j1]);  // p stands for 0 inside the field
         }
     }
 };
@@ -268,7 +273,7 @@ GL_HD void c_inv_col_a(int t, const u64* sm, u64* dst, u64 base, u64 keep) {
 #pragma unroll
     for (int j1 = 0; j1 < 8; j1++) {
         int off = (ln.u + 8 * j1) * 64 + ln.idx;
-        if (base + off < keep) dst[off] = v[j1];
+        if (base + off < keep) dst[off] = gl::canon(v[j1]);
     }
 }
 

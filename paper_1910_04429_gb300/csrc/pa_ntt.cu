@@ -5,29 +5,43 @@
 
 namespace pa {
 
-// Strided pass over both operands (blockIdx.y selects x or a).
+// Strided pass over one tile of both operands: the twiddles computed for x
+// are kept in registers and reused for a.
 template <int RA, int RB, bool PACK>
-__global__ void __launch_bounds__(NT) k_fwd_strided(StridedGeom g, u64* buf0, u64* buf1,
+__global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, u64* buf0, u64* buf1,
                                                     Digits d0, Digits d1, Twiddles tw) {
     using S = Strided<RA, RB>;
     __shared__ u64 sm[TILE];
-    u64* buf = blockIdx.y ? buf1 : buf0;
-    const Digits& d = blockIdx.y ? d1 : d0;
-    u64 t = blockIdx.x;
-    for (int it = threadIdx.x; it < RA * S::C; it += NT) S::template fwd_a<PACK>(g, t, it, buf, d, sm);
-    __syncthreads();
-    for (int it = threadIdx.x; it < RB * S::C; it += NT) S::fwd_b(g, t, it, buf, sm, tw);
+    TilePos tp = S::tile(g, blockIdx.x);
+    u64 w[S::ITEMS_B][RA];
+#pragma unroll
+    for (int i = 0; i < S::ITEMS_B; i++) S::twiddles(g, tp, threadIdx.x + i * NT, tw, w[i]);
+#pragma unroll
+    for (int op = 0; op < 2; op++) {
+        u64* buf = op ? buf1 : buf0;
+        const Digits& d = op ? d1 : d0;
+        if (op) __syncthreads();  // the tile of x is out of shared memory
+#pragma unroll
+        for (int i = 0; i < S::ITEMS_A; i++)
+            S::template fwd_a<PACK>(g, tp, threadIdx.x + i * NT, buf, d, sm);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < S::ITEMS_B; i++) S::fwd_b(g, tp, threadIdx.x + i * NT, buf, sm, w[i]);
+    }
 }
 
 template <int RA, int RB, bool LAST>
-__global__ void __launch_bounds__(NT) k_inv_strided(StridedGeom g, u64* buf, u64 keep,
+__global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, u64* buf, u64 keep,
                                                     Twiddles tw) {
     using S = Strided<RA, RB>;
     __shared__ u64 sm[TILE];
-    u64 t = blockIdx.x;
-    for (int it = threadIdx.x; it < RB * S::C; it += NT) S::inv_b(g, t, it, buf, sm, tw);
+    TilePos tp = S::tile(g, blockIdx.x);
+#pragma unroll
+    for (int i = 0; i < S::ITEMS_B; i++) S::inv_b(g, tp, threadIdx.x + i * NT, buf, sm, tw);
     __syncthreads();
-    for (int it = threadIdx.x; it < RA * S::C; it += NT) S::template inv_a<LAST>(g, t, it, buf, sm, keep);
+#pragma unroll
+    for (int i = 0; i < S::ITEMS_A; i++)
+        S::template inv_a<LAST>(g, tp, threadIdx.x + i * NT, buf, sm, keep);
 }
 
 // Forward contiguous pass of one tile; leaves the spectrum in registers.
@@ -99,7 +113,7 @@ __global__ void __launch_bounds__(NT) k_contig_fused(u64* buf, Digits d, const u
 // ---------------------------------------------------------------------------
 template <int RA, int RB>
 static void fwd_pass(const StridedGeom& g, bool pack, const NttJob& j, cudaStream_t st) {
-    dim3 grid((unsigned)(g.N / TILE), 2);
+    unsigned grid = (unsigned)(g.N / TILE);
     if (pack)
         k_fwd_strided<RA, RB, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
     else
@@ -137,10 +151,17 @@ static void dispatch_inv(int R, const StridedGeom& g, bool last, const NttJob& j
     }
 }
 
+static StridedGeom strided_geom(const Geom& G, int p) {
+    u64 C = TILE / G.pass[p].R;
+    int log_tpb = 0;
+    while ((C << log_tpb) < G.pass[p].S) log_tpb++;
+    return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, log_tpb};
+}
+
 cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
     const Geom& G = j.geom;
     for (int p = 0; p < G.nstrided; p++) {
-        StridedGeom g{G.N, G.pass[p].M, G.pass[p].S};
+        StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
         dispatch_fwd(G.pass[p].R, g, p == 0, j, st);
         prof_end(st);
@@ -162,7 +183,7 @@ cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
         k_contig_fused<false><<<tiles, NT, 0, st>>>(j.buf_x, j.dx, j.ahat, keep, j.tw);
     prof_end(st);
     for (int p = G.nstrided - 1; p >= 0; p--) {
-        StridedGeom g{G.N, G.pass[p].M, G.pass[p].S};
+        StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
         dispatch_inv(G.pass[p].R, g, p == 0, j, st);
         prof_end(st);
