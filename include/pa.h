@@ -125,9 +125,10 @@ typedef struct {
 int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream);
 
 /*
- * pa_prepare: build the twiddle tables for transforms that serve keys of up
- * to n bits on the current device (synchronous). Optional: pa_hash does this
- * lazily. Call it before capturing a stream into a CUDA graph.
+ * pa_prepare: build the twiddle tables of the transform that serves keys of
+ * n bits on the current device (synchronous). Optional: pa_hash does this
+ * lazily. Call it for every key size before capturing a stream into a CUDA
+ * graph.
  */
 int pa_prepare(uint64_t n);
 

@@ -176,14 +176,14 @@ GL_HD u64 shl_v(u64 x, int s) {
 }
 
 // Shift for w^e where w = 2^(192/R) is the R-th root of unity used by every
-// radix-R DFT here (R | 64); INV selects w^-e.
+// radix-R DFT here (R | 192; 2 has order 192 mod p); INV selects w^-e.
 template <int R, bool INV>
 GL_HD int root_shift(int e) {
     int s = ((192 / R) * e) % 192;
     return INV ? (192 - s) % 192 : s;
 }
 
-// In-register DFT of length R in {1, 2, 4, 8}, natural order in and out:
+// In-register DFT of length R in {1, 2, 3, 4, 6, 8}, natural order in and out:
 // v[k] <- sum_j v[j] w^(jk), w = 2^(192/R) (or its inverse), no 1/R scaling.
 template <int R, bool INV>
 GL_HD void dft(u64* v) {
@@ -202,6 +202,29 @@ GL_HD void dft(u64* v) {
         v[2] = sub(a, c);
         v[1] = add(b, d);
         v[3] = sub(b, d);
+    } else if constexpr (R == 3) {
+        // w = 2^64 (forward), w^2 = -1 - w:
+        // X0 = a + b + c, X1 = (a - c) + w (b - c), X2 = (a - b) - w (b - c)
+        u64 a = v[0], b = v[1], c = v[2];
+        u64 t = shl_v(sub(b, c), root_shift<3, INV>(1));
+        v[0] = add(add(a, b), c);
+        v[1] = add(sub(a, c), t);
+        v[2] = sub(sub(a, b), t);
+    } else if constexpr (R == 6) {
+        // X[2k] = DFT3(v_i + v_{i+3}), X[2k+1] = DFT3((v_i - v_{i+3}) w^i), w = 2^32
+        u64 s[3], t[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            s[i] = add(v[i], v[i + 3]);
+            t[i] = shl_v(sub(v[i], v[i + 3]), root_shift<6, INV>(i));
+        }
+        dft<3, INV>(s);
+        dft<3, INV>(t);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            v[2 * k] = s[k];
+            v[2 * k + 1] = t[k];
+        }
     } else if constexpr (R == 8) {
         // one radix-2 decimation-in-frequency step, then two length-4 DFTs:
         // X[2k] = DFT4(v_i + v_{i+4}), X[2k+1] = DFT4((v_i - v_{i+4}) w^i)

@@ -63,7 +63,7 @@ GL_HD u64 digit_at(const Digits& d, u64 pos) {
 }
 
 // ---------------------------------------------------------------------------
-// strided pass, radix R = RA * RB, tile = R rows x C columns
+// strided pass, radix R = RA * RB in {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}
 // ---------------------------------------------------------------------------
 struct StridedGeom {
     u64 N, M, S;    // transform length, sub-problem size, stride (= M / R)
@@ -76,12 +76,16 @@ struct TilePos {
     u64 jl0;   // first column of the tile within its sub-problem
 };
 
-template <int RA, int RB>
+// Tile of a radix-R pass: R rows (digits) x C consecutive columns, R * C <= 4096.
+template <int RA, int RB, int CC>
 struct Strided {
     static constexpr int R = RA * RB;
-    static constexpr int C = TILE / R;
-    static constexpr int ITEMS_A = TILE / RB / NT;  // phase-A items per thread
-    static constexpr int ITEMS_B = TILE / RA / NT;  // phase-B items per thread
+    static constexpr int C = CC;
+    static constexpr int NA = RA * C;                   // phase-A items (RB words each)
+    static constexpr int NB = RB * C;                   // phase-B items (RA words each)
+    static constexpr int ITEMS_A = (NA + NT - 1) / NT;  // per thread
+    static constexpr int ITEMS_B = (NB + NT - 1) / NT;
+    static_assert(R * C <= TILE, "tile larger than shared memory");
 
     static GL_HD TilePos tile(const StridedGeom& g, u64 t) {
         u64 b = t >> g.log_tpb, cg = t & ((1ull << g.log_tpb) - 1);

@@ -29,7 +29,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 struct Device {
     cudaMemPool_t pool = nullptr;
-    std::unordered_map<int, u64*> tables;  // logN -> device twiddle tables
+    std::unordered_map<u64, u64*> tables;  // transform length N -> device twiddle tables
 };
 
 std::mutex g_mu;
@@ -57,22 +57,22 @@ int get_pool(int dev, cudaMemPool_t* out) {
     return PA_OK;
 }
 
-int get_tables(int dev, int logN, Twiddles* tw) {
+int get_tables(int dev, const Geom& G, Twiddles* tw) {
     Device& d = g_dev[dev];
-    auto it = d.tables.find(logN);
+    auto it = d.tables.find(G.N);
     u64* p = nullptr;
     if (it == d.tables.end()) {
         std::vector<u64> host;
-        make_tables(logN, host);
+        make_tables(G.logN, host, G.three);
         cudaError_t e = cudaMalloc(&p, host.size() * sizeof(u64));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(twiddles)");
         e = cudaMemcpy(p, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaFree(p); return cuda_fail(e, "cudaMemcpy(twiddles)"); }
-        d.tables[logN] = p;
+        d.tables[G.N] = p;
     } else {
         p = it->second;
     }
-    u64 nh = (1ull << logN) >> 12;
+    u64 nh = G.N >> 12;
     tw->w4096 = p;
     tw->w4096i = p + 4096;
     tw->wlo = p + 8192;
@@ -100,7 +100,7 @@ struct Scratch {
 
 bool check_sizes(uint64_t n, uint64_t m) { return n >= 1 && m >= 1 && m <= n && n <= PA_MAX_BITS; }
 
-int logn_for_bits(uint64_t n) { return logn_for_digits((n + 15) / 16); }
+Geom geom_for_bits(uint64_t n) { return choose_geom((n + 15) / 16); }
 
 uint16_t top_digit_mask(uint64_t n) {
     return (n & 15) ? (uint16_t)((1u << (n & 15)) - 1) : (uint16_t)0xFFFF;
@@ -110,11 +110,10 @@ uint16_t top_digit_mask(uint64_t n) {
 int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, cudaStream_t st,
                       Scratch& scr, int dev, u64** coef) {
     u64 L = (n + 15) / 16;
-    int logN = logn_for_bits(n);
     NttJob j;
-    j.geom = make_geom(logN);
+    j.geom = geom_for_bits(n);
     j.L = L;
-    int rc = get_tables(dev, logN, &j.tw);
+    int rc = get_tables(dev, j.geom, &j.tw);
     if (rc) return rc;
     void *bx, *ba;
     if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
@@ -337,12 +336,12 @@ int pa_prepare(uint64_t n) {
     int rc = setup(&dev, &pool);
     if (rc) return rc;
     Twiddles tw;
-    return get_tables(dev, logn_for_bits(n), &tw);
+    return get_tables(dev, geom_for_bits(n), &tw);
 }
 
 uint64_t pa_workspace_bytes(uint64_t n) {
     if (n < 1 || n > PA_MAX_BITS) return 0;
-    uint64_t N = 1ull << logn_for_bits(n);
+    uint64_t N = geom_for_bits(n).N;
     return 2 * N * sizeof(u64) + 2 * carry_tiles(n);
 }
 

@@ -7,41 +7,54 @@ namespace pa {
 
 // Strided pass over one tile of both operands: the twiddles computed for x
 // are kept in registers and reused for a.
-template <int RA, int RB, bool PACK>
+template <int RA, int RB, int C, bool PACK>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, u64* buf0, u64* buf1,
-                                                    Digits d0, Digits d1, Twiddles tw) {
-    using S = Strided<RA, RB>;
+                                                       Digits d0, Digits d1, Twiddles tw) {
+    using S = Strided<RA, RB, C>;
     __shared__ u64 sm[TILE];
     TilePos tp = S::tile(g, blockIdx.x);
     u64 w[S::ITEMS_B][RA];
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_B; i++) S::twiddles(g, tp, threadIdx.x + i * NT, tw, w[i]);
+    for (int i = 0; i < S::ITEMS_B; i++) {
+        int it = threadIdx.x + i * NT;
+        if (S::NB % NT == 0 || it < S::NB) S::twiddles(g, tp, it, tw, w[i]);
+    }
 #pragma unroll
     for (int op = 0; op < 2; op++) {
         u64* buf = op ? buf1 : buf0;
         const Digits& d = op ? d1 : d0;
         if (op) __syncthreads();  // the tile of x is out of shared memory
 #pragma unroll
-        for (int i = 0; i < S::ITEMS_A; i++)
-            S::template fwd_a<PACK>(g, tp, threadIdx.x + i * NT, buf, d, sm);
+        for (int i = 0; i < S::ITEMS_A; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NA % NT == 0 || it < S::NA) S::template fwd_a<PACK>(g, tp, it, buf, d, sm);
+        }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < S::ITEMS_B; i++) S::fwd_b(g, tp, threadIdx.x + i * NT, buf, sm, w[i]);
+        for (int i = 0; i < S::ITEMS_B; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NB % NT == 0 || it < S::NB) S::fwd_b(g, tp, it, buf, sm, w[i]);
+        }
     }
 }
 
-template <int RA, int RB, bool LAST>
+template <int RA, int RB, int C, bool LAST>
 __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, u64* buf, u64 keep,
-                                                    Twiddles tw) {
-    using S = Strided<RA, RB>;
+                                                       Twiddles tw) {
+    using S = Strided<RA, RB, C>;
     __shared__ u64 sm[TILE];
     TilePos tp = S::tile(g, blockIdx.x);
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_B; i++) S::inv_b(g, tp, threadIdx.x + i * NT, buf, sm, tw);
+    for (int i = 0; i < S::ITEMS_B; i++) {
+        int it = threadIdx.x + i * NT;
+        if (S::NB % NT == 0 || it < S::NB) S::inv_b(g, tp, it, buf, sm, tw);
+    }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_A; i++)
-        S::template inv_a<LAST>(g, tp, threadIdx.x + i * NT, buf, sm, keep);
+    for (int i = 0; i < S::ITEMS_A; i++) {
+        int it = threadIdx.x + i * NT;
+        if (S::NA % NT == 0 || it < S::NA) S::template inv_a<LAST>(g, tp, it, buf, sm, keep);
+    }
 }
 
 // Forward contiguous pass of one tile; leaves the spectrum in registers.
@@ -111,48 +124,51 @@ __global__ void __launch_bounds__(NT) k_contig_fused(u64* buf, Digits d, const u
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-template <int RA, int RB>
+template <int RA, int RB, int C>
 static void fwd_pass(const StridedGeom& g, bool pack, const NttJob& j, cudaStream_t st) {
-    unsigned grid = (unsigned)(g.N / TILE);
+    unsigned grid = (unsigned)(g.N / (RA * RB * C));
     if (pack)
-        k_fwd_strided<RA, RB, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
+        k_fwd_strided<RA, RB, C, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
     else
-        k_fwd_strided<RA, RB, false><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
+        k_fwd_strided<RA, RB, C, false><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
 }
 
-template <int RA, int RB>
+template <int RA, int RB, int C>
 static void inv_pass(const StridedGeom& g, bool last, const NttJob& j, cudaStream_t st) {
-    unsigned grid = (unsigned)(g.N / TILE);
+    unsigned grid = (unsigned)(g.N / (RA * RB * C));
     if (last)
-        k_inv_strided<RA, RB, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.L, j.tw);
+        k_inv_strided<RA, RB, C, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.L, j.tw);
     else
-        k_inv_strided<RA, RB, false><<<grid, NT, 0, st>>>(g, j.buf_x, j.L, j.tw);
+        k_inv_strided<RA, RB, C, false><<<grid, NT, 0, st>>>(g, j.buf_x, j.L, j.tw);
+}
+
+// radix -> (RA, RB, columns per tile)
+#define PA_RADIX_TABLE(X)                                                                  \
+    X(2, 1, 2, 2048) X(4, 2, 2, 1024) X(8, 2, 4, 512) X(16, 4, 4, 256) X(32, 4, 8, 128)     \
+    X(64, 8, 8, 64) X(3, 3, 1, 1024) X(6, 3, 2, 512) X(12, 3, 4, 256) X(24, 3, 8, 128)      \
+    X(48, 6, 8, 64)
+
+int strided_columns(int R) {
+#define PA_COLS(r, a, b, c) if (R == r) return c;
+    PA_RADIX_TABLE(PA_COLS)
+#undef PA_COLS
+    return 0;
 }
 
 static void dispatch_fwd(int R, const StridedGeom& g, bool pack, const NttJob& j, cudaStream_t st) {
-    switch (R) {
-        case 2: fwd_pass<1, 2>(g, pack, j, st); break;
-        case 4: fwd_pass<2, 2>(g, pack, j, st); break;
-        case 8: fwd_pass<2, 4>(g, pack, j, st); break;
-        case 16: fwd_pass<4, 4>(g, pack, j, st); break;
-        case 32: fwd_pass<4, 8>(g, pack, j, st); break;
-        default: fwd_pass<8, 8>(g, pack, j, st); break;
-    }
+#define PA_FWD(r, a, b, c) if (R == r) return fwd_pass<a, b, c>(g, pack, j, st);
+    PA_RADIX_TABLE(PA_FWD)
+#undef PA_FWD
 }
 
 static void dispatch_inv(int R, const StridedGeom& g, bool last, const NttJob& j, cudaStream_t st) {
-    switch (R) {
-        case 2: inv_pass<1, 2>(g, last, j, st); break;
-        case 4: inv_pass<2, 2>(g, last, j, st); break;
-        case 8: inv_pass<2, 4>(g, last, j, st); break;
-        case 16: inv_pass<4, 4>(g, last, j, st); break;
-        case 32: inv_pass<4, 8>(g, last, j, st); break;
-        default: inv_pass<8, 8>(g, last, j, st); break;
-    }
+#define PA_INV(r, a, b, c) if (R == r) return inv_pass<a, b, c>(g, last, j, st);
+    PA_RADIX_TABLE(PA_INV)
+#undef PA_INV
 }
 
 static StridedGeom strided_geom(const Geom& G, int p) {
-    u64 C = TILE / G.pass[p].R;
+    u64 C = (u64)strided_columns(G.pass[p].R);
     int log_tpb = 0;
     while ((C << log_tpb) < G.pass[p].S) log_tpb++;
     return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, log_tpb};
@@ -168,7 +184,7 @@ cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
     }
     unsigned tiles = (unsigned)(G.N / TILE);
     bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
-    u64 ninv = n_inverse(G.logN);
+    u64 ninv = n_inverse(G.logN, G.three);
     u64 keep = pack ? j.L : G.N;
     prof_begin(st, "ntt_contig_seed");
     if (pack)

@@ -18,24 +18,28 @@ struct PassDesc {
 };
 
 struct Geom {
-    int logN = 0;
+    int logN = 0;    // log2 of the power-of-two part of N
+    int three = 0;   // 1: N = 3 * 2^logN, 0: N = 2^logN
     uint64_t N = 0;
     int nstrided = 0;
     PassDesc pass[8];
 };
 
-// N = 2^logN (logN >= 12) = R_0 * 64^q * 4096: one strided pass of radix
-// 2^((logN-12) mod 6) if that is > 1, then q strided passes of radix 64, then
-// the contiguous 4096-element pass.
-inline Geom make_geom(int logN) {
+// N = R_0 * 64^q * 4096 with N = 2^logN (R_0 = 2^((logN-12) mod 6), omitted when
+// 1) or N = 3 * 2^logN (R_0 = 3 * 2^((logN-12) mod 6), which must be <= 48):
+// one strided pass of radix R_0, then q strided passes of radix 64, then the
+// contiguous 4096-element pass.
+inline Geom make_geom(int logN, int three = 0) {
     Geom g;
     g.logN = logN;
-    g.N = 1ull << logN;
+    g.three = three;
+    g.N = (three ? 3ull : 1ull) << logN;
     int rem = (logN - LOG_TILE) % 6, q = (logN - LOG_TILE) / 6;
     uint64_t M = g.N;
-    if (rem) {
-        g.pass[g.nstrided++] = PassDesc{1 << rem, M, M >> rem};
-        M >>= rem;
+    int R0 = (three ? 3 : 1) << rem;
+    if (R0 > 1) {
+        g.pass[g.nstrided++] = PassDesc{R0, M, M / R0};
+        M /= R0;
     }
     for (int i = 0; i < q; i++) {
         g.pass[g.nstrided++] = PassDesc{64, M, M >> 6};
@@ -54,36 +58,53 @@ inline int logn_for_digits(uint64_t L) {
     return k;
 }
 
-// A primitive 2^32-th root of unity r with r^(2^26) = 8, so that every
-// w_N = r^(2^32 / N) satisfies w_N^(N/64) = 8 = 2^3 and all length-64 DFT roots
-// are powers of two. 7 generates GF(p)^*.
-inline uint64_t root_2_32() {
+// The shortest transform, 2^k or 3 * 2^k (with a first radix of at most 48),
+// that holds the linear convolution of two L-digit operands.
+inline Geom choose_geom(uint64_t L) {
+    uint64_t need = 2 * L - 1;
+    int k = logn_for_digits(L);
+    for (int j = LOG_TILE; j < k; j++) {
+        bool fits = (3ull << j) >= need && (3ull << j) < (1ull << k);
+        if (fits && (j - LOG_TILE) % 6 <= 4) return make_geom(j, 1);
+    }
+    return make_geom(k, 0);
+}
+
+// A primitive (3 * 2^32)-th root of unity R with R^(2^26) = 2: every
+// w_N = R^(3 * 2^32 / N) then satisfies w_N^(N/192) = 2 when 192 | N and
+// w_N^(N/64) = 8 when 64 | N, so all DFTs of length dividing 192 inside a
+// transform have power-of-two roots. 7 generates GF(p)^*, and 2 has order 192.
+inline uint64_t root_3_2_32() {
     const uint64_t p1 = gl::P - 1;
-    uint64_t r0 = gl::pow(7, p1 >> 32);
-    uint64_t c = gl::pow(r0, 1ull << 26);  // a primitive 64-th root: 8^u for an odd u
+    uint64_t r0 = gl::pow(7, p1 / (3ull << 32));  // order 3 * 2^32
+    uint64_t c = gl::pow(r0, 1ull << 26);         // order 192: c = 2^u, gcd(u, 192) = 1
     int u = -1;
     uint64_t e = 1;
-    for (int i = 0; i < 64; i++) {
+    for (int i = 0; i < 192; i++) {
         if (e == c) { u = i; break; }
-        e = gl::mul(e, 8);
+        e = gl::mul(e, 2);
     }
     if (u < 0) return 0;
     int v = 1;
-    while ((u * v) % 64 != 1) v += 2;  // v = u^-1 mod 64
+    while ((u * v) % 192 != 1) v++;               // v = u^-1 mod 192
     return gl::pow(r0, (uint64_t)v);
 }
 
-inline uint64_t omega(int logN) { return gl::pow(root_2_32(), 1ull << (32 - logN)); }
+// primitive N-th root for N = 2^logN (three = 0) or 3 * 2^logN (three = 1)
+inline uint64_t omega(int logN, int three = 0) {
+    return gl::pow(root_3_2_32(), (three ? 1ull : 3ull) << (32 - logN));
+}
 
 // Table layout: w4096 | w4096^-1 | wlo | wlo^-1 | whi | whi^-1
-inline size_t table_words(int logN) { return 4 * 4096 + 2 * ((1ull << logN) >> 12); }
+inline size_t table_words_n(uint64_t N) { return 4 * 4096 + 2 * (N >> 12); }
+inline size_t table_words(int logN) { return table_words_n(1ull << logN); }
 
-inline void make_tables(int logN, std::vector<uint64_t>& t) {
-    uint64_t N = 1ull << logN;
-    uint64_t w = omega(logN), wi = gl::pow(w, gl::P - 2);
+inline void make_tables(int logN, std::vector<uint64_t>& t, int three = 0) {
+    uint64_t N = (three ? 3ull : 1ull) << logN;
+    uint64_t w = omega(logN, three), wi = gl::pow(w, gl::P - 2);
     uint64_t w4 = gl::pow(w, N >> 12), w4i = gl::pow(wi, N >> 12);
     uint64_t nh = N >> 12;
-    t.assign(table_words(logN), 0);
+    t.assign(table_words_n(N), 0);
     uint64_t* w4096 = t.data();
     uint64_t* w4096i = w4096 + 4096;
     uint64_t* wlo = w4096i + 4096;
@@ -105,6 +126,8 @@ inline void make_tables(int logN, std::vector<uint64_t>& t) {
     }
 }
 
-inline uint64_t n_inverse(int logN) { return gl::P - ((gl::P - 1) >> logN); }
+inline uint64_t n_inverse(int logN, int three = 0) {
+    return gl::pow((three ? 3ull : 1ull) << logN, gl::P - 2);
+}
 
 }  // namespace pa

@@ -104,10 +104,12 @@ def test_argument_checks_without_gpu():
     assert lib.pa_hash_noalloc(p, p, p, 10, 11, p, null) == binding.PA_EINVAL
 
 
-@pytest.mark.parametrize("n,N", [(1, 4096), (32768, 4096), (32769, 8192), (1_000_000, 1 << 17),
-                                 (100_000_000, 1 << 24), (1_000_000_000, 1 << 27)])
+@pytest.mark.parametrize("n,N", [(1, 4096), (32768, 4096), (32769, 8192), (96_000, 3 << 12),
+                                 (1_000_000, 1 << 17), (1_536_000, 3 << 16),
+                                 (100_000_000, 3 << 22), (1_000_000_000, 1 << 27)])
 def test_workspace_bytes(n, N):
-    """Transform length N = smallest power of two >= max(4096, 2 ceil(n/16) - 1)."""
+    """Transform length N = smallest 2^k or 3 * 2^k (first radix <= 48) that is
+    >= max(4096, 2 ceil(n/16) - 1)."""
     tiles = -(-(-(-n // 64)) // 1024)
     assert binding.workspace_bytes(n) == 2 * N * 8 + 2 * tiles
     assert binding.workspace_bytes(0) == 0

@@ -39,11 +39,14 @@ def _check_block(blk, threads=None):
     assert bad.size == 0, f"n={blk.n} m={blk.m}: {bad.size} limbs differ, first at {bad[:5]}"
 
 
-# sizes spanning every pass layout (transform lengths 2^12 .. 2^21), ragged
+# sizes spanning every pass layout (transform lengths 2^12 .. 2^24 and 3 * 2^12 ..
+# 3 * 2^18), ragged
 # digit and limb tails, and the single-tile / multi-tile boundary
 SIZES = [1, 2, 3, 15, 16, 17, 63, 64, 65, 100, 127, 128, 129, 1000, 4095, 4097,
          32767, 32768, 32769, 65536 + 5, 100_003, 131_072, 262_144 + 1, 524_287,
-         1_000_000, 2_097_152 + 16, 4_194_304 + 33, 8_388_609, 16_777_000]
+         1_000_000, 2_097_152 + 16, 4_194_304 + 33, 8_388_609, 16_777_000,
+         # transform lengths 3 * 2^k (first radix 3, 6, 12, 24, 48)
+         96_000 - 5, 192_000 + 3, 384_000, 768_000 - 1, 1_536_000 + 7, 4_800_000]
 
 
 @pytest.mark.parametrize("n", SIZES)
