@@ -40,6 +40,29 @@ ROTATE = 4                      # distinct input blocks: 4 x 37.5 MB > L2
 PAPER_I9_N1E8_MBPS = 140.96     # Table 2, i9-9900k, 100M-bit block (other hardware)
 
 
+def rank_seeds(rank: int) -> list[int]:
+    """Seeds of the blocks one rank hashes: ranks own disjoint blocks (replicas,
+    no data exchange between ranks)."""
+    return [1 + rank * ROTATE + i for i in range(ROTATE)]
+
+
+def aggregate_mbps(world: int, steps: int, n: int, ms_max: float) -> float:
+    """Whole-job key throughput: every rank hashed `steps` blocks of n bits in at
+    most ms_max milliseconds (the slowest rank's time)."""
+    return world * steps * n / (ms_max / 1e3) / 1e6
+
+
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise max of per-rank timings (a collective on timings only)."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -48,6 +71,13 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=N_BITS)
     p.add_argument("--m", type=int, default=M_BITS)
+    p.add_argument("--workload", choices=["single", "batched", "served"], default="single",
+                   help="single: one 10^8-bit block per step (default); batched: 256 blocks of "
+                        "10^6..10^7 bits per pa_hash_batched call; served: Poisson arrivals "
+                        "through pa_submit/pa_poll")
+    p.add_argument("--blocks", type=int, default=256)
+    p.add_argument("--rate", type=float, default=200.0)
+    p.add_argument("--duration", type=float, default=60.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     return p.parse_args()
@@ -160,7 +190,7 @@ def run_ours(args, rank, world, local):
     n, m = args.n, args.m
     L = (n + 63) // 64
     Mo = (m + 63) // 64
-    blocks = [inputs.make_block(n, m, seed=1 + rank * ROTATE + i) for i in range(ROTATE)]
+    blocks = [inputs.make_block(n, m, seed=s) for s in rank_seeds(rank)]
 
     def to_dev(a):
         return torch.from_numpy(a.view(np.int64)).to(dev)
@@ -245,13 +275,136 @@ def run_ours(args, rank, world, local):
     if not ok:
         raise RuntimeError("host-buffer results differ from device-buffer results")
 
-    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total, e2e_ms = float(t[0]), float(t[1])
+    ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], world, dev)
     return dict(ms_total=ms_total, e2e_ms=e2e_ms, kstats=kstats, clocks=clk,
                 h2d=3 * L * 8, d2h=Mo * 8)
+
+
+def run_batched(args):
+    """256 independent blocks, n = floor(exp(U(ln 1e6, ln 1e7))), m = floor(n r),
+    r ~ U(0.1, 0.5): one pa_hash_batched per step, against the same blocks as
+    plain single-block pa_hash calls on one stream."""
+    import torch
+
+    from paper_1910_04429_gb300 import binding
+
+    binding.load()
+    blks = inputs.make_batch(args.blocks, 1_000_000, 10_000_000, seed=1)
+    d = [tuple(torch.from_numpy(v.view(np.int64)).cuda() for v in (b.x, b.a, b.b)) for b in blks]
+    outs = [torch.empty((b.m + 63) // 64, dtype=torch.int64, device="cuda") for b in blks]
+    for b in blks:
+        binding.prepare(b.n)
+    spec = [(x, a, bb, b.n, b.m, o) for (x, a, bb), b, o in zip(d, blks, outs)]
+    bits = sum(b.n for b in blks)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def batched():
+        binding.hash_batched(spec)
+
+    def plain():
+        for x, a, bb, n, m, o in spec:
+            binding.hash(x, a, bb, n, m, out=o)
+
+    steps = max(3, min(args.steps, 20))
+    ms_b = timed(batched, steps)
+    ref = [o.clone() for o in outs]
+    ms_p = timed(plain, steps)
+    same = all(torch.equal(r, o) for r, o in zip(ref, outs))
+    return {"metric": "PA input throughput (Mbps of key bits), batched blocks", "unit": UNIT,
+            "workload": f"{len(blks)} blocks, n log-uniform in [1e6, 1e7] (sum {bits} bits), "
+                        f"m = floor(n r), r ~ U(0.1, 0.5), seeds 1..{len(blks)}",
+            "batched": {"value": round(bits / ms_b / 1e3, 1), "ms_per_batch": round(ms_b, 3)},
+            "plain_single_launches": {"value": round(bits / ms_p / 1e3, 1),
+                                      "ms_per_batch": round(ms_p, 3)},
+            "results_identical": same, "steps": steps}
+
+
+def run_served(args):
+    """Poisson arrivals through pa_submit; keys are prefixes of one resident
+    10^8-bit pool (the bits do not affect the work), outputs rotate over a ring."""
+    import threading as th
+
+    import torch
+
+    from paper_1910_04429_gb300 import binding
+
+    binding.load()
+    pool = inputs.make_block(100_000_000, 1, seed=1)
+    px, pa_, pb = (torch.from_numpy(v.view(np.int64)).cuda() for v in (pool.x, pool.a, pool.b))
+    arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=7)
+    sizes = inputs.batch_sizes(len(arrivals), 1_000_000, 100_000_000, seed=11)
+    ring = 512
+    outs = [torch.empty((50_000_000 + 63) // 64, dtype=torch.int64, device="cuda") for _ in range(ring)]
+    # footprint alone of the largest block sets no extra limit; default budget
+    binding.serve_stop()
+    binding.serve_init(max_batch=32, streams=3)
+    for n, _ in sizes[:64]:
+        binding.prepare(n)
+    tickets = []
+    polled = [0]
+    done_evt = th.Event()
+
+    def poller():
+        i = 0
+        while i < len(arrivals):
+            if i >= len(tickets):
+                time.sleep(0.0005)
+                continue
+            rc, st = binding.poll(tickets[i], 1_000_000)
+            if rc == binding.PA_OK:
+                if st != binding.PA_OK:
+                    raise RuntimeError(f"served block failed: {st}")
+                i += 1
+                polled[0] = i
+        done_evt.set()
+
+    t_poll = th.Thread(target=poller, daemon=True)
+    t_poll.start()
+    t0 = time.perf_counter()
+    for i, (t_arr, (n, m)) in enumerate(zip(arrivals, sizes)):
+        while i - polled[0] >= ring - 1:   # keep the output ring from wrapping
+            time.sleep(0.0002)
+        delay = t0 + t_arr - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(binding.submit(px, pa_, pb, n, m, outs[i % ring]))
+    done_evt.wait(timeout=600)
+    wall = time.perf_counter() - t0
+    st = binding.serve_stats()
+    binding.serve_stop()
+    bits = sum(n for n, _ in sizes)
+    # latency of the same sizes hashed alone with plain launches (no queueing)
+    alone = []
+    for n, m in sizes[:50]:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        binding.hash(px, pa_, pb, n, m, out=outs[0])
+        e1.record()
+        torch.cuda.synchronize()
+        alone.append(e0.elapsed_time(e1) * 1e3)
+    alone.sort()
+    return {"metric": "served PA throughput (Mbps of key bits) and latency", "unit": UNIT,
+            "workload": f"Poisson arrivals at {args.rate}/s for {args.duration} s ({len(arrivals)} blocks), "
+                        f"n log-uniform in [1e6, 1e8], r ~ U(0.1, 0.5)",
+            "offered_mbps": round(bits / args.duration / 1e6, 1),
+            "sustained_mbps": round(st["bits"] / wall / 1e6, 1),
+            "p50_latency_us": round(st["p50_us"], 1), "p99_latency_us": round(st["p99_us"], 1),
+            "max_latency_us": round(st["max_us"], 1), "batches": st["batches"],
+            "peak_inflight_blocks": st["peak_inflight_blocks"],
+            "peak_inflight_bytes": st["peak_inflight_bytes"], "hbm_budget_bytes": st["hbm_budget_bytes"],
+            "plain_single_launch_p50_us": round(alone[len(alone) // 2], 1),
+            "plain_single_launch_p99_us": round(alone[min(len(alone) - 1, int(0.99 * len(alone)))], 1)}
 
 
 def cpu_oracle_rate(n_sample: int, reps: int = 1):
@@ -317,12 +470,21 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
 
+    if args.workload != "single":
+        import torch
+
+        torch.cuda.set_device(local)
+        out = run_batched(args) if args.workload == "batched" else run_served(args)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return 0
+
     res = run_ours(args, rank, world, local)
     n, m = args.n, args.m
     K = args.steps
     ms_step = res["ms_total"] / K
-    value = world * K * n / (res["ms_total"] / 1e3) / 1e6
-    e2e_value = world * n / (res["e2e_ms"] / 1e3) / 1e6
+    value = aggregate_mbps(world, K, n, res["ms_total"])
+    e2e_value = aggregate_mbps(world, 1, n, res["e2e_ms"])
     N = 1 << max(12, math.ceil(math.log2(2 * ((n + 15) // 16) - 1)))
 
     roofline = None

@@ -52,8 +52,8 @@ extern "C" {
 #define PA_EINVAL (-1)   /* bad size, null pointer, m > n, or n beyond PA_MAX_BITS */
 #define PA_ENOMEM (-2)   /* device or host allocation failed */
 #define PA_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
-#define PA_EAGAIN (-4)   /* serving: not admitted now / result not ready */
-#define PA_ETIMEOUT (-5) /* serving: a bounded wait expired */
+#define PA_EAGAIN (-4)   /* serving: queue full / result not ready yet */
+#define PA_ETIMEOUT (-5) /* a bounded device wait expired */
 
 /* Largest key length: 2^31 bits (transform length 2^28, two 2 GiB buffers). */
 #define PA_MAX_BITS (1ull << 31)
@@ -123,6 +123,60 @@ typedef struct {
  * work is queued (PA_EINVAL if any is invalid).
  */
 int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: blocks arrive one at a time (as error reconciliation emits them,
+ * Sec. 2.2) and are hashed by a background loop that forms batches
+ * continuously: a request is admitted once a device stream slot is free and
+ * the sum of in-flight footprints (transform workspace + the block's I/O,
+ * pa_workspace_bytes(n) + 8 * (3 ceil(n/64) + ceil(m/64)) bytes) stays within
+ * the HBM budget; admitted batches run concurrently on `streams` device
+ * streams. Requests are taken in arrival order (the head waits for memory
+ * rather than being overtaken). Each result equals pa_hash on that block
+ * alone. The block's buffers must stay valid until its ticket completes.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int device;                /* CUDA device of the serving loop; -1 = the current one */
+    uint32_t max_batch;        /* blocks per device batch (0 = 64) */
+    uint32_t streams;          /* concurrent device batches (0 = 2, at most 8) */
+    uint32_t max_pending;      /* queue length before pa_submit returns PA_EAGAIN (0 = 65536) */
+    uint64_t hbm_budget_bytes; /* admission budget (0 = half of the free device memory) */
+} pa_config;
+
+/*
+ * pa_init: start the serving loop with `cfg` (NULL = defaults on the current
+ * device). Optional: the first pa_submit starts it with defaults. PA_EINVAL if
+ * it is already running (stop it first).
+ */
+int pa_init(const pa_config* cfg);
+
+/*
+ * pa_submit: queue one block (device pointers, as in pa_block) and return its
+ * ticket. Non-blocking. PA_EINVAL for bad sizes or pointers, or if the block's
+ * footprint alone exceeds the budget; PA_EAGAIN if the queue is full.
+ */
+int pa_submit(const pa_block* blk, uint64_t* ticket);
+
+/*
+ * pa_poll: wait up to timeout_us for the ticket. PA_OK when it has completed
+ * (*status = the hashing status, PA_OK on success; the ticket is then
+ * released), PA_EAGAIN if it is still queued or running, PA_EINVAL for an
+ * unknown or already released ticket.
+ */
+int pa_poll(uint64_t ticket, uint32_t timeout_us, int* status);
+
+/* Serving counters since the loop started. Latency = submit to device completion. */
+typedef struct {
+    uint64_t completed, pending, batches, bits;
+    uint64_t peak_inflight_bytes, peak_inflight_blocks, hbm_budget_bytes;
+    double p50_us, p99_us, max_us;
+    double mbps;               /* key bits completed / (last completion - first submit) */
+} pa_serve_stats_t;
+
+int pa_serve_stats(pa_serve_stats_t* out);
+
+/* pa_serve_stop: finish queued and running work, stop the loop, reset the counters. */
+int pa_serve_stop(void);
 
 /*
  * pa_prepare: build the twiddle tables of the transform that serves keys of

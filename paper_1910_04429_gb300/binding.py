@@ -33,6 +33,11 @@ _SIGS = {
     "pa_workspace_bytes": ([ctypes.c_uint64], ctypes.c_uint64),
     "pa_shutdown": ([], ctypes.c_int),
     "pa_profile": ([ctypes.c_int], ctypes.c_int),
+    "pa_init": ([ctypes.c_void_p], ctypes.c_int),
+    "pa_submit": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "pa_poll": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pa_serve_stats": ([ctypes.c_void_p], ctypes.c_int),
+    "pa_serve_stop": ([], ctypes.c_int),
     "pa_profile_collect": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "pa_last_error": ([], ctypes.c_char_p),
     "pa_version": ([], ctypes.c_char_p),
@@ -50,6 +55,23 @@ class PaKernelStat(ctypes.Structure):
     """Mirror of ``pa_kernel_stat`` in include/pa.h."""
 
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
+
+
+class PaConfig(ctypes.Structure):
+    """Mirror of ``pa_config`` in include/pa.h."""
+
+    _fields_ = [("device", ctypes.c_int), ("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32),
+                ("max_pending", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class PaServeStats(ctypes.Structure):
+    """Mirror of ``pa_serve_stats_t`` in include/pa.h."""
+
+    _fields_ = [("completed", ctypes.c_uint64), ("pending", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("bits", ctypes.c_uint64), ("peak_inflight_bytes", ctypes.c_uint64),
+                ("peak_inflight_blocks", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("mbps", ctypes.c_double)]
 
 
 class PaError(RuntimeError):
@@ -184,6 +206,41 @@ def hash_batched(blocks, stream=None):
         arr[i] = PaBlock(_dev_ptr(k, L, "key").value, _dev_ptr(a, L, "seed_a").value,
                          _dev_ptr(b, L, "seed_b").value, n, m, _dev_ptr(o, limbs(m), "out").value)
     _check(load().pa_hash_batched(arr, len(blocks), _stream_ptr(stream)), "pa_hash_batched")
+
+
+def serve_init(device: int = -1, max_batch: int = 0, streams: int = 0, max_pending: int = 0,
+               hbm_budget_bytes: int = 0):
+    cfg = PaConfig(device, max_batch, streams, max_pending, hbm_budget_bytes)
+    _check(load().pa_init(ctypes.byref(cfg)), "pa_init")
+
+
+def submit(key, seed_a, seed_b, n: int, m: int, out) -> int:
+    """Queue one block (CUDA tensors that must stay alive until it completes)."""
+    L = limbs(n)
+    blk = PaBlock(_dev_ptr(key, L, "key").value, _dev_ptr(seed_a, L, "seed_a").value,
+                  _dev_ptr(seed_b, L, "seed_b").value, n, m, _dev_ptr(out, limbs(m), "out").value)
+    t = ctypes.c_uint64(0)
+    rc = load().pa_submit(ctypes.byref(blk), ctypes.byref(t))
+    if rc != PA_OK:
+        raise PaError(rc, f"pa_submit: {load().pa_last_error().decode()}")
+    return int(t.value)
+
+
+def poll(ticket: int, timeout_us: int = 0):
+    """(rc, status): rc PA_OK when done (status = hashing status), PA_EAGAIN if not yet."""
+    st = ctypes.c_int(0)
+    rc = load().pa_poll(ticket, timeout_us, ctypes.byref(st))
+    return rc, st.value
+
+
+def serve_stats() -> dict:
+    s = PaServeStats()
+    _check(load().pa_serve_stats(ctypes.byref(s)), "pa_serve_stats")
+    return {name: getattr(s, name) for name, _ in PaServeStats._fields_}
+
+
+def serve_stop():
+    _check(load().pa_serve_stop(), "pa_serve_stop")
 
 
 def prepare(n: int):

@@ -27,9 +27,13 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA;
 }
 
+constexpr int SIDE_STREAMS = 4;  // concurrent size classes inside one batched call
+
 struct Device {
     cudaMemPool_t pool = nullptr;
     std::unordered_map<u64, u64*> tables;  // transform length N -> device twiddle tables
+    cudaStream_t side[SIDE_STREAMS] = {};  // forked from the caller's stream per batch
+    cudaEvent_t fork = nullptr, join[SIDE_STREAMS] = {};
 };
 
 std::mutex g_mu;
@@ -150,6 +154,87 @@ int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* see
     int rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef);
     if (rc) return rc;
     return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr);
+}
+
+int side_streams(int dev) {
+    Device& d = g_dev[dev];
+    if (d.fork) return PA_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming);
+    for (int i = 0; e == cudaSuccess && i < SIDE_STREAMS; i++) {
+        e = cudaStreamCreateWithFlags(&d.side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        d.fork = nullptr;
+        return cuda_fail(e, "side stream set-up");
+    }
+    return PA_OK;
+}
+
+// Blocks grouped by transform geometry: each group runs its passes as batched
+// launches (blocks along gridDim.y), groups on side streams forked from and
+// joined back into `st`, then one batched carry launch for every block.
+int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, int dev,
+                      cudaMemPool_t pool) {
+    int rc = side_streams(dev);
+    if (rc) return rc;
+    Device& d = g_dev[dev];
+    std::vector<std::pair<u64, std::vector<uint32_t>>> groups;  // N -> block indices
+    for (uint32_t i = 0; i < count; i++) {
+        u64 N = geom_for_bits(blocks[i].n).N;
+        size_t g = 0;
+        while (g < groups.size() && groups[g].first != N) g++;
+        if (g == groups.size()) groups.push_back({N, {}});
+        groups[g].second.push_back(i);
+    }
+    // workspace: all transform buffers, then the carry bytes, in one allocation
+    u64 words = 0, carry_bytes = 0;
+    for (auto& gr : groups) words += 2 * gr.first * gr.second.size();
+    for (uint32_t i = 0; i < count; i++) carry_bytes += 2 * carry_tiles(blocks[i].n);
+    Scratch scr(st, pool);
+    void* ws;
+    if ((rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
+    u64* w = (u64*)ws;
+    uint8_t* cb = (uint8_t*)(w + words);
+    std::vector<CarryJob> cj(count);
+
+    cudaError_t e = cudaEventRecord(d.fork, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(fork)");
+    int used = 0;
+    for (size_t g = 0; g < groups.size(); g++) {
+        const auto& idx = groups[g].second;
+        Geom G = geom_for_bits(blocks[idx[0]].n);
+        Twiddles tw;
+        if ((rc = get_tables(dev, G, &tw))) return rc;
+        std::vector<BlockIO> io(idx.size());
+        for (size_t k = 0; k < idx.size(); k++) {
+            const pa_block& b = blocks[idx[k]];
+            u64 L = (b.n + 15) / 16;
+            uint16_t top = top_digit_mask(b.n);
+            io[k] = BlockIO{w, w + G.N, Digits{(const uint16_t*)b.key, L, top},
+                            Digits{(const uint16_t*)b.seed_a, L, top}, L};
+            u64 t = carry_tiles(b.n);
+            cj[idx[k]] = CarryJob{w, L, b.seed_b, b.n, b.m, b.out, cb, cb + t};
+            cb += 2 * t;
+            w += 2 * G.N;
+        }
+        cudaStream_t s = d.side[g % SIDE_STREAMS];
+        if (g < SIDE_STREAMS) {
+            if ((e = cudaStreamWaitEvent(s, d.fork, 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent(fork)");
+            used++;
+        }
+        if ((e = launch_convolution_batch(G, tw, io.data(), (int)io.size(), s)) != cudaSuccess)
+            return cuda_fail(e, "batched NTT launch");
+    }
+    for (int i = 0; i < used; i++) {
+        if ((e = cudaEventRecord(d.join[i], d.side[i])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, d.join[i], 0)) != cudaSuccess)
+            return cuda_fail(e, "join");
+    }
+    if ((e = launch_carry_batch(cj.data(), (int)count, st)) != cudaSuccess)
+        return cuda_fail(e, "batched carry launch");
+    return PA_OK;
 }
 
 int setup(int* dev, cudaMemPool_t* pool) {
@@ -315,17 +400,13 @@ int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream) {
         if (!check_sizes(b.n, b.m) || !b.key || !b.seed_a || !b.seed_b || !b.out)
             return fail(PA_EINVAL, "pa_hash_batched: invalid block " + std::to_string(i));
     }
+    if (!count) return PA_OK;
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
     cudaMemPool_t pool;
     int rc = setup(&dev, &pool);
     if (rc) return rc;
-    for (uint32_t i = 0; i < count; i++) {
-        const pa_block& b = blocks[i];
-        rc = hash_device(b.key, b.seed_a, b.seed_b, b.n, b.m, b.out, (cudaStream_t)stream, dev, pool);
-        if (rc) return rc;
-    }
-    return PA_OK;
+    return hash_batch_device(blocks, count, (cudaStream_t)stream, dev, pool);
 }
 
 int pa_prepare(uint64_t n) {
@@ -353,6 +434,13 @@ int pa_shutdown(void) {
         cudaSetDevice(kv.first);
         for (auto& t : kv.second.tables) cudaFree(t.second);
         if (kv.second.pool) cudaMemPoolDestroy(kv.second.pool);
+        if (kv.second.fork) {
+            cudaEventDestroy(kv.second.fork);
+            for (int i = 0; i < SIDE_STREAMS; i++) {
+                cudaStreamDestroy(kv.second.side[i]);
+                cudaEventDestroy(kv.second.join[i]);
+            }
+        }
     }
     g_dev.clear();
     if (prev >= 0) cudaSetDevice(prev);

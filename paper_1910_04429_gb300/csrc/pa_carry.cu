@@ -97,7 +97,17 @@ __device__ __forceinline__ int block_exclusive(int v, int* total) {
     return compose(wpre, exc);
 }
 
-__global__ void __launch_bounds__(CARRY_THREADS) k_carry_tiles(CarryJob c, u64 Ly) {
+template <int B>
+struct CarryBatch {
+    int count;
+    CarryJob job[B];
+};
+
+template <int B>
+__global__ void __launch_bounds__(CARRY_THREADS) k_carry_tiles(const __grid_constant__ CarryBatch<B> cb) {
+    const CarryJob& c = cb.job[blockIdx.y];
+    u64 Ly = (c.n + 63) / 64;
+    if (blockIdx.x >= carry_tiles(c.n)) return;
     long long j0 = ((long long)blockIdx.x * CARRY_THREADS + threadIdx.x) * CARRY_LIMBS;
     Limb u[CARRY_LIMBS];
     limbs_u<CARRY_LIMBS>(c, j0, Ly, u);
@@ -110,8 +120,11 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry_tiles(CarryJob c, u64 L
     if (threadIdx.x == 0) c.agg[blockIdx.x] = (uint8_t)total;
 }
 
-// One block: carry into every tile from the tile aggregates.
-__global__ void __launch_bounds__(1024) k_carry_scan(CarryJob c, u64 ntiles) {
+// One CTA per block: carry into every tile from the tile aggregates.
+template <int B>
+__global__ void __launch_bounds__(1024) k_carry_scan(const __grid_constant__ CarryBatch<B> cb) {
+    const CarryJob& c = cb.job[blockIdx.x];
+    u64 ntiles = carry_tiles(c.n);
     __shared__ int part[1024];
     u64 per = (ntiles + 1023) / 1024;
     u64 lo = threadIdx.x * per, hi = lo + per < ntiles ? lo + per : ntiles;
@@ -136,7 +149,11 @@ __global__ void __launch_bounds__(1024) k_carry_scan(CarryJob c, u64 ntiles) {
     }
 }
 
-__global__ void __launch_bounds__(CARRY_THREADS) k_carry_out(CarryJob c, u64 Ly) {
+template <int B>
+__global__ void __launch_bounds__(CARRY_THREADS) k_carry_out(const __grid_constant__ CarryBatch<B> cb) {
+    const CarryJob& c = cb.job[blockIdx.y];
+    u64 Ly = (c.n + 63) / 64;
+    if (blockIdx.x >= carry_tiles(c.n)) return;
     long long j0 = ((long long)blockIdx.x * CARRY_THREADS + threadIdx.x) * CARRY_LIMBS;
     Limb u[CARRY_LIMBS + 1];
     limbs_u<CARRY_LIMBS + 1>(c, j0, Ly, u);
@@ -171,19 +188,42 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry_out(CarryJob c, u64 Ly)
     }
 }
 
-cudaError_t launch_carry(const CarryJob& c, cudaStream_t st) {
-    u64 Ly = (c.n + 63) / 64;
-    u64 tiles = carry_tiles(c.n);
+template <int B>
+static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
+    u64 tiles = 0;
+    for (int i = 0; i < cb.count; i++) {
+        u64 t = carry_tiles(cb.job[i].n);
+        tiles = t > tiles ? t : tiles;
+    }
+    dim3 grid((unsigned)tiles, (unsigned)cb.count);
     prof_begin(st, "carry_tiles");
-    k_carry_tiles<<<(unsigned)tiles, CARRY_THREADS, 0, st>>>(c, Ly);
+    k_carry_tiles<B><<<grid, CARRY_THREADS, 0, st>>>(cb);
     prof_end(st);
     prof_begin(st, "carry_scan");
-    k_carry_scan<<<1, 1024, 0, st>>>(c, tiles);
+    k_carry_scan<B><<<cb.count, 1024, 0, st>>>(cb);
     prof_end(st);
     prof_begin(st, "carry_out");
-    k_carry_out<<<(unsigned)tiles, CARRY_THREADS, 0, st>>>(c, Ly);
+    k_carry_out<B><<<grid, CARRY_THREADS, 0, st>>>(cb);
     prof_end(st);
     return cudaGetLastError();
+}
+
+cudaError_t launch_carry(const CarryJob& c, cudaStream_t st) {
+    CarryBatch<1> cb;
+    cb.count = 1;
+    cb.job[0] = c;
+    return launch_carry_b<1>(cb, st);
+}
+
+cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st) {
+    for (int i = 0; i < count; i += MAX_BATCH) {
+        CarryBatch<MAX_BATCH> cb;
+        cb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
+        for (int k = 0; k < cb.count; k++) cb.job[k] = jobs[i + k];
+        cudaError_t e = launch_carry_b<MAX_BATCH>(cb, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace pa

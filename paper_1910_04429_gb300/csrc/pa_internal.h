@@ -21,7 +21,25 @@ struct NttJob {
 };
 
 // Launches: digits of x and a -> convolution digits c_k (k < L) in buf_x.
+// (ahat must equal buf_a: the seed's spectrum is written over its buffer.)
 cudaError_t launch_convolution(const NttJob& job, cudaStream_t st);
+
+// One block of a batch of transforms that share a geometry.
+struct BlockIO {
+    u64* buf_x;   // N words: x, then the product digits
+    u64* buf_a;   // N words: a, then its spectrum (tile register order, times N^-1)
+    Digits dx, da;
+    u64 L;        // digits kept by the last inverse pass
+};
+constexpr int MAX_BATCH = 32;  // blocks per launch (kernel parameter array)
+template <int B>
+struct NttBatch {
+    int count;
+    BlockIO io[B];
+};
+// Launches the transforms of `count` blocks of geometry G, MAX_BATCH blocks per launch.
+cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const BlockIO* io,
+                                     int count, cudaStream_t st);
 
 // Carry resolve, + b, mod 2^n and extraction of bits [n-m, n) (Algorithm 1
 // steps 6-7, Sec. 3.2.2-3.2.5).
@@ -37,8 +55,10 @@ struct CarryJob {
 constexpr int CARRY_THREADS = 256;
 constexpr int CARRY_LIMBS = 4;  // limbs per thread
 constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
-inline u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
+GL_HD u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
 cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
+// Carry steps of `count` independent blocks (any sizes), MAX_BATCH per launch.
+cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st);
 
 // Per-kernel timing with CUDA events on the launching stream (off unless
 // pa_profile(1) was called). prof_begin/prof_end bracket one launch.

@@ -1,17 +1,22 @@
 // NTT multiply kernels: zero fill + split into 16-bit digits, forward
 // transforms, pointwise product and inverse transform (Algorithm 1, steps
 // 1-5, Sec. 3.2.2), as tile kernels over GF(p), p = 2^64 - 2^32 + 1.
+//
+// Every kernel serves a batch of independent blocks that share one transform
+// geometry: blockIdx.x is the tile, blockIdx.y the block, and the per-block
+// buffers and digit sources arrive in a __grid_constant__ parameter array.
 #include "pa_internal.h"
 
 namespace pa {
 
 // Strided pass over one tile of both operands: the twiddles computed for x
 // are kept in registers and reused for a.
-template <int RA, int RB, int C, bool PACK>
-__global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, u64* buf0, u64* buf1,
-                                                       Digits d0, Digits d1, Twiddles tw) {
+template <int RA, int RB, int C, bool PACK, int B>
+__global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
+                                                       Twiddles tw) {
     using S = Strided<RA, RB, C>;
     __shared__ u64 sm[TILE];
+    const BlockIO& io = nb.io[blockIdx.y];
     TilePos tp = S::tile(g, blockIdx.x);
     u64 w[S::ITEMS_B][RA];
 #pragma unroll
@@ -21,8 +26,8 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, u64* buf0,
     }
 #pragma unroll
     for (int op = 0; op < 2; op++) {
-        u64* buf = op ? buf1 : buf0;
-        const Digits& d = op ? d1 : d0;
+        u64* buf = op ? io.buf_a : io.buf_x;
+        const Digits& d = op ? io.da : io.dx;
         if (op) __syncthreads();  // the tile of x is out of shared memory
 #pragma unroll
         for (int i = 0; i < S::ITEMS_A; i++) {
@@ -38,22 +43,24 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, u64* buf0,
     }
 }
 
-template <int RA, int RB, int C, bool LAST>
-__global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, u64* buf, u64 keep,
+template <int RA, int RB, int C, bool LAST, int B>
+__global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     using S = Strided<RA, RB, C>;
     __shared__ u64 sm[TILE];
+    const BlockIO& io = nb.io[blockIdx.y];
     TilePos tp = S::tile(g, blockIdx.x);
 #pragma unroll
     for (int i = 0; i < S::ITEMS_B; i++) {
         int it = threadIdx.x + i * NT;
-        if (S::NB % NT == 0 || it < S::NB) S::inv_b(g, tp, it, buf, sm, tw);
+        if (S::NB % NT == 0 || it < S::NB) S::inv_b(g, tp, it, io.buf_x, sm, tw);
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < S::ITEMS_A; i++) {
         int it = threadIdx.x + i * NT;
-        if (S::NA % NT == 0 || it < S::NA) S::template inv_a<LAST>(g, tp, it, buf, sm, keep);
+        if (S::NA % NT == 0 || it < S::NA)
+            S::template inv_a<LAST>(g, tp, it, io.buf_x, sm, io.L);
     }
 }
 
@@ -76,31 +83,35 @@ __device__ __forceinline__ void contig_forward(const u64* src, const Digits& d, 
 }
 
 // Spectrum of a, scaled by N^-1 (the inverse transform's normalisation),
-// stored in register order: thread t of tile T owns words T*4096 + 8t .. +7.
-template <bool PACK>
-__global__ void __launch_bounds__(NT) k_contig_seed(u64* buf, Digits d, u64* ahat, u64 ninv,
+// stored over buf_a in register order: thread t of tile T owns words
+// T*4096 + 8t .. +7. Each tile is read completely before it is overwritten.
+template <bool PACK, int B>
+__global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttBatch<B> nb, u64 ninv,
                                                     Twiddles tw) {
     __shared__ u64 sm[TILE];
+    const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
     u64 v[8];
-    contig_forward<PACK>(buf + base, d, base, tw, sm, v);
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(ahat + base + 8 * threadIdx.x);
+    contig_forward<PACK>(io.buf_a + base, io.da, base, tw, sm, v);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(io.buf_a + base + 8 * threadIdx.x);
 #pragma unroll
     for (int k = 0; k < 4; k++)
         dst[k] = make_ulonglong2(gl::mul(v[2 * k], ninv), gl::mul(v[2 * k + 1], ninv));
 }
 
 // Forward contiguous pass of x, pointwise product with a's spectrum (Algorithm 1
-// step 4) and the inverse contiguous pass, in one tile-resident kernel.
-template <bool PACK>
-__global__ void __launch_bounds__(NT) k_contig_fused(u64* buf, Digits d, const u64* ahat,
-                                                     u64 keep, Twiddles tw) {
+// step 4) and the inverse contiguous pass, in one tile-resident kernel. With
+// PACK (a single-tile transform) this is also the last inverse pass, which keeps
+// only the digits below io.L.
+template <bool PACK, int B>
+__global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ NttBatch<B> nb, Twiddles tw) {
     __shared__ u64 sm[TILE];
+    const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
     int t = threadIdx.x;
     u64 v[8];
-    contig_forward<PACK>(buf + base, d, base, tw, sm, v);
-    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(ahat + base + 8 * t);
+    contig_forward<PACK>(io.buf_x + base, io.dx, base, tw, sm, v);
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(io.buf_a + base + 8 * t);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         ulonglong2 w = src[k];
@@ -118,29 +129,12 @@ __global__ void __launch_bounds__(NT) k_contig_fused(u64* buf, Digits d, const u
     __syncthreads();
     c_inv_col_b_store(t, sm, v);
     __syncthreads();
-    c_inv_col_a(t, sm, buf + base, base, keep);
+    c_inv_col_a(t, sm, io.buf_x + base, base, PACK ? io.L : ~0ull);
 }
 
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-template <int RA, int RB, int C>
-static void fwd_pass(const StridedGeom& g, bool pack, const NttJob& j, cudaStream_t st) {
-    unsigned grid = (unsigned)(g.N / (RA * RB * C));
-    if (pack)
-        k_fwd_strided<RA, RB, C, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
-    else
-        k_fwd_strided<RA, RB, C, false><<<grid, NT, 0, st>>>(g, j.buf_x, j.buf_a, j.dx, j.da, j.tw);
-}
-
-template <int RA, int RB, int C>
-static void inv_pass(const StridedGeom& g, bool last, const NttJob& j, cudaStream_t st) {
-    unsigned grid = (unsigned)(g.N / (RA * RB * C));
-    if (last)
-        k_inv_strided<RA, RB, C, true><<<grid, NT, 0, st>>>(g, j.buf_x, j.L, j.tw);
-    else
-        k_inv_strided<RA, RB, C, false><<<grid, NT, 0, st>>>(g, j.buf_x, j.L, j.tw);
-}
 
 // radix -> (RA, RB, columns per tile)
 #define PA_RADIX_TABLE(X)                                                                  \
@@ -155,17 +149,40 @@ int strided_columns(int R) {
     return 0;
 }
 
-static void dispatch_fwd(int R, const StridedGeom& g, bool pack, const NttJob& j, cudaStream_t st) {
-#define PA_FWD(r, a, b, c) if (R == r) return fwd_pass<a, b, c>(g, pack, j, st);
-    PA_RADIX_TABLE(PA_FWD)
-#undef PA_FWD
-}
+template <int B>
+struct Launcher {
+    const StridedGeom* g;
+    const NttBatch<B>* nb;
+    const Twiddles* tw;
+    cudaStream_t st;
 
-static void dispatch_inv(int R, const StridedGeom& g, bool last, const NttJob& j, cudaStream_t st) {
-#define PA_INV(r, a, b, c) if (R == r) return inv_pass<a, b, c>(g, last, j, st);
-    PA_RADIX_TABLE(PA_INV)
+    template <int RA, int RB, int C>
+    void fwd(bool pack) const {
+        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
+        if (pack)
+            k_fwd_strided<RA, RB, C, true, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
+        else
+            k_fwd_strided<RA, RB, C, false, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
+    }
+    template <int RA, int RB, int C>
+    void inv(bool last) const {
+        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
+        if (last)
+            k_inv_strided<RA, RB, C, true, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
+        else
+            k_inv_strided<RA, RB, C, false, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
+    }
+    void dispatch_fwd(int R, bool pack) const {
+#define PA_FWD(r, a, b, c) if (R == r) return fwd<a, b, c>(pack);
+        PA_RADIX_TABLE(PA_FWD)
+#undef PA_FWD
+    }
+    void dispatch_inv(int R, bool last) const {
+#define PA_INV(r, a, b, c) if (R == r) return inv<a, b, c>(last);
+        PA_RADIX_TABLE(PA_INV)
 #undef PA_INV
-}
+    }
+};
 
 static StridedGeom strided_geom(const Geom& G, int p) {
     u64 C = (u64)strided_columns(G.pass[p].R);
@@ -174,37 +191,56 @@ static StridedGeom strided_geom(const Geom& G, int p) {
     return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, log_tpb};
 }
 
-cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
-    const Geom& G = j.geom;
+template <int B>
+static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatch<B>& nb,
+                                cudaStream_t st) {
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        dispatch_fwd(G.pass[p].R, g, p == 0, j, st);
+        Launcher<B>{&g, &nb, &tw, st}.dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }
-    unsigned tiles = (unsigned)(G.N / TILE);
+    dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
     bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
     u64 ninv = n_inverse(G.logN, G.three);
-    u64 keep = pack ? j.L : G.N;
     prof_begin(st, "ntt_contig_seed");
     if (pack)
-        k_contig_seed<true><<<tiles, NT, 0, st>>>(j.buf_a, j.da, j.ahat, ninv, j.tw);
+        k_contig_seed<true, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
     else
-        k_contig_seed<false><<<tiles, NT, 0, st>>>(j.buf_a, j.da, j.ahat, ninv, j.tw);
+        k_contig_seed<false, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
     prof_end(st);
     prof_begin(st, "ntt_contig_fused");
     if (pack)
-        k_contig_fused<true><<<tiles, NT, 0, st>>>(j.buf_x, j.dx, j.ahat, keep, j.tw);
+        k_contig_fused<true, B><<<tiles, NT, 0, st>>>(nb, tw);
     else
-        k_contig_fused<false><<<tiles, NT, 0, st>>>(j.buf_x, j.dx, j.ahat, keep, j.tw);
+        k_contig_fused<false, B><<<tiles, NT, 0, st>>>(nb, tw);
     prof_end(st);
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        dispatch_inv(G.pass[p].R, g, p == 0, j, st);
+        Launcher<B>{&g, &nb, &tw, st}.dispatch_inv(G.pass[p].R, p == 0);
         prof_end(st);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
+    NttBatch<1> nb;
+    nb.count = 1;
+    nb.io[0] = BlockIO{j.buf_x, j.buf_a, j.dx, j.da, j.L};
+    return launch_batch<1>(j.geom, j.tw, nb, st);
+}
+
+cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const BlockIO* io,
+                                     int count, cudaStream_t st) {
+    for (int i = 0; i < count; i += MAX_BATCH) {
+        NttBatch<MAX_BATCH> nb;
+        nb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
+        for (int k = 0; k < nb.count; k++) nb.io[k] = io[i + k];
+        cudaError_t e = launch_batch<MAX_BATCH>(G, tw, nb, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace pa

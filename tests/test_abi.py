@@ -102,6 +102,15 @@ def test_argument_checks_without_gpu():
     assert lib.pa_hash_noalloc(p, p, p, (1 << 20) + 1, 1, p, null) == binding.PA_EINVAL
     assert b"PA_NOALLOC_MAX_BITS" in lib.pa_last_error()
     assert lib.pa_hash_noalloc(p, p, p, 10, 11, p, null) == binding.PA_EINVAL
+    # serving: bad requests are refused before the loop (or CUDA) is touched
+    t = ctypes.c_uint64(0)
+    bad = binding.PaBlock(z.ctypes.data, z.ctypes.data, z.ctypes.data, 100, 0, z.ctypes.data)
+    assert lib.pa_submit(ctypes.byref(bad), ctypes.byref(t)) == binding.PA_EINVAL
+    nul = binding.PaBlock(0, z.ctypes.data, z.ctypes.data, 100, 10, z.ctypes.data)
+    assert lib.pa_submit(ctypes.byref(nul), ctypes.byref(t)) == binding.PA_EINVAL
+    st = ctypes.c_int(0)
+    assert lib.pa_poll(12345, 0, ctypes.byref(st)) == binding.PA_EINVAL
+    assert b"unknown ticket" in lib.pa_last_error()
 
 
 @pytest.mark.parametrize("n,N", [(1, 4096), (32768, 4096), (32769, 8192), (96_000, 3 << 12),
