@@ -246,6 +246,20 @@ int pa_hash_noalloc(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
 /* pa_shutdown: free tables and pooled memory of all devices (no work may be in flight). */
 int pa_shutdown(void);
 
+/*
+ * pa_device_status: waits for all work on the current device, then returns
+ * PA_ETIMEOUT if any kernel of this library has given up a bounded wait since
+ * the last clear (the carry look-back waits at most ~2^20 polls for an earlier
+ * tile; on timeout that call's output is wrong but the kernel finishes and the
+ * context stays usable), else PA_OK. clear != 0 resets the flag.
+ */
+int pa_device_status(int clear);
+
+/* Fault injection for tests of the timeout path (faults nothing on the GPU). */
+#define PA_FAULT_CARRY_WAIT 1 /* the next carry launch never processes its first tile,
+                                 so the second tile's bounded wait runs out (short limit) */
+int pa_fault_inject(int what);
+
 /* Human-readable text of the last error on the calling thread ("" if none). */
 const char* pa_last_error(void);
 

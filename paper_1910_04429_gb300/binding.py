@@ -17,6 +17,7 @@ from . import build as _build
 
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_EAGAIN, PA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PA_MAX_BITS = 1 << 31
+PA_FAULT_CARRY_WAIT = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -39,6 +40,8 @@ _SIGS = {
     "pa_serve_stats": ([ctypes.c_void_p], ctypes.c_int),
     "pa_serve_stop": ([], ctypes.c_int),
     "pa_profile_collect": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "pa_device_status": ([ctypes.c_int], ctypes.c_int),
+    "pa_fault_inject": ([ctypes.c_int], ctypes.c_int),
     "pa_last_error": ([], ctypes.c_char_p),
     "pa_version": ([], ctypes.c_char_p),
 }
@@ -263,6 +266,15 @@ def profile_collect() -> dict:
     if n < 0:
         _check(n, "pa_profile_collect")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n)}
+
+
+def device_status(clear: bool = False) -> int:
+    """PA_OK, or PA_ETIMEOUT if a bounded device wait ran out since the last clear."""
+    return int(load().pa_device_status(1 if clear else 0))
+
+
+def fault_inject(what: int = PA_FAULT_CARRY_WAIT):
+    _check(load().pa_fault_inject(what), "pa_fault_inject")
 
 
 def version() -> str:

@@ -136,12 +136,10 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
 
 int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint64_t m,
                 uint64_t* out, cudaStream_t st, Scratch& scr) {
-    u64 tiles = carry_tiles(n);
-    void *agg, *cin;
+    void* state;
     int rc;
-    if ((rc = scr.get(tiles, &agg))) return rc;
-    if ((rc = scr.get(tiles, &cin))) return rc;
-    CarryJob c{coef, L, seed_b, n, m, out, (uint8_t*)agg, (uint8_t*)cin};
+    if ((rc = scr.get(carry_state_words(n) * sizeof(u32), &state))) return rc;
+    CarryJob c{coef, L, seed_b, n, m, out, (u32*)state};
     cudaError_t e = launch_carry(c, st);
     if (e != cudaSuccess) return cuda_fail(e, "carry launch");
     return PA_OK;
@@ -190,12 +188,12 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     // workspace: all transform buffers, then the carry bytes, in one allocation
     u64 words = 0, carry_bytes = 0;
     for (auto& gr : groups) words += 2 * gr.first * gr.second.size();
-    for (uint32_t i = 0; i < count; i++) carry_bytes += 2 * carry_tiles(blocks[i].n);
+    for (uint32_t i = 0; i < count; i++) carry_bytes += carry_state_words(blocks[i].n) * sizeof(u32);
     Scratch scr(st, pool);
     void* ws;
     if ((rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
     u64* w = (u64*)ws;
-    uint8_t* cb = (uint8_t*)(w + words);
+    u32* cb = (u32*)(w + words);
     std::vector<CarryJob> cj(count);
 
     cudaError_t e = cudaEventRecord(d.fork, st);
@@ -213,9 +211,8 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
             uint16_t top = top_digit_mask(b.n);
             io[k] = BlockIO{w, w + G.N, Digits{(const uint16_t*)b.key, L, top},
                             Digits{(const uint16_t*)b.seed_a, L, top}, L};
-            u64 t = carry_tiles(b.n);
-            cj[idx[k]] = CarryJob{w, L, b.seed_b, b.n, b.m, b.out, cb, cb + t};
-            cb += 2 * t;
+            cj[idx[k]] = CarryJob{w, L, b.seed_b, b.n, b.m, b.out, cb};
+            cb += carry_state_words(b.n);
             w += 2 * G.N;
         }
         cudaStream_t s = d.side[g % SIDE_STREAMS];
@@ -423,7 +420,7 @@ int pa_prepare(uint64_t n) {
 uint64_t pa_workspace_bytes(uint64_t n) {
     if (n < 1 || n > PA_MAX_BITS) return 0;
     uint64_t N = geom_for_bits(n).N;
-    return 2 * N * sizeof(u64) + 2 * carry_tiles(n);
+    return 2 * N * sizeof(u64) + carry_state_words(n) * sizeof(u32);
 }
 
 int pa_shutdown(void) {
@@ -444,6 +441,22 @@ int pa_shutdown(void) {
     }
     g_dev.clear();
     if (prev >= 0) cudaSetDevice(prev);
+    return PA_OK;
+}
+
+int pa_device_status(int clear) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    u32 st = 0;
+    if ((e = read_device_status(&st, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
+    if (st & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (carry look-back)");
+    return PA_OK;
+}
+
+int pa_fault_inject(int what) {
+    if (what != PA_FAULT_CARRY_WAIT) return fail(PA_EINVAL, "pa_fault_inject: unknown fault");
+    std::lock_guard<std::mutex> lk(g_mu);
+    fault_inject_carry();
     return PA_OK;
 }
 

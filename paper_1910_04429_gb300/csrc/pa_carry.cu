@@ -11,11 +11,20 @@
 // so that y = sum_j u_j 2^(64 j) exactly. What remains is a one-bit carry
 // chain: carry_{j+1} = [u_j + carry_j >= 2^64], whose generate / propagate
 // pairs (g_j = [u_j = 2^64], p_j = [u_j = 2^64 - 1]) compose associatively.
-// Three kernels: tile aggregates, one scan over tiles, then every tile
-// re-derives its limbs with its carry-in and writes the output bits.
+//
+// One kernel, decoupled look-back: each CTA takes the next tile of 1024 limbs
+// from an atomic ticket (so every earlier tile has started), stages its digits
+// and addend limbs in shared memory with coalesced loads, scans its (g, p)
+// pairs, publishes the tile aggregate, walks back over the published states of
+// earlier tiles to obtain its carry-in, publishes its inclusive prefix, and
+// writes its output bits. Every wait on another tile is bounded: when the
+// limit runs out the kernel records PA_STATUS_TIMEOUT in the device status word
+// and carries on with a carry-in of 0, so it always terminates.
 #include "pa_internal.h"
 
 namespace pa {
+
+__device__ u32 g_status;  // sticky device status (PA_STATUS_* bits), read by pa_device_status
 
 // (G, P) packed in two bits: bit 0 generate, bit 1 propagate.
 __device__ __forceinline__ int compose(int earlier, int later) {
@@ -25,38 +34,44 @@ __device__ __forceinline__ int compose(int earlier, int later) {
 }
 constexpr int GP_IDENTITY = 2;
 
+// tile state word: 0 = nothing yet, (1 << 2 | gp) = aggregate of the tile,
+// (2 << 2 | gp) = inclusive prefix from tile 0 through the tile
+constexpr u32 ST_AGG = 1u << 2, ST_INC = 2u << 2;
+
+constexpr int HALO_LO = 2, HALO_HI = 1;                       // extra limbs before / after a tile
+constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 1024
+constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 1027
+constexpr int SM_COEF = 4 * SM_LIMBS;                         // 4108
+
 struct Limb {
     u64 lo;   // u_j mod 2^64
     int gp;   // (g_j, p_j)
 };
 
-// V_j as (lo, hi); V_j = 0 outside [0, Ly)
-__device__ __forceinline__ void limb_v(const CarryJob& c, long long j, u64 Ly, u64* vlo, u64* vhi) {
-    if (j < 0 || (u64)j >= Ly) { *vlo = 0; *vhi = 0; return; }
+// V of the limb at shared-memory position l (limb J0 + l)
+__device__ __forceinline__ void limb_v(const u64* cs, const u64* bs, int l, u64* vlo, u64* vhi) {
     u64 lo = 0, hi = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        u64 k = 4 * (u64)j + i;
-        u64 ck = k < c.L ? c.coef[k] : 0;
+        u64 ck = cs[4 * l + i];
         u64 plo = i ? (ck << (16 * i)) : ck;
         u64 phi = i ? (ck >> (64 - 16 * i)) : 0;
         lo += plo;
         hi += phi + (lo < plo);
     }
-    u64 bj = c.b[j];
+    u64 bj = bs[l];
     lo += bj;
     hi += (lo < bj);
     *vlo = lo;
     *vhi = hi;
 }
 
-// u_j for j = j0 .. j0 + CNT - 1, from V_{j0-2} .. V_{j0+CNT-1}
+// u of CNT limbs starting at shared position l0 (needs V at l0-2 .. l0+CNT-1)
 template <int CNT>
-__device__ __forceinline__ void limbs_u(const CarryJob& c, long long j0, u64 Ly, Limb* u) {
+__device__ __forceinline__ void limbs_u(const u64* cs, const u64* bs, int l0, Limb* u) {
     u64 vlo[CNT + 2], vhi[CNT + 2];
 #pragma unroll
-    for (int i = 0; i < CNT + 2; i++) limb_v(c, j0 - 2 + i, Ly, &vlo[i], &vhi[i]);
-    // E_{j0-1+i} = lo(V_{j0-1+i}) + hi(V_{j0-2+i}), i = 0 .. CNT
+    for (int i = 0; i < CNT + 2; i++) limb_v(cs, bs, l0 - 2 + i, &vlo[i], &vhi[i]);
     u64 e[CNT + 1];
     int f[CNT + 1];
 #pragma unroll
@@ -97,80 +112,92 @@ __device__ __forceinline__ int block_exclusive(int v, int* total) {
     return compose(wpre, exc);
 }
 
-template <int B>
-struct CarryBatch {
-    int count;
-    CarryJob job[B];
-};
-
-template <int B>
-__global__ void __launch_bounds__(CARRY_THREADS) k_carry_tiles(const __grid_constant__ CarryBatch<B> cb) {
-    const CarryJob& c = cb.job[blockIdx.y];
-    u64 Ly = (c.n + 63) / 64;
-    if (blockIdx.x >= carry_tiles(c.n)) return;
-    long long j0 = ((long long)blockIdx.x * CARRY_THREADS + threadIdx.x) * CARRY_LIMBS;
-    Limb u[CARRY_LIMBS];
-    limbs_u<CARRY_LIMBS>(c, j0, Ly, u);
-    int acc = GP_IDENTITY;
-#pragma unroll
-    for (int i = 0; i < CARRY_LIMBS; i++)
-        if ((u64)(j0 + i) < Ly) acc = compose(acc, u[i].gp);
-    int total;
-    block_exclusive(acc, &total);
-    if (threadIdx.x == 0) c.agg[blockIdx.x] = (uint8_t)total;
+__device__ __forceinline__ void publish(u32* p, u32 v) {
+    __threadfence();
+    atomicExch(p, v);
 }
 
-// One CTA per block: carry into every tile from the tile aggregates.
-template <int B>
-__global__ void __launch_bounds__(1024) k_carry_scan(const __grid_constant__ CarryBatch<B> cb) {
-    const CarryJob& c = cb.job[blockIdx.x];
-    u64 ntiles = carry_tiles(c.n);
-    __shared__ int part[1024];
-    u64 per = (ntiles + 1023) / 1024;
-    u64 lo = threadIdx.x * per, hi = lo + per < ntiles ? lo + per : ntiles;
-    int acc = GP_IDENTITY;
-    for (u64 t = lo; t < hi; t++) acc = compose(acc, c.agg[t]);
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    // exclusive prefix over the 1024 partials (simple, ordered, per thread)
-    if (threadIdx.x == 0) {
-        int run = GP_IDENTITY;
-        for (int i = 0; i < 1024; i++) {
-            int x = part[i];
-            part[i] = run;
-            run = compose(run, x);
-        }
-    }
-    __syncthreads();
-    int pre = part[threadIdx.x];
-    for (u64 t = lo; t < hi; t++) {
-        c.cin[t] = (uint8_t)(pre & 1);  // carry into tile t (chain starts at 0)
-        pre = compose(pre, c.agg[t]);
-    }
+__device__ __forceinline__ u32 observe(const u32* p) {
+    u32 v = *(const volatile u32*)p;
+    __threadfence();
+    return v;
 }
 
 template <int B>
-__global__ void __launch_bounds__(CARRY_THREADS) k_carry_out(const __grid_constant__ CarryBatch<B> cb) {
+__global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
+                                                         u32 ticket_start, u32 spin_limit) {
+    __shared__ u64 cs[SM_COEF];
+    __shared__ u64 bs[SM_LIMBS];
+    __shared__ u32 tile_sh;
+    __shared__ int carry_in_sh;
     const CarryJob& c = cb.job[blockIdx.y];
-    u64 Ly = (c.n + 63) / 64;
-    if (blockIdx.x >= carry_tiles(c.n)) return;
-    long long j0 = ((long long)blockIdx.x * CARRY_THREADS + threadIdx.x) * CARRY_LIMBS;
+    const u64 Ly = (c.n + 63) / 64, tiles = carry_tiles(c.n);
+    u32* state = c.state;  // tiles words, then the ticket counter
+    if (threadIdx.x == 0) tile_sh = atomicAdd(&state[tiles], 1u) + ticket_start;
+    __syncthreads();
+    const u64 t = tile_sh;
+    if (t >= tiles) return;
+
+    // stage digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS), J0 = 1024 t - 2
+    const long long J0 = (long long)t * TILE_LIMBS - HALO_LO;
+    for (int i = threadIdx.x; i < SM_COEF; i += CARRY_THREADS) {
+        long long k = 4 * J0 + i;
+        cs[i] = (k >= 0 && (u64)k < c.L) ? c.coef[k] : 0;
+    }
+    for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
+        long long j = J0 + i;
+        bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
+    }
+    __syncthreads();
+
+    const int l0 = HALO_LO + CARRY_LIMBS * threadIdx.x;  // shared position of the thread's first limb
+    const u64 j0 = t * TILE_LIMBS + CARRY_LIMBS * threadIdx.x;
     Limb u[CARRY_LIMBS + 1];
-    limbs_u<CARRY_LIMBS + 1>(c, j0, Ly, u);
+    limbs_u<CARRY_LIMBS + 1>(cs, bs, l0, u);
     int acc = GP_IDENTITY;
 #pragma unroll
     for (int i = 0; i < CARRY_LIMBS; i++)
-        if ((u64)(j0 + i) < Ly) acc = compose(acc, u[i].gp);
+        if (j0 + i < Ly) acc = compose(acc, u[i].gp);
     int total;
     int pre = block_exclusive(acc, &total);
-    int tile_in = c.cin[blockIdx.x];
-    int carry = (pre & 1) | ((pre >> 1) & tile_in);
+
+    if (threadIdx.x == 0) {
+        int excl = GP_IDENTITY;  // prefix of tiles 0 .. t-1 applied in order
+        if (t == 0) {
+            publish(&state[0], ST_INC | (u32)total);
+        } else {
+            publish(&state[t], ST_AGG | (u32)total);
+            long long i = (long long)t - 1;
+            int later = GP_IDENTITY;  // tiles i+1 .. t-1 composed
+            while (true) {
+                u32 s = observe(&state[i]);
+                u32 spins = 0;
+                while (!(s & (ST_AGG | ST_INC))) {
+                    if (++spins > spin_limit) {
+                        atomicOr(&g_status, PA_STATUS_TIMEOUT);
+                        s = ST_INC;  // give up: treat as an inclusive prefix (0, 0)
+                        break;
+                    }
+                    __nanosleep(64);
+                    s = observe(&state[i]);
+                }
+                later = compose((int)(s & 3u), later);
+                if (s & ST_INC) break;
+                i--;
+            }
+            excl = later;
+            publish(&state[t], ST_INC | (u32)compose(excl, total));
+        }
+        carry_in_sh = excl & 1;  // carry into the tile (the chain starts with 0)
+    }
+    __syncthreads();
+    int carry = (pre & 1) | ((pre >> 1) & carry_in_sh);
     u64 y[CARRY_LIMBS + 1];
 #pragma unroll
     for (int i = 0; i < CARRY_LIMBS + 1; i++) {
         y[i] = u[i].lo + (u64)carry;
         carry = (u[i].gp & 1) | ((u[i].gp >> 1) & carry);
-        u64 j = (u64)j0 + i;
+        u64 j = j0 + i;
         if (j >= Ly) y[i] = 0;
         else if (j == Ly - 1 && (c.n & 63)) y[i] &= (1ull << (c.n & 63)) - 1;  // mod 2^n
     }
@@ -179,7 +206,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry_out(const __grid_consta
     u64 Mo = (c.m + 63) >> 6;
 #pragma unroll
     for (int i = 0; i < CARRY_LIMBS; i++) {
-        u64 j = (u64)j0 + i;
+        u64 j = j0 + i;
         if (j < q || j >= q + Mo) continue;
         u64 o = r ? ((y[i] >> r) | (y[i + 1] << (64 - r))) : y[i];
         u64 oi = j - q;
@@ -188,22 +215,28 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry_out(const __grid_consta
     }
 }
 
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static u32 g_inject_ticket = 0;  // armed by fault_inject_carry(); consumed by the next launch
+
+void fault_inject_carry() { g_inject_ticket = 1; }
+
 template <int B>
 static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     u64 tiles = 0;
     for (int i = 0; i < cb.count; i++) {
-        u64 t = carry_tiles(cb.job[i].n);
-        tiles = t > tiles ? t : tiles;
+        u64 tt = carry_tiles(cb.job[i].n);
+        tiles = tt > tiles ? tt : tiles;
+        cudaError_t e = cudaMemsetAsync(cb.job[i].state, 0, (tt + 1) * sizeof(u32), st);
+        if (e != cudaSuccess) return e;
     }
+    u32 start = g_inject_ticket;
+    u32 limit = start ? 1000u : CARRY_SPIN_LIMIT;
+    g_inject_ticket = 0;
     dim3 grid((unsigned)tiles, (unsigned)cb.count);
-    prof_begin(st, "carry_tiles");
-    k_carry_tiles<B><<<grid, CARRY_THREADS, 0, st>>>(cb);
-    prof_end(st);
-    prof_begin(st, "carry_scan");
-    k_carry_scan<B><<<cb.count, 1024, 0, st>>>(cb);
-    prof_end(st);
-    prof_begin(st, "carry_out");
-    k_carry_out<B><<<grid, CARRY_THREADS, 0, st>>>(cb);
+    prof_begin(st, "carry_lookback");
+    k_carry<B><<<grid, CARRY_THREADS, 0, st>>>(cb, start, limit);
     prof_end(st);
     return cudaGetLastError();
 }
@@ -224,6 +257,15 @@ cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t read_device_status(u32* out, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_status, sizeof(u32));
+    if (e == cudaSuccess && clear) {
+        u32 zero = 0;
+        e = cudaMemcpyToSymbol(g_status, &zero, sizeof(u32));
+    }
+    return e;
 }
 
 }  // namespace pa

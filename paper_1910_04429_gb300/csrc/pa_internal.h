@@ -42,23 +42,36 @@ cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const Bl
                                      int count, cudaStream_t st);
 
 // Carry resolve, + b, mod 2^n and extraction of bits [n-m, n) (Algorithm 1
-// steps 6-7, Sec. 3.2.2-3.2.5).
+// steps 6-7, Sec. 3.2.2-3.2.5), one decoupled look-back kernel.
 struct CarryJob {
     const u64* coef;  // convolution digits, coefficient k weighs 2^(16k)
     u64 L;            // digits present (coef[k] = 0 for k >= L)
     const u64* b;     // addend limbs, ceil(n/64)
     u64 n, m;
     u64* out;         // ceil(m/64) limbs
-    uint8_t* agg;     // per-tile carry aggregates (scratch)
-    uint8_t* cin;     // per-tile carry-in (scratch)
+    u32* state;       // scratch, carry_state_words(n) words, 4-byte aligned (zeroed by the launch)
+};
+template <int B>
+struct CarryBatch {
+    int count;
+    CarryJob job[B];
 };
 constexpr int CARRY_THREADS = 256;
 constexpr int CARRY_LIMBS = 4;  // limbs per thread
 constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
+constexpr u32 CARRY_SPIN_LIMIT = 1u << 20;  // polls of a predecessor tile before giving up (~0.1-1 s)
+constexpr u32 PA_STATUS_TIMEOUT = 1u;       // device status bit: a bounded wait ran out
 GL_HD u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
+GL_HD u64 carry_state_words(u64 n) { return carry_tiles(n) + 1; }  // tile states + ticket
 cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
 // Carry steps of `count` independent blocks (any sizes), MAX_BATCH per launch.
 cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st);
+// The next carry launch leaves its first tile unprocessed, so the wait of the
+// second tile on it runs out (bounded, short limit): a host-armed test of the
+// timeout path that faults nothing.
+void fault_inject_carry();
+// Sticky device status bits (PA_STATUS_*); synchronous.
+cudaError_t read_device_status(u32* out, bool clear);
 
 // Per-kernel timing with CUDA events on the launching stream (off unless
 // pa_profile(1) was called). prof_begin/prof_end bracket one launch.

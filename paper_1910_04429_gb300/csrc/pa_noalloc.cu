@@ -34,7 +34,7 @@ constexpr u64 NA_MAX_N = 1ull << NA_MAX_LOGN;
 constexpr int NA_LOGN0 = LOG_TILE;                       // smallest transform, 2^12
 constexpr int NA_SIZES = NA_MAX_LOGN - NA_LOGN0 + 1;
 constexpr u64 NA_TABLE_WORDS = 4 * 4096 + 2 * (NA_MAX_N >> 12);
-constexpr u64 NA_CARRY_BYTES = 256;                      // 2 x 128 carry tiles
+constexpr u64 NA_CARRY_BYTES = 256;                      // carry tile states (17 words used)
 
 static_assert(PA_NOALLOC_MAX_BITS <= 16 * (NA_MAX_N / 2), "transform too short for the cap");
 
@@ -145,7 +145,7 @@ extern "C" int pa_hash_noalloc(const uint64_t* key, const uint64_t* seed_a, cons
         set_error("pa_hash_noalloc: NTT launch failed");
         return PA_ECUDA;
     }
-    CarryJob c{j.buf_x, L, seed_b, n, m, out, d->carry, d->carry + NA_CARRY_BYTES / 2};
+    CarryJob c{j.buf_x, L, seed_b, n, m, out, reinterpret_cast<uint32_t*>(d->carry)};
     if (launch_carry(c, st) != cudaSuccess) {
         set_error("pa_hash_noalloc: carry launch failed");
         return PA_ECUDA;

@@ -98,6 +98,7 @@ def test_argument_checks_without_gpu():
     assert lib.pa_hash_batched(blocks, 2, null) == binding.PA_EINVAL
     assert b"block 1" in lib.pa_last_error()
     assert lib.pa_prepare(0) == binding.PA_EINVAL
+    assert lib.pa_fault_inject(99) == binding.PA_EINVAL
     # the fixed-scratch entry point refuses keys beyond its scratch size
     assert lib.pa_hash_noalloc(p, p, p, (1 << 20) + 1, 1, p, null) == binding.PA_EINVAL
     assert b"PA_NOALLOC_MAX_BITS" in lib.pa_last_error()
@@ -120,5 +121,5 @@ def test_workspace_bytes(n, N):
     """Transform length N = smallest 2^k or 3 * 2^k (first radix <= 48) that is
     >= max(4096, 2 ceil(n/16) - 1)."""
     tiles = -(-(-(-n // 64)) // 1024)
-    assert binding.workspace_bytes(n) == 2 * N * 8 + 2 * tiles
+    assert binding.workspace_bytes(n) == 2 * N * 8 + 4 * (tiles + 1)
     assert binding.workspace_bytes(0) == 0
