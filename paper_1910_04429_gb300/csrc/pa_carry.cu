@@ -17,7 +17,8 @@
 // and addend limbs in shared memory with coalesced loads, scans its (g, p)
 // pairs, publishes the tile aggregate, walks back over the published states of
 // earlier tiles to obtain its carry-in, publishes its inclusive prefix, and
-// writes its output bits. Every wait on another tile is bounded: when the
+// writes its output bits. Warp 0 reads 32 predecessor states per round, so a
+// tile does not wait for the inclusive prefix of its neighbour. Every wait on another tile is bounded: when the
 // limit runs out the kernel records PA_STATUS_TIMEOUT in the device status word
 // and carries on with a carry-in of 0, so it always terminates.
 #include "pa_internal.h"
@@ -161,34 +162,50 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     int total;
     int pre = block_exclusive(acc, &total);
 
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // warp 0: publish the aggregate, then look back 32 predecessors at a time
+        const int lane = threadIdx.x;
         int excl = GP_IDENTITY;  // prefix of tiles 0 .. t-1 applied in order
         if (t == 0) {
-            publish(&state[0], ST_INC | (u32)total);
+            if (lane == 0) publish(&state[0], ST_INC | (u32)total);
         } else {
-            publish(&state[t], ST_AGG | (u32)total);
-            long long i = (long long)t - 1;
-            int later = GP_IDENTITY;  // tiles i+1 .. t-1 composed
+            if (lane == 0) publish(&state[t], ST_AGG | (u32)total);
+            long long base = (long long)t - 1;  // lane l looks at tile base - l
+            int later = GP_IDENTITY;            // tiles after the current window, composed
             while (true) {
-                u32 s = observe(&state[i]);
-                u32 spins = 0;
-                while (!(s & (ST_AGG | ST_INC))) {
-                    if (++spins > spin_limit) {
-                        atomicOr(&g_status, PA_STATUS_TIMEOUT);
-                        s = ST_INC;  // give up: treat as an inclusive prefix (0, 0)
-                        break;
-                    }
-                    __nanosleep(64);
+                long long i = base - lane;
+                u32 s = ST_INC;  // below tile 0: the chain starts with carry 0
+                if (i >= 0) {
                     s = observe(&state[i]);
+                    u32 spins = 0;
+                    while (!(s & (ST_AGG | ST_INC))) {
+                        if (++spins > spin_limit) {
+                            atomicOr(&g_status, PA_STATUS_TIMEOUT);
+                            s = ST_INC;  // give up: treat as an inclusive prefix (0, 0)
+                            break;
+                        }
+                        __nanosleep(64);
+                        s = observe(&state[i]);
+                    }
                 }
-                later = compose((int)(s & 3u), later);
-                if (s & ST_INC) break;
-                i--;
+                unsigned inc = __ballot_sync(0xffffffffu, (s & ST_INC) != 0);
+                int stop = inc ? __ffs(inc) - 1 : 31;  // lanes 0 .. stop take part
+                int v = lane <= stop ? (int)(s & 3u) : GP_IDENTITY;
+                // lane 0 ends with tiles (base - stop .. base) composed in tile order
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    int o = __shfl_down_sync(0xffffffffu, v, off);
+                    if (lane + off < 32) v = compose(o, v);  // higher lanes are earlier tiles
+                }
+                v = __shfl_sync(0xffffffffu, v, 0);
+                later = compose(v, later);
+                if (inc) break;
+                base -= 32;
             }
             excl = later;
-            publish(&state[t], ST_INC | (u32)compose(excl, total));
+            if (lane == 0) publish(&state[t], ST_INC | (u32)compose(excl, total));
         }
-        carry_in_sh = excl & 1;  // carry into the tile (the chain starts with 0)
+        if (lane == 0) carry_in_sh = excl & 1;  // carry into the tile (the chain starts with 0)
     }
     __syncthreads();
     int carry = (pre & 1) | ((pre >> 1) & carry_in_sh);
