@@ -17,7 +17,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -154,9 +153,67 @@ def load_peaks():
     try:
         with open(path) as f:
             pk = json.load(f)
-        return float(pk["hbm_gbs"]), "measured"
+        return float(pk["hbm_gbs"]), float(pk.get("sm_max_mhz", 2070.0)), "measured"
     except (OSError, KeyError, ValueError):
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
+
+
+# Integer ALU-pipe peak: 152 SMs x 64 lanes (the ALU pipe accepts one warp
+# instruction every second cycle per scheduler) x the maximum SM clock.
+SMS, ALU_LANES_PER_SM = 152, 64
+
+# Cost model: int32 ALU-pipe instructions of the minimal exact sequences for
+# one Goldilocks operation (values kept in [0, p]): modular add = 64-bit add,
+# add of 2^64 mod p, select (6); modular sub = 64-bit sub, borrow-masked fix
+# (5); multiply by a constant 2^s = 96-bit shift + fold of the top word (its
+# product on the FMA pipe) + carry fix + canonical select (11); general
+# modmul = reduction of the 128-bit product (4 IMAD.WIDE on the FMA pipe,
+# not counted) (15).
+COST = {"add": 6, "sub": 5, "shl": 11, "mul": 15}
+
+
+def contig_ops_per_word(seed: bool) -> dict:
+    """Operation counts per transform word of the 4096-point tile transform
+    (64 x 64, each 64-point DFT as 8 x 8 with length-8 DFTs of 12 butterflies
+    and 5 root multiplies, 49 non-trivial middle roots, 3969 non-trivial
+    w_4096 twiddles per tile): seed = forward + scale by N^-1; fused =
+    forward + pointwise product + inverse."""
+    per64 = {"add": 192, "sub": 192, "shl": 16 * 5 + 49}
+    t = {k: 128 * v / 4096 for k, v in per64.items()}
+    t["mul"] = 3969 / 4096
+    if seed:
+        return {"add": t["add"], "sub": t["sub"], "shl": t["shl"], "mul": t["mul"] + 1}
+    return {"add": 2 * t["add"], "sub": 2 * t["sub"], "shl": 2 * t["shl"], "mul": 2 * t["mul"] + 1}
+
+
+def alu_ops(name: str, N: int):
+    if name == "ntt_contig_fused":
+        ops = contig_ops_per_word(False)
+    elif name == "ntt_contig_seed":
+        ops = contig_ops_per_word(True)
+    else:
+        return None
+    return N * sum(COST[k] * v for k, v in ops.items())
+
+
+# DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
+# launch at n = 10^8), valid only for the kernel sources it was taken on.
+TRAFFIC = {"kernel": "ntt_contig_fused", "bytes": 261.7e6, "src_sha": "4eb4ea51b737d155",
+           "profile": "profiles/k_contig_fused_n1e8.md"}
+
+
+def kernel_src_sha() -> str:
+    import glob
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_1910_04429_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu"))) + sorted(glob.glob(os.path.join(csrc, "*.cuh"))) \
+        + sorted(glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def kernel_bytes(name: str, n: int, m: int, N: int) -> float:
@@ -173,10 +230,21 @@ def kernel_bytes(name: str, n: int, m: int, N: int) -> float:
         "ntt_contig_fused": 3 * N * w,                        # x tile, a spectrum in; product out
         "ntt_inv_strided_r64": 2 * N * w,
         "ntt_inv_strided_last": N * w + L * w,                # only digits k < L written
-        "carry_tiles": L * w + Ly * w,
-        "carry_scan": 0,
-        "carry_out": L * w + Ly * w + Mo * w,
+        "carry_lookback": L * w + Ly * w + Mo * w,
     }.get(name, 0.0)
+
+
+def transform_length(n: int) -> int:
+    """The transform length the library picks: smallest 2^k or 3 * 2^k (first
+    radix <= 48) covering 2 ceil(n/16) - 1 words, at least 4096."""
+    need = 2 * ((n + 15) // 16) - 1
+    k = 12
+    while (1 << k) < need:
+        k += 1
+    for j in range(12, k):
+        if need <= (3 << j) < (1 << k) and (j - 12) % 6 <= 4:
+            return 3 << j
+    return 1 << k
 
 
 def run_ours(args, rank, world, local):
@@ -485,21 +553,37 @@ def main():
     ms_step = res["ms_total"] / K
     value = aggregate_mbps(world, K, n, res["ms_total"])
     e2e_value = aggregate_mbps(world, 1, n, res["e2e_ms"])
-    N = 1 << max(12, math.ceil(math.log2(2 * ((n + 15) // 16) - 1)))
 
+    N = transform_length(n)
     roofline = None
     launches = None
     if res["kstats"]:
         launches = sum(v[0] for v in res["kstats"].values())
-        top = max(res["kstats"].items(), key=lambda kv: kv[1][1])
-        name, (cnt, tot_ms) = top
-        per_launch_ms = tot_ms / cnt
-        peak, src = load_peaks()
-        achieved = kernel_bytes(name, n, m, N) / (per_launch_ms / 1e3) / 1e9
-        roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                    "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": None, "launch_ms": round(per_launch_ms, 4),
-                    "share": round(tot_ms / sum(v[1] for v in res["kstats"].values()), 3)}
+        total_ms = sum(v[1] for v in res["kstats"].values())
+        name, (cnt, tot_ms) = max(res["kstats"].items(), key=lambda kv: kv[1][1])
+        per_launch_s = tot_ms / cnt / 1e3
+        hbm_peak, mhz, src = load_peaks()
+        alu_peak = SMS * ALU_LANES_PER_SM * mhz * 1e6 / 1e12   # T int ops / s
+        ops = alu_ops(name, N)
+        hbm_achieved = kernel_bytes(name, n, m, N) / per_launch_s / 1e9
+        traffic = None
+        if TRAFFIC["kernel"] == name and TRAFFIC["src_sha"] == kernel_src_sha():
+            traffic = TRAFFIC["bytes"]
+        roofline = {"kernel": name, "share": round(tot_ms / total_ms, 3),
+                    "launch_ms": round(per_launch_s * 1e3, 4), "traffic": traffic,
+                    "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                            "frac": round(hbm_achieved / hbm_peak, 4), "peak_source": src}}
+        if ops is not None:
+            achieved = ops / per_launch_s / 1e12
+            roofline.update({"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
+                             "unit": "Tops/s", "frac": round(achieved / alu_peak, 4),
+                             "peak_source": f"derived: {SMS} SMs x {ALU_LANES_PER_SM} int32 ALU lanes x "
+                                            f"{mhz:.0f} MHz ({src} max clock)",
+                             "ops_model": "ALU-pipe int32 ops: add 6, sub 5, shift-multiply 11, "
+                                          "modmul 15 per Goldilocks operation"})
+        else:
+            roofline.update({"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak,
+                             "unit": "GB/s", "frac": round(hbm_achieved / hbm_peak, 4)})
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
