@@ -109,6 +109,46 @@ struct Strided {
             sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
     }
 
+    // fwd_a reading the tile from a [R][C] staging copy: words, or (PACK) 16-bit
+    // digits already zero past the last live digit
+    template <bool PACK>
+    static GL_HD void fwd_a_staged(const StridedGeom& g, const TilePos& tp, int it, const u64* st64,
+                                   const uint16_t* st16, const Digits& dig, u64* sm) {
+        int j0 = it / C, c = it % C;
+        u64 v[RB];
+#pragma unroll
+        for (int j1 = 0; j1 < RB; j1++) {
+            int d = j0 + RA * j1;
+            if (PACK) {
+                uint16_t x = st16[d * C + c];
+                if (tp.base + c + g.S * (u64)d == dig.L - 1) x &= dig.top_mask;
+                v[j1] = x;
+            } else {
+                v[j1] = st64[d * C + c];
+            }
+        }
+        gl::dft<RB, false>(v);
+#pragma unroll
+        for (int kr = 0; kr < RB; kr++)
+            sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
+    }
+
+    // inv_b reading the tile from a [R][C] staging copy of words
+    static GL_HD void inv_b_staged(const StridedGeom& g, const TilePos& tp, int it, const u64* st64,
+                                   u64* sm, const Twiddles& tw) {
+        int kr = it / C, c = it % C;
+        u64 w[RA];
+        u64 e = (g.N / g.M) * (tp.jl0 + c);
+#pragma unroll
+        for (int ks = 0; ks < RA; ks++) {
+            int k = RB * ks + kr;
+            w[ks] = gl::mul(st64[k * C + c], omega_n<true>(tw, e * (u64)k));
+        }
+        gl::dft<RA, true>(w);
+#pragma unroll
+        for (int j0 = 0; j0 < RA; j0++) sm[(kr * RA + j0) * C + c] = w[j0];
+    }
+
     // inter-pass twiddles w_M^(jl k) of one phase-B item, k = RB ks + kr
     static GL_HD void twiddles(const StridedGeom& g, const TilePos& tp, int it, const Twiddles& tw,
                                u64* w) {

@@ -5,19 +5,81 @@
 // Every kernel serves a batch of independent blocks that share one transform
 // geometry: blockIdx.x is the tile, blockIdx.y the block, and the per-block
 // buffers and digit sources arrive in a __grid_constant__ parameter array.
+#include <mutex>
+#include <unordered_set>
+
 #include "pa_internal.h"
 
 namespace pa {
 
+// ---------------------------------------------------------------------------
+// asynchronous staging of tile inputs (cp.async, 16-byte chunks)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Words of a tile (R rows at stride S, C columns) into stage[d * C + c]. Tile
+// bases and strides are even, so every 16-byte chunk is aligned.
+template <int R, int C>
+__device__ __forceinline__ void stage_words(u64* stage, const u64* buf, const StridedGeom& g,
+                                            const TilePos& tp) {
+    constexpr int CH = R * C / 2;
+    for (int ch = threadIdx.x; ch < CH; ch += NT) {
+        int d = ch / (C / 2), c = (ch % (C / 2)) * 2;
+        cp_async16(stage + d * C + c, buf + tp.base + c + g.S * (u64)d, 16);
+    }
+}
+
+// 16-bit digits of a tile into stage[d * C + c]; digits at positions >= L are
+// zero-filled by the copy (and never read from memory). The caller checks
+// that the digit source is 16-byte aligned.
+template <int R, int C>
+__device__ __forceinline__ void stage_digits(uint16_t* stage, const Digits& dig, const StridedGeom& g,
+                                             const TilePos& tp) {
+    constexpr int CH = R * C / 8;
+    for (int ch = threadIdx.x; ch < CH; ch += NT) {
+        int d = ch / (C / 8), c = (ch % (C / 8)) * 8;
+        u64 pos = tp.base + c + g.S * (u64)d;
+        u64 live = pos < dig.L ? dig.L - pos : 0;
+        int n = live >= 8 ? 8 : (int)live;
+        cp_async16(stage + d * C + c, n ? dig.src + pos : dig.src, 2 * n);
+    }
+}
+
+template <int R, int C, bool PACK>
+struct StageSize {
+    static constexpr int WORDS = PACK ? R * C / 4 : R * C;  // one staged tile, in 8-byte words
+    static constexpr size_t BYTES = (size_t)(TILE + 2 * WORDS) * sizeof(u64);
+};
+
 // Strided pass over one tile of both operands: the twiddles computed for x
-// are kept in registers and reused for a.
-template <int RA, int RB, int C, bool PACK, int B>
+// are kept in registers and reused for a. STAGED: both operands' tiles are
+// copied into shared memory asynchronously first, so a's loads overlap x's
+// arithmetic.
+template <int RA, int RB, int C, bool PACK, int B, bool STAGED>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     using S = Strided<RA, RB, C>;
-    __shared__ u64 sm[TILE];
+    using SZ = StageSize<S::R, C, PACK>;
+    extern __shared__ __align__(16) u64 dsm[];
+    u64* sm = dsm;
+    u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
     const BlockIO& io = nb.io[blockIdx.y];
     TilePos tp = S::tile(g, blockIdx.x);
+    if (STAGED) {
+#pragma unroll
+        for (int op = 0; op < 2; op++) {
+            if (PACK) stage_digits<S::R, C>((uint16_t*)st[op], op ? io.da : io.dx, g, tp);
+            else stage_words<S::R, C>(st[op], op ? io.buf_a : io.buf_x, g, tp);
+            cp_async_commit();
+        }
+    }
     u64 w[S::ITEMS_B][RA];
 #pragma unroll
     for (int i = 0; i < S::ITEMS_B; i++) {
@@ -28,11 +90,20 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     for (int op = 0; op < 2; op++) {
         u64* buf = op ? io.buf_a : io.buf_x;
         const Digits& d = op ? io.da : io.dx;
-        if (op) __syncthreads();  // the tile of x is out of shared memory
+        if (STAGED) {
+            if (op) cp_async_wait<0>();
+            else cp_async_wait<1>();
+        }
+        __syncthreads();  // staged tile complete; the previous tile is out of sm
 #pragma unroll
         for (int i = 0; i < S::ITEMS_A; i++) {
             int it = threadIdx.x + i * NT;
-            if (S::NA % NT == 0 || it < S::NA) S::template fwd_a<PACK>(g, tp, it, buf, d, sm);
+            if (S::NA % NT == 0 || it < S::NA) {
+                if (STAGED)
+                    S::template fwd_a_staged<PACK>(g, tp, it, st[op], (const uint16_t*)st[op], d, sm);
+                else
+                    S::template fwd_a<PACK>(g, tp, it, buf, d, sm);
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -43,24 +114,41 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     }
 }
 
+// Inverse strided pass over two adjacent tiles of x per CTA, both staged
+// asynchronously up front so the second tile's loads overlap the first's
+// arithmetic.
 template <int RA, int RB, int C, bool LAST, int B>
 __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     using S = Strided<RA, RB, C>;
-    __shared__ u64 sm[TILE];
+    using SZ = StageSize<S::R, C, false>;
+    extern __shared__ __align__(16) u64 dsm[];
+    u64* sm = dsm;
+    u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
     const BlockIO& io = nb.io[blockIdx.y];
-    TilePos tp = S::tile(g, blockIdx.x);
+    TilePos tp[2] = {S::tile(g, 2 * (u64)blockIdx.x), S::tile(g, 2 * (u64)blockIdx.x + 1)};
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_B; i++) {
-        int it = threadIdx.x + i * NT;
-        if (S::NB % NT == 0 || it < S::NB) S::inv_b(g, tp, it, io.buf_x, sm, tw);
+    for (int h = 0; h < 2; h++) {
+        stage_words<S::R, C>(st[h], io.buf_x, g, tp[h]);
+        cp_async_commit();
     }
-    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_A; i++) {
-        int it = threadIdx.x + i * NT;
-        if (S::NA % NT == 0 || it < S::NA)
-            S::template inv_a<LAST>(g, tp, it, io.buf_x, sm, io.L);
+    for (int h = 0; h < 2; h++) {
+        if (h) cp_async_wait<0>();
+        else cp_async_wait<1>();
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < S::ITEMS_B; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NB % NT == 0 || it < S::NB) S::inv_b_staged(g, tp[h], it, st[h], sm, tw);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < S::ITEMS_A; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NA % NT == 0 || it < S::NA)
+                S::template inv_a<LAST>(g, tp[h], it, io.buf_x, sm, io.L);
+        }
     }
 }
 
@@ -149,28 +237,52 @@ int strided_columns(int R) {
     return 0;
 }
 
+// Opt a kernel into the dynamic shared memory it needs (once per kernel).
+template <typename K>
+static void allow_smem(K kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_set<const void*> done;
+    if (bytes <= 48 * 1024) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.insert((const void*)kernel).second)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <int B>
 struct Launcher {
     const StridedGeom* g;
     const NttBatch<B>* nb;
     const Twiddles* tw;
     cudaStream_t st;
+    bool stage_digits_ok;  // every digit source 16-byte aligned
 
+    template <int RA, int RB, int C, bool PACK, bool STAGED>
+    void fwd_k() const {
+        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
+        size_t smem = STAGED ? StageSize<RA * RB, C, PACK>::BYTES : TILE * sizeof(u64);
+        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED>;
+        allow_smem(k, smem);
+        k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+    }
     template <int RA, int RB, int C>
     void fwd(bool pack) const {
-        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
-        if (pack)
-            k_fwd_strided<RA, RB, C, true, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
-        else
-            k_fwd_strided<RA, RB, C, false, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
+        if (!pack) return fwd_k<RA, RB, C, false, true>();
+        if (stage_digits_ok) return fwd_k<RA, RB, C, true, true>();
+        fwd_k<RA, RB, C, true, false>();
     }
     template <int RA, int RB, int C>
     void inv(bool last) const {
-        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
-        if (last)
-            k_inv_strided<RA, RB, C, true, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
-        else
-            k_inv_strided<RA, RB, C, false, B><<<grid, NT, 0, st>>>(*g, *nb, *tw);
+        dim3 grid((unsigned)(g->N / (RA * RB * C) / 2), (unsigned)nb->count);
+        size_t smem = StageSize<RA * RB, C, false>::BYTES;
+        if (last) {
+            auto k = k_inv_strided<RA, RB, C, true, B>;
+            allow_smem(k, smem);
+            k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+        } else {
+            auto k = k_inv_strided<RA, RB, C, false, B>;
+            allow_smem(k, smem);
+            k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+        }
     }
     void dispatch_fwd(int R, bool pack) const {
 #define PA_FWD(r, a, b, c) if (R == r) return fwd<a, b, c>(pack);
@@ -194,10 +306,13 @@ static StridedGeom strided_geom(const Geom& G, int p) {
 template <int B>
 static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatch<B>& nb,
                                 cudaStream_t st) {
+    bool aligned = true;
+    for (int i = 0; i < nb.count; i++)
+        aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0);
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st}.dispatch_fwd(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &nb, &tw, st, aligned}.dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }
     dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
@@ -218,7 +333,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st}.dispatch_inv(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &nb, &tw, st, aligned}.dispatch_inv(G.pass[p].R, p == 0);
         prof_end(st);
     }
     return cudaGetLastError();
