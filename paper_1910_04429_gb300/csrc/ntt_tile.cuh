@@ -133,17 +133,22 @@ struct Strided {
             sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
     }
 
-    // inv_b reading the tile from a [R][C] staging copy of words
-    static GL_HD void inv_b_staged(const StridedGeom& g, const TilePos& tp, int it, const u64* st64,
-                                   u64* sm, const Twiddles& tw) {
+    // inverse inter-pass twiddles w_M^-(jl k) of one phase-B item, k = RB ks + kr
+    static GL_HD void inv_twiddles(const StridedGeom& g, const TilePos& tp, int it, const Twiddles& tw,
+                                   u64* w) {
         int kr = it / C, c = it % C;
-        u64 w[RA];
         u64 e = (g.N / g.M) * (tp.jl0 + c);
 #pragma unroll
-        for (int ks = 0; ks < RA; ks++) {
-            int k = RB * ks + kr;
-            w[ks] = gl::mul(st64[k * C + c], omega_n<true>(tw, e * (u64)k));
-        }
+        for (int ks = 0; ks < RA; ks++) w[ks] = omega_n<true>(tw, e * (u64)(RB * ks + kr));
+    }
+
+    // inv_b reading the tile from a [R][C] staging copy, with its twiddles given
+    static GL_HD void inv_b_staged(const StridedGeom& g, const TilePos& tp, int it, const u64* st64,
+                                   u64* sm, const u64* tws) {
+        int kr = it / C, c = it % C;
+        u64 w[RA];
+#pragma unroll
+        for (int ks = 0; ks < RA; ks++) w[ks] = gl::mul(st64[(RB * ks + kr) * C + c], tws[ks]);
         gl::dft<RA, true>(w);
 #pragma unroll
         for (int j0 = 0; j0 < RA; j0++) sm[(kr * RA + j0) * C + c] = w[j0];

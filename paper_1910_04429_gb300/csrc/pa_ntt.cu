@@ -114,41 +114,37 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     }
 }
 
-// Inverse strided pass over two adjacent tiles of x per CTA, both staged
-// asynchronously up front so the second tile's loads overlap the first's
-// arithmetic.
+// Inverse strided pass over one tile: the tile is copied into shared memory
+// asynchronously while the inverse twiddles are computed.
 template <int RA, int RB, int C, bool LAST, int B>
 __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     using S = Strided<RA, RB, C>;
-    using SZ = StageSize<S::R, C, false>;
     extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
-    u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
+    u64* st = dsm + TILE;
     const BlockIO& io = nb.io[blockIdx.y];
-    TilePos tp[2] = {S::tile(g, 2 * (u64)blockIdx.x), S::tile(g, 2 * (u64)blockIdx.x + 1)};
+    TilePos tp = S::tile(g, blockIdx.x);
+    stage_words<S::R, C>(st, io.buf_x, g, tp);
+    cp_async_commit();
+    u64 w[S::ITEMS_B][RA];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        stage_words<S::R, C>(st[h], io.buf_x, g, tp[h]);
-        cp_async_commit();
+    for (int i = 0; i < S::ITEMS_B; i++) {
+        int it = threadIdx.x + i * NT;
+        if (S::NB % NT == 0 || it < S::NB) S::inv_twiddles(g, tp, it, tw, w[i]);
     }
+    cp_async_wait<0>();
+    __syncthreads();
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        if (h) cp_async_wait<0>();
-        else cp_async_wait<1>();
-        __syncthreads();
+    for (int i = 0; i < S::ITEMS_B; i++) {
+        int it = threadIdx.x + i * NT;
+        if (S::NB % NT == 0 || it < S::NB) S::inv_b_staged(g, tp, it, st, sm, w[i]);
+    }
+    __syncthreads();
 #pragma unroll
-        for (int i = 0; i < S::ITEMS_B; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NB % NT == 0 || it < S::NB) S::inv_b_staged(g, tp[h], it, st[h], sm, tw);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < S::ITEMS_A; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NA % NT == 0 || it < S::NA)
-                S::template inv_a<LAST>(g, tp[h], it, io.buf_x, sm, io.L);
-        }
+    for (int i = 0; i < S::ITEMS_A; i++) {
+        int it = threadIdx.x + i * NT;
+        if (S::NA % NT == 0 || it < S::NA) S::template inv_a<LAST>(g, tp, it, io.buf_x, sm, io.L);
     }
 }
 
@@ -272,8 +268,8 @@ struct Launcher {
     }
     template <int RA, int RB, int C>
     void inv(bool last) const {
-        dim3 grid((unsigned)(g->N / (RA * RB * C) / 2), (unsigned)nb->count);
-        size_t smem = StageSize<RA * RB, C, false>::BYTES;
+        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
+        size_t smem = (TILE + RA * RB * C) * sizeof(u64);
         if (last) {
             auto k = k_inv_strided<RA, RB, C, true, B>;
             allow_smem(k, smem);
