@@ -106,6 +106,25 @@ int pa_convolve16(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint6
 int pa_carry_extract(const uint64_t* coef, uint64_t L, const uint64_t* seed_b, uint64_t n,
                      uint64_t m, uint64_t* out, void* stream);
 
+/*
+ * Seed reuse. Alice and Bob apply the same publicly chosen g = g_{c,d} to their
+ * strings X and X' (Sec. 2.2), and a system may keep one seed for several
+ * blocks of the same length: the transform of c can then be computed once.
+ * pa_seed_create transforms seed_a (device, ceil(n/64) limbs, read during the
+ * call's stream work only) into a handle that owns its spectrum (one
+ * transform of N words, allocated with cudaMalloc, synchronous). It queues the
+ * transform on `stream`; later calls that use the handle on other streams must
+ * be ordered after it. pa_hash_seeded(seed, key, seed_b, m, out, stream) then
+ * equals pa_hash(key, seed_a, seed_b, n, m, out, stream) for the handle's n
+ * and skips the seed's transform. pa_seed_destroy frees the handle; no work
+ * that uses it may be in flight.
+ */
+typedef struct pa_seed_s* pa_seed;
+int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* out);
+int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, uint64_t m,
+                   uint64_t* out, void* stream);
+int pa_seed_destroy(pa_seed seed);
+
 /* One hash problem for the batched call (all pointers device pointers). */
 typedef struct {
     const uint64_t* key;

@@ -25,6 +25,10 @@ _lib = None
 _SIGS = {
     "pa_hash": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_hash_noalloc": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_seed_create": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+                       ctypes.c_int),
+    "pa_hash_seeded": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_seed_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
@@ -159,6 +163,32 @@ def hash_noalloc(key, seed_a, seed_b, n: int, m: int, out=None, stream=None):
     _check(load().pa_hash_noalloc(*args, n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)),
            "pa_hash_noalloc")
     return out
+
+
+class Seed:
+    """A seed whose transform is computed once (pa_seed_create); hash keys of
+    the same length against it with ``hash``. Free with ``close``."""
+
+    def __init__(self, seed_a, n: int, stream=None):
+        h = ctypes.c_void_p(0)
+        _check(load().pa_seed_create(_dev_ptr(seed_a, limbs(n), "seed_a"), n, _stream_ptr(stream),
+                                     ctypes.byref(h)), "pa_seed_create")
+        self.handle, self.n = h, n
+
+    def hash(self, key, seed_b, m: int, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(limbs(m), dtype=torch.int64, device=key.device)
+        _check(load().pa_hash_seeded(self.handle, _dev_ptr(key, limbs(self.n), "key"),
+                                     _dev_ptr(seed_b, limbs(self.n), "seed_b"), m,
+                                     _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)), "pa_hash_seeded")
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(load().pa_seed_destroy(self.handle), "pa_seed_destroy")
+            self.handle = None
 
 
 def hash_host(key: np.ndarray, seed_a: np.ndarray, seed_b: np.ndarray, n: int, m: int,

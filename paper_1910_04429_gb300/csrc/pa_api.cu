@@ -406,6 +406,80 @@ int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream) {
     return hash_batch_device(blocks, count, (cudaStream_t)stream, dev, pool);
 }
 
+}  // extern "C"
+
+struct pa_seed_s {
+    int dev;
+    uint64_t n;
+    Geom G;
+    u64* spec;  // the seed's spectrum, N words (tile register order, times N^-1)
+};
+
+extern "C" {
+
+int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* out) {
+    if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_seed_create: need 1 <= n <= PA_MAX_BITS");
+    if (!seed_a || !out) return fail(PA_EINVAL, "pa_seed_create: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    NttJob j;
+    j.geom = geom_for_bits(n);
+    j.L = (n + 15) / 16;
+    if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+    u64* spec = nullptr;
+    cudaError_t e = cudaMalloc(&spec, j.geom.N * sizeof(u64));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(seed spectrum)");
+    j.buf_x = j.buf_a = j.ahat = spec;
+    j.da = j.dx = Digits{reinterpret_cast<const uint16_t*>(seed_a), j.L, top_digit_mask(n)};
+    if ((e = launch_seed_spectrum(j, (cudaStream_t)stream)) != cudaSuccess) {
+        cudaFree(spec);
+        return cuda_fail(e, "seed transform launch");
+    }
+    *out = new pa_seed_s{dev, n, j.geom, spec};
+    return PA_OK;
+}
+
+int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, uint64_t m,
+                   uint64_t* out, void* stream) {
+    if (!seed || !key || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_seeded: null pointer");
+    if (m < 1 || m > seed->n) return fail(PA_EINVAL, "pa_hash_seeded: need 1 <= m <= n");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    if (dev != seed->dev) return fail(PA_EINVAL, "pa_hash_seeded: seed made on another device");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch scr(st, pool);
+    NttJob j;
+    j.geom = seed->G;
+    j.L = (seed->n + 15) / 16;
+    if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+    void* bx;
+    if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
+    j.buf_x = (u64*)bx;
+    j.buf_a = j.ahat = seed->spec;
+    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top_digit_mask(seed->n)};
+    j.da = j.dx;
+    cudaError_t e = launch_convolution_seeded(j, st);
+    if (e != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
+    return queue_carry(j.buf_x, j.L, seed_b, seed->n, m, out, st, scr);
+}
+
+int pa_seed_destroy(pa_seed seed) {
+    if (!seed) return PA_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(seed->dev);
+    cudaError_t e = cudaFree(seed->spec);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete seed;
+    return e == cudaSuccess ? PA_OK : cuda_fail(e, "cudaFree(seed spectrum)");
+}
+
 int pa_prepare(uint64_t n) {
     if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_prepare: need 1 <= n <= PA_MAX_BITS");
     std::lock_guard<std::mutex> lk(g_mu);

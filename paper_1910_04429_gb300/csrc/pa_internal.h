@@ -24,6 +24,10 @@ struct NttJob {
 // (ahat must equal buf_a: the seed's spectrum is written over its buffer.)
 cudaError_t launch_convolution(const NttJob& job, cudaStream_t st);
 
+// Seed reuse: a's spectrum alone into buf_a; then x's transform against it.
+cudaError_t launch_seed_spectrum(const NttJob& job, cudaStream_t st);
+cudaError_t launch_convolution_seeded(const NttJob& job, cudaStream_t st);
+
 // One block of a batch of transforms that share a geometry.
 struct BlockIO {
     u64* buf_x;   // N words: x, then the product digits

@@ -58,11 +58,11 @@ struct StageSize {
     static constexpr size_t BYTES = (size_t)(TILE + 2 * WORDS) * sizeof(u64);
 };
 
-// Strided pass over one tile of both operands: the twiddles computed for x
-// are kept in registers and reused for a. STAGED: both operands' tiles are
-// copied into shared memory asynchronously first, so a's loads overlap x's
-// arithmetic.
-template <int RA, int RB, int C, bool PACK, int B, bool STAGED>
+// Strided pass over one tile of both operands (OPS = 2: x and a; OPS = 1: x
+// only, when a's spectrum is reused): the twiddles computed for x are kept in
+// registers and reused for a. STAGED: the operands' tiles are copied into
+// shared memory asynchronously first, so a's loads overlap x's arithmetic.
+template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     using S = Strided<RA, RB, C>;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     TilePos tp = S::tile(g, blockIdx.x);
     if (STAGED) {
 #pragma unroll
-        for (int op = 0; op < 2; op++) {
+        for (int op = 0; op < OPS; op++) {
             if (PACK) stage_digits<S::R, C>((uint16_t*)st[op], op ? io.da : io.dx, g, tp);
             else stage_words<S::R, C>(st[op], op ? io.buf_a : io.buf_x, g, tp);
             cp_async_commit();
@@ -87,11 +87,11 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
         if (S::NB % NT == 0 || it < S::NB) S::twiddles(g, tp, it, tw, w[i]);
     }
 #pragma unroll
-    for (int op = 0; op < 2; op++) {
+    for (int op = 0; op < OPS; op++) {
         u64* buf = op ? io.buf_a : io.buf_x;
         const Digits& d = op ? io.da : io.dx;
         if (STAGED) {
-            if (op) cp_async_wait<0>();
+            if (op || OPS == 1) cp_async_wait<0>();
             else cp_async_wait<1>();
         }
         __syncthreads();  // staged tile complete; the previous tile is out of sm
@@ -252,19 +252,26 @@ struct Launcher {
     cudaStream_t st;
     bool stage_digits_ok;  // every digit source 16-byte aligned
 
-    template <int RA, int RB, int C, bool PACK, bool STAGED>
+    int ops;               // 2: transform x and a; 1: x only (a's spectrum reused)
+
+    template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS>
     void fwd_k() const {
         dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
         size_t smem = STAGED ? StageSize<RA * RB, C, PACK>::BYTES : TILE * sizeof(u64);
-        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED>;
+        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS>;
         allow_smem(k, smem);
         k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
     }
+    template <int RA, int RB, int C, int OPS>
+    void fwd_ops(bool pack) const {
+        if (!pack) return fwd_k<RA, RB, C, false, true, OPS>();
+        if (stage_digits_ok) return fwd_k<RA, RB, C, true, true, OPS>();
+        fwd_k<RA, RB, C, true, false, OPS>();
+    }
     template <int RA, int RB, int C>
     void fwd(bool pack) const {
-        if (!pack) return fwd_k<RA, RB, C, false, true>();
-        if (stage_digits_ok) return fwd_k<RA, RB, C, true, true>();
-        fwd_k<RA, RB, C, true, false>();
+        if (ops == 1) return fwd_ops<RA, RB, C, 1>(pack);
+        fwd_ops<RA, RB, C, 2>(pack);
     }
     template <int RA, int RB, int C>
     void inv(bool last) const {
@@ -299,27 +306,31 @@ static StridedGeom strided_geom(const Geom& G, int p) {
     return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, log_tpb};
 }
 
+// ops = 2: transform x and a and build a's spectrum; ops = 1: x only, each
+// block's buf_a already holds a's spectrum (tile register order, times N^-1).
 template <int B>
 static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatch<B>& nb,
-                                cudaStream_t st) {
+                                cudaStream_t st, int ops = 2) {
     bool aligned = true;
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0);
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned}.dispatch_fwd(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &nb, &tw, st, aligned, ops}.dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }
     dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
     bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
     u64 ninv = n_inverse(G.logN, G.three);
-    prof_begin(st, "ntt_contig_seed");
-    if (pack)
-        k_contig_seed<true, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
-    else
-        k_contig_seed<false, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
-    prof_end(st);
+    if (ops == 2) {
+        prof_begin(st, "ntt_contig_seed");
+        if (pack)
+            k_contig_seed<true, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
+        else
+            k_contig_seed<false, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
+        prof_end(st);
+    }
     prof_begin(st, "ntt_contig_fused");
     if (pack)
         k_contig_fused<true, B><<<tiles, NT, 0, st>>>(nb, tw);
@@ -329,7 +340,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned}.dispatch_inv(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &nb, &tw, st, aligned, ops}.dispatch_inv(G.pass[p].R, p == 0);
         prof_end(st);
     }
     return cudaGetLastError();
@@ -340,6 +351,39 @@ cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
     nb.count = 1;
     nb.io[0] = BlockIO{j.buf_x, j.buf_a, j.dx, j.da, j.L};
     return launch_batch<1>(j.geom, j.tw, nb, st);
+}
+
+// Forward transform of a alone into buf_a (its spectrum, register order, x N^-1):
+// the strided passes run with x = a (the x half of each CTA is skipped by
+// pointing both halves at a and running ops = 1 on buf_a), then contig_seed.
+cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
+    NttBatch<1> nb;
+    nb.count = 1;
+    nb.io[0] = BlockIO{j.buf_a, j.buf_a, j.da, j.da, j.L};
+    bool aligned = (uintptr_t)j.da.src % 16 == 0;
+    const Geom& G = j.geom;
+    for (int p = 0; p < G.nstrided; p++) {
+        StridedGeom g = strided_geom(G, p);
+        prof_begin(st, "ntt_seed_strided");
+        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1}.dispatch_fwd(G.pass[p].R, p == 0);
+        prof_end(st);
+    }
+    dim3 tiles((unsigned)(G.N / TILE), 1);
+    prof_begin(st, "ntt_contig_seed");
+    if (G.nstrided == 0)
+        k_contig_seed<true, 1><<<tiles, NT, 0, st>>>(nb, n_inverse(G.logN, G.three), j.tw);
+    else
+        k_contig_seed<false, 1><<<tiles, NT, 0, st>>>(nb, n_inverse(G.logN, G.three), j.tw);
+    prof_end(st);
+    return cudaGetLastError();
+}
+
+// x's transform, product with the stored spectrum in buf_a, inverse.
+cudaError_t launch_convolution_seeded(const NttJob& j, cudaStream_t st) {
+    NttBatch<1> nb;
+    nb.count = 1;
+    nb.io[0] = BlockIO{j.buf_x, j.buf_a, j.dx, j.da, j.L};
+    return launch_batch<1>(j.geom, j.tw, nb, st, 1);
 }
 
 cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const BlockIO* io,

@@ -99,6 +99,11 @@ def test_argument_checks_without_gpu():
     assert b"block 1" in lib.pa_last_error()
     assert lib.pa_prepare(0) == binding.PA_EINVAL
     assert lib.pa_fault_inject(99) == binding.PA_EINVAL
+    h = ctypes.c_void_p(0)
+    assert lib.pa_seed_create(null, 100, null, ctypes.byref(h)) == binding.PA_EINVAL
+    assert lib.pa_seed_create(p, 0, null, ctypes.byref(h)) == binding.PA_EINVAL
+    assert lib.pa_hash_seeded(null, p, p, 10, p, null) == binding.PA_EINVAL
+    assert lib.pa_seed_destroy(null) == binding.PA_OK
     # the fixed-scratch entry point refuses keys beyond its scratch size
     assert lib.pa_hash_noalloc(p, p, p, (1 << 20) + 1, 1, p, null) == binding.PA_EINVAL
     assert b"PA_NOALLOC_MAX_BITS" in lib.pa_last_error()
