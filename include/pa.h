@@ -74,11 +74,12 @@ int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
             uint64_t m, uint64_t* out, void* stream);
 
 /*
- * pa_hash_host: pa_hash on HOST buffers (same shapes). Copies the inputs to
- * the device, hashes, copies the result back and waits for the stream, so it
- * returns with `out` filled. Pinned host memory gives asynchronous copies;
- * pageable memory also works. Device staging buffers come from the library's
- * pool.
+ * pa_hash_host: pa_hash on HOST buffers (same shapes); returns with `out`
+ * filled (it waits for `stream`). If all four buffers are pinned (page-locked
+ * and mapped, e.g. cudaHostAlloc), the kernels read the key and seeds and
+ * write the result directly in host memory (over NVLink-C2C on Grace systems),
+ * with no staging copies; otherwise the inputs are copied to device staging
+ * buffers from the library's pool and the result is copied back.
  */
 int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
                  uint64_t n, uint64_t m, uint64_t* out, void* stream);

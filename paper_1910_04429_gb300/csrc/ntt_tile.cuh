@@ -53,6 +53,7 @@ struct Digits {
     const uint16_t* src;  // little-endian limbs viewed as 16-bit digits
     u64 L;                // live digits: ceil(n / 16)
     uint16_t top_mask;    // mask of digit L-1 (bits >= n cleared)
+    uint16_t sysmem;      // 1: src is host memory mapped into the device (read with plain loads)
 };
 
 GL_HD u64 digit_at(const Digits& d, u64 pos) {

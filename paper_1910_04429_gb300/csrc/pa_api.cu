@@ -111,8 +111,9 @@ uint16_t top_digit_mask(uint64_t n) {
 }
 
 // Queue steps 1-5 of Algorithm 1; on success *coef points at the digits (k < L).
+// sysmem: key and seed_a are host memory mapped into the device.
 int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, cudaStream_t st,
-                      Scratch& scr, int dev, u64** coef) {
+                      Scratch& scr, int dev, u64** coef, bool sysmem = false) {
     u64 L = (n + 15) / 16;
     NttJob j;
     j.geom = geom_for_bits(n);
@@ -126,8 +127,8 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
     j.buf_a = (u64*)ba;
     j.ahat = (u64*)ba;  // each tile is read completely before it is overwritten
     uint16_t top = top_digit_mask(n);
-    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top};
-    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top};
+    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top, (uint16_t)sysmem};
+    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top, (uint16_t)sysmem};
     cudaError_t e = launch_convolution(j, st);
     if (e != cudaSuccess) return cuda_fail(e, "NTT launch");
     *coef = j.buf_x;
@@ -146,10 +147,11 @@ int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint
 }
 
 int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
-                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool) {
+                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool,
+                bool sysmem = false) {
     Scratch scr(st, pool);
     u64* coef = nullptr;
-    int rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef);
+    int rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef, sysmem);
     if (rc) return rc;
     return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr);
 }
@@ -232,6 +234,18 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     if ((e = launch_carry_batch(cj.data(), (int)count, st)) != cudaSuccess)
         return cuda_fail(e, "batched carry launch");
     return PA_OK;
+}
+
+// Device address of pinned (page-locked, mapped) host memory, if p is such memory.
+bool host_mapped(const void* p, void** dptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dptr = a.devicePointer;
+    return true;
 }
 
 int setup(int* dev, cudaMemPool_t* pool) {
@@ -334,6 +348,16 @@ int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* se
         int dev;
         cudaMemPool_t pool;
         if ((rc = setup(&dev, &pool))) return rc;
+        // Pinned host buffers are mapped into the device (over NVLink-C2C on
+        // Grace systems): the kernels read the key and seeds and write the
+        // result in place, with no staging copies.
+        void *mx, *ma, *mb, *mo;
+        if (host_mapped(key, &mx) && host_mapped(seed_a, &ma) && host_mapped(seed_b, &mb) &&
+            host_mapped(out, &mo)) {
+            rc = hash_device((const u64*)mx, (const u64*)ma, (const u64*)mb, n, m, (u64*)mo, st, dev,
+                             pool, true);
+            if (rc) return rc;
+        } else {
         Scratch scr(st, pool);
         size_t in_bytes = ((n + 63) / 64) * sizeof(u64), out_bytes = ((m + 63) / 64) * sizeof(u64);
         void *dx, *da, *db, *dout;
@@ -350,6 +374,7 @@ int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* se
         if (rc) return rc;
         if ((e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+        }
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");

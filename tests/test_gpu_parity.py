@@ -166,6 +166,25 @@ def test_hash_host_buffers():
     np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("n,m", [(3_000_017, 800_001), (1000, 333), (100_000_000, 25_000_000)])
+def test_hash_host_pinned_zero_copy(n, m):
+    """Pinned host buffers: the kernels read and write host memory directly."""
+    import ctypes
+
+    import torch
+
+    blk = inputs.make_block(n, m, seed=13)
+    pins = [torch.from_numpy(v.view(np.int64)).pin_memory() for v in (blk.x, blk.a, blk.b)]
+    out = torch.full(((m + 63) // 64,), -1, dtype=torch.int64).pin_memory()
+    lib = binding.load()
+    ptr = [ctypes.c_void_p(t.data_ptr()) for t in pins]
+    for _ in range(2):
+        rc = lib.pa_hash_host(*ptr, n, m, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(0))
+        assert rc == binding.PA_OK, lib.pa_last_error()
+        want = oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads())
+        np.testing.assert_array_equal(out.numpy().view(np.uint64), want)
+
+
 def test_nondefault_streams_and_repeat():
     import torch
 
