@@ -75,11 +75,12 @@ int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
 
 /*
  * pa_hash_host: pa_hash on HOST buffers (same shapes); returns with `out`
- * filled (it waits for `stream`). If all four buffers are pinned (page-locked
- * and mapped, e.g. cudaHostAlloc), the kernels read the key and seeds and
- * write the result directly in host memory (over NVLink-C2C on Grace systems),
- * with no staging copies; otherwise the inputs are copied to device staging
- * buffers from the library's pool and the result is copied back.
+ * filled (it waits for `stream`). key and seed_a are copied to device staging
+ * buffers from the library's pool first; seed_b is copied on a second stream
+ * while the transforms run. If `out` is pinned (page-locked and mapped, e.g.
+ * cudaHostAlloc) the last kernel writes the result into it directly (over
+ * NVLink-C2C on Grace systems); otherwise it is copied back. Pinned inputs
+ * make the copies asynchronous; pageable memory also works.
  */
 int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
                  uint64_t n, uint64_t m, uint64_t* out, void* stream);

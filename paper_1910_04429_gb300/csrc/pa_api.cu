@@ -348,33 +348,30 @@ int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* se
         int dev;
         cudaMemPool_t pool;
         if ((rc = setup(&dev, &pool))) return rc;
-        // Pinned host buffers are mapped into the device (over NVLink-C2C on
-        // Grace systems): the kernels read the key and seeds and write the
-        // result in place, with no staging copies.
-        void *mx, *ma, *mb, *mo;
-        if (host_mapped(key, &mx) && host_mapped(seed_a, &ma) && host_mapped(seed_b, &mb) &&
-            host_mapped(out, &mo)) {
-            rc = hash_device((const u64*)mx, (const u64*)ma, (const u64*)mb, n, m, (u64*)mo, st, dev,
-                             pool, true);
-            if (rc) return rc;
-        } else {
+        if ((rc = side_streams(dev))) return rc;
+        Device& d = g_dev[dev];
         Scratch scr(st, pool);
         size_t in_bytes = ((n + 63) / 64) * sizeof(u64), out_bytes = ((m + 63) / 64) * sizeof(u64);
-        void *dx, *da, *db, *dout;
-        if ((rc = scr.get(in_bytes, &dx)) || (rc = scr.get(in_bytes, &da)) ||
-            (rc = scr.get(in_bytes, &db)) || (rc = scr.get(out_bytes, &dout)))
+        void *dx, *da, *db, *mo = nullptr;
+        if ((rc = scr.get(in_bytes, &dx)) || (rc = scr.get(in_bytes, &da)) || (rc = scr.get(in_bytes, &db)))
             return rc;
+        // a pinned result buffer is written in place by the carry kernel
+        bool out_mapped = host_mapped(out, &mo);
+        if (!out_mapped && (rc = scr.get(out_bytes, &mo))) return rc;
         cudaError_t e;
-        if ((e = cudaMemcpyAsync(dx, key, in_bytes, cudaMemcpyHostToDevice, st)) ||
+        // x and a first (the transforms need them); b on a side stream while they run
+        if ((e = cudaEventRecord(d.fork, st)) || (e = cudaStreamWaitEvent(d.side[0], d.fork, 0)) ||
+            (e = cudaMemcpyAsync(dx, key, in_bytes, cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(da, seed_a, in_bytes, cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(db, seed_b, in_bytes, cudaMemcpyHostToDevice, st)))
+            (e = cudaMemcpyAsync(db, seed_b, in_bytes, cudaMemcpyHostToDevice, d.side[0])) ||
+            (e = cudaEventRecord(d.join[0], d.side[0])))
             return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-        rc = hash_device((const u64*)dx, (const u64*)da, (const u64*)db, n, m, (u64*)dout, st, dev,
-                         pool);
-        if (rc) return rc;
-        if ((e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st)))
+        u64* coef = nullptr;
+        if ((rc = queue_convolution((const u64*)dx, (const u64*)da, n, st, scr, dev, &coef))) return rc;
+        if ((e = cudaStreamWaitEvent(st, d.join[0], 0))) return cuda_fail(e, "cudaStreamWaitEvent");
+        if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr))) return rc;
+        if (!out_mapped && (e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "cudaMemcpyAsync(D2H)");
-        }
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
