@@ -72,28 +72,46 @@ GL_HD u64 canon(u64 a) { return a == P ? 0 : a; }
 
 // (hi:lo) mod p for any 128-bit value, using 2^64 = EPS and 2^96 = -1;
 // result in [0, p).
-GL_HD u64 reduce128(u64 lo, u64 hi) {
 #if defined(__CUDA_ARCH__)
-    u32 h0 = (u32)hi, h1 = (u32)(hi >> 32);
-    u64 t, r, q;
-    u32 m, c, c2;
-    asm("sub.cc.u64 %0, %2, %3;\n\t"
-        "subc.u32 %1, 0, 0;"
-        : "=l"(t), "=r"(m)
-        : "l"(lo), "l"((u64)h1));
-    t -= (u64)m;                                   // lo - h1 (borrow of 2^64 = EPS)
-    u64 u;
-    asm("mul.wide.u32 %0, %1, 4294967295;" : "=l"(u) : "r"(h0));  // h0 * EPS
+// r - p when r >= p (r + EPS carries out exactly then); r < 2^64
+__device__ __forceinline__ u64 canon_lt2p(u64 r) {
+    u64 q;
+    u32 c;
+    asm("add.cc.u64 %0, %2, 4294967295;\n\t"
+        "addc.u32 %1, 0, 0;"
+        : "=l"(q), "=r"(c)
+        : "l"(r));
+    return c ? q : r;
+}
+
+// t + h0 * 2^64 (mod p) for t < 2^64 and h0 < 2^32, in [0, p): 2^64 = EPS,
+// the product h0 * EPS and the carry's EPS go through the multiplier (FMA pipe)
+__device__ __forceinline__ u64 fold_word(u64 t, u32 h0) {
+    u64 u, r;
+    u32 c;
+    asm("mul.wide.u32 %0, %1, 4294967295;" : "=l"(u) : "r"(h0));
     asm("add.cc.u64 %0, %2, %3;\n\t"
         "addc.u32 %1, 0, 0;"
         : "=l"(r), "=r"(c)
         : "l"(t), "l"(u));
-    r += (u64)(0u - c);                            // carry of 2^64 = EPS; cannot carry again
-    asm("add.cc.u64 %0, %2, 4294967295;\n\t"
-        "addc.u32 %1, 0, 0;"
-        : "=l"(q), "=r"(c2)
-        : "l"(r));
-    return c2 ? q : r;                             // r - p when r >= p
+    asm("mad.wide.u32 %0, %1, 4294967295, %0;" : "+l"(r) : "r"(c));  // carry of 2^64 = EPS
+    return canon_lt2p(r);
+}
+#endif
+
+// (hi:lo) mod p for any 128-bit value, using 2^64 = EPS and 2^96 = -1;
+// result in [0, p).
+GL_HD u64 reduce128(u64 lo, u64 hi) {
+#if defined(__CUDA_ARCH__)
+    u32 h0 = (u32)hi, h1 = (u32)(hi >> 32);
+    u64 t;
+    u32 m;
+    asm("sub.cc.u64 %0, %2, %3;\n\t"
+        "subc.u32 %1, 0, 0;"
+        : "=l"(t), "=r"(m)
+        : "l"(lo), "l"((u64)h1));
+    t -= (u64)m;  // lo - h1 (a borrow of 2^64 = EPS)
+    return fold_word(t, h0);
 #else
     u64 h0 = hi & 0xFFFFFFFFull, h1 = hi >> 32;
     u64 t = lo - h1;
@@ -129,24 +147,6 @@ GL_HD u64 mul(u64 a, u64 b) {
 #endif
 }
 
-// x * 2^S mod p for a compile-time S in [0, 192).
-template <int S>
-GL_HD u64 shl(u64 x) {
-    static_assert(S >= 0 && S < 192, "shift out of range");
-    if constexpr (S >= 96) {
-        return neg(shl<S - 96>(x));         // 2^96 = -1
-    } else if constexpr (S == 0) {
-        return x;
-    } else if constexpr (S < 64) {
-        return reduce128(x << S, x >> (64 - S));
-    } else if constexpr (S == 64) {
-        return reduce128(0, x);
-    } else {
-        // x * 2^S = (x * 2^(S-64)) * 2^64, the inner product below 2^96
-        return reduce128(0, reduce128(x << (S - 64), x >> (128 - S)));
-    }
-}
-
 GL_HD u64 pow(u64 b, u64 e) {
     u64 r = 1;
     while (e) {
@@ -161,18 +161,98 @@ GL_HD u64 pow(u64 b, u64 e) {
 
 namespace gl {
 
-// x * 2^s mod p for a run-time s in [0, 192). Inside fully unrolled loops s
-// is a constant and the branches fold away; where s varies it is uniform
-// across a warp in every caller, so the branches do not diverge.
+// 2^s mod p for s in [0, 192)
+#if defined(__CUDACC__)
+static __constant__ u64 c_pow2[192] = {  // 2^s mod p, s = 0 .. 191
+    0x0000000000000001ull, 0x0000000000000002ull, 0x0000000000000004ull, 0x0000000000000008ull,
+    0x0000000000000010ull, 0x0000000000000020ull, 0x0000000000000040ull, 0x0000000000000080ull,
+    0x0000000000000100ull, 0x0000000000000200ull, 0x0000000000000400ull, 0x0000000000000800ull,
+    0x0000000000001000ull, 0x0000000000002000ull, 0x0000000000004000ull, 0x0000000000008000ull,
+    0x0000000000010000ull, 0x0000000000020000ull, 0x0000000000040000ull, 0x0000000000080000ull,
+    0x0000000000100000ull, 0x0000000000200000ull, 0x0000000000400000ull, 0x0000000000800000ull,
+    0x0000000001000000ull, 0x0000000002000000ull, 0x0000000004000000ull, 0x0000000008000000ull,
+    0x0000000010000000ull, 0x0000000020000000ull, 0x0000000040000000ull, 0x0000000080000000ull,
+    0x0000000100000000ull, 0x0000000200000000ull, 0x0000000400000000ull, 0x0000000800000000ull,
+    0x0000001000000000ull, 0x0000002000000000ull, 0x0000004000000000ull, 0x0000008000000000ull,
+    0x0000010000000000ull, 0x0000020000000000ull, 0x0000040000000000ull, 0x0000080000000000ull,
+    0x0000100000000000ull, 0x0000200000000000ull, 0x0000400000000000ull, 0x0000800000000000ull,
+    0x0001000000000000ull, 0x0002000000000000ull, 0x0004000000000000ull, 0x0008000000000000ull,
+    0x0010000000000000ull, 0x0020000000000000ull, 0x0040000000000000ull, 0x0080000000000000ull,
+    0x0100000000000000ull, 0x0200000000000000ull, 0x0400000000000000ull, 0x0800000000000000ull,
+    0x1000000000000000ull, 0x2000000000000000ull, 0x4000000000000000ull, 0x8000000000000000ull,
+    0x00000000ffffffffull, 0x00000001fffffffeull, 0x00000003fffffffcull, 0x00000007fffffff8ull,
+    0x0000000ffffffff0ull, 0x0000001fffffffe0ull, 0x0000003fffffffc0ull, 0x0000007fffffff80ull,
+    0x000000ffffffff00ull, 0x000001fffffffe00ull, 0x000003fffffffc00ull, 0x000007fffffff800ull,
+    0x00000ffffffff000ull, 0x00001fffffffe000ull, 0x00003fffffffc000ull, 0x00007fffffff8000ull,
+    0x0000ffffffff0000ull, 0x0001fffffffe0000ull, 0x0003fffffffc0000ull, 0x0007fffffff80000ull,
+    0x000ffffffff00000ull, 0x001fffffffe00000ull, 0x003fffffffc00000ull, 0x007fffffff800000ull,
+    0x00ffffffff000000ull, 0x01fffffffe000000ull, 0x03fffffffc000000ull, 0x07fffffff8000000ull,
+    0x0ffffffff0000000ull, 0x1fffffffe0000000ull, 0x3fffffffc0000000ull, 0x7fffffff80000000ull,
+    0xffffffff00000000ull, 0xfffffffeffffffffull, 0xfffffffefffffffdull, 0xfffffffefffffff9ull,
+    0xfffffffefffffff1ull, 0xfffffffeffffffe1ull, 0xfffffffeffffffc1ull, 0xfffffffeffffff81ull,
+    0xfffffffeffffff01ull, 0xfffffffefffffe01ull, 0xfffffffefffffc01ull, 0xfffffffefffff801ull,
+    0xfffffffefffff001ull, 0xfffffffeffffe001ull, 0xfffffffeffffc001ull, 0xfffffffeffff8001ull,
+    0xfffffffeffff0001ull, 0xfffffffefffe0001ull, 0xfffffffefffc0001ull, 0xfffffffefff80001ull,
+    0xfffffffefff00001ull, 0xfffffffeffe00001ull, 0xfffffffeffc00001ull, 0xfffffffeff800001ull,
+    0xfffffffeff000001ull, 0xfffffffefe000001ull, 0xfffffffefc000001ull, 0xfffffffef8000001ull,
+    0xfffffffef0000001ull, 0xfffffffee0000001ull, 0xfffffffec0000001ull, 0xfffffffe80000001ull,
+    0xfffffffe00000001ull, 0xfffffffd00000001ull, 0xfffffffb00000001ull, 0xfffffff700000001ull,
+    0xffffffef00000001ull, 0xffffffdf00000001ull, 0xffffffbf00000001ull, 0xffffff7f00000001ull,
+    0xfffffeff00000001ull, 0xfffffdff00000001ull, 0xfffffbff00000001ull, 0xfffff7ff00000001ull,
+    0xffffefff00000001ull, 0xffffdfff00000001ull, 0xffffbfff00000001ull, 0xffff7fff00000001ull,
+    0xfffeffff00000001ull, 0xfffdffff00000001ull, 0xfffbffff00000001ull, 0xfff7ffff00000001ull,
+    0xffefffff00000001ull, 0xffdfffff00000001ull, 0xffbfffff00000001ull, 0xff7fffff00000001ull,
+    0xfeffffff00000001ull, 0xfdffffff00000001ull, 0xfbffffff00000001ull, 0xf7ffffff00000001ull,
+    0xefffffff00000001ull, 0xdfffffff00000001ull, 0xbfffffff00000001ull, 0x7fffffff00000001ull,
+    0xfffffffe00000002ull, 0xfffffffd00000003ull, 0xfffffffb00000005ull, 0xfffffff700000009ull,
+    0xffffffef00000011ull, 0xffffffdf00000021ull, 0xffffffbf00000041ull, 0xffffff7f00000081ull,
+    0xfffffeff00000101ull, 0xfffffdff00000201ull, 0xfffffbff00000401ull, 0xfffff7ff00000801ull,
+    0xffffefff00001001ull, 0xffffdfff00002001ull, 0xffffbfff00004001ull, 0xffff7fff00008001ull,
+    0xfffeffff00010001ull, 0xfffdffff00020001ull, 0xfffbffff00040001ull, 0xfff7ffff00080001ull,
+    0xffefffff00100001ull, 0xffdfffff00200001ull, 0xffbfffff00400001ull, 0xff7fffff00800001ull,
+    0xfeffffff01000001ull, 0xfdffffff02000001ull, 0xfbffffff04000001ull, 0xf7ffffff08000001ull,
+    0xefffffff10000001ull, 0xdfffffff20000001ull, 0xbfffffff40000001ull, 0x7fffffff80000001ull,
+};
+#endif
+
+GL_HD constexpr u64 pow2_mod(int s) {
+    // 2^s for s < 64, folded with 2^64 = EPS, 2^96 = -1 (constexpr, host and device)
+    u64 r = 1;
+    for (int i = 0; i < s; i++) {
+        u64 t = r << 1;
+        bool carry = r >> 63;
+        if (carry) t += EPS;            // t + 2^64 = t + EPS; t < 2^64 - 2 so no second carry
+        if (t >= P) t -= P;
+        r = t;
+    }
+    return r;
+}
+
+// x * 2^s mod p for s in (0, 32): the product spans 96 bits and its top word
+// h0 < 2^32 folds in once.
+GL_HD u64 shl_small(u64 x, int s) {
+#if defined(__CUDA_ARCH__)
+    u64 lo = x << s;
+    u32 h0 = (u32)(x >> (64 - s));
+    return fold_word(lo, h0);
+#else
+    return reduce128(x << s, x >> (64 - s));
+#endif
+}
+
+// x * 2^s mod p for a run-time s in [0, 192): small shifts fold one word;
+// larger ones (including the negative powers, 2^96 = -1) multiply by the
+// constant 2^s mod p, whose four partial products run on the multiplier.
+// Inside fully unrolled loops s is a constant and the branches fold away;
+// where s varies it is uniform across a warp in every caller.
 GL_HD u64 shl_v(u64 x, int s) {
-    bool negate = s >= 96;
-    if (negate) s -= 96;
-    u64 r;
-    if (s == 0) r = x;
-    else if (s < 64) r = reduce128(x << s, x >> (64 - s));
-    else if (s == 64) r = reduce128(0, x);
-    else r = reduce128(0, reduce128(x << (s - 64), x >> (128 - s)));
-    return negate ? neg(r) : r;
+    if (s == 0) return x;
+    if (s < 32) return shl_small(x, s);
+#if defined(__CUDA_ARCH__)
+    return mul(x, c_pow2[s]);
+#else
+    return mul(x, pow2_mod(s));
+#endif
 }
 
 // Shift for w^e where w = 2^(192/R) is the R-th root of unity used by every
