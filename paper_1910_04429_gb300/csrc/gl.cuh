@@ -28,26 +28,11 @@ constexpr u64 EPS = 0xFFFFFFFFull;  // 2^64 mod p
 // Values are kept in [0, p]: p itself may stand for 0 inside a transform
 // (neg(0) = p); add, sub, mul and the shifts accept and return that range, and
 // canon() maps p to 0 where an exact integer leaves the field.
-GL_HD u64 add(u64 a, u64 b) {
-#if defined(__CUDA_ARCH__)
-    // s = a + b (65 bits); s >= p iff s + EPS carries out of 64 bits
-    u64 s, t;
-    u32 c;
-    asm("add.cc.u64 %0, %3, %4;\n\t"
-        "addc.u32 %2, 0, 0;\n\t"
-        "add.cc.u64 %1, %0, 4294967295;\n\t"
-        "addc.u32 %2, %2, 0;"
-        : "=l"(s), "=l"(t), "=r"(c)
-        : "l"(a), "l"(b));
-    return c ? t : s;
-#else
-    u64 s = a + b;
-    bool c1 = s < a;
-    u64 t = s + EPS;
-    bool c2 = t < s;
-    return (c1 || c2) ? t : s;
-#endif
-}
+GL_HD u64 sub(u64 a, u64 b);
+
+// a + b = a - (p - b): the subtraction's borrow fix-up is cheaper than an add's
+// compare-and-select (p - b stays in [0, p] for b in [0, p]).
+GL_HD u64 add(u64 a, u64 b) { return sub(a, P - b); }
 
 GL_HD u64 sub(u64 a, u64 b) {
 #if defined(__CUDA_ARCH__)
@@ -240,14 +225,19 @@ GL_HD u64 shl_small(u64 x, int s) {
 #endif
 }
 
-// x * 2^s mod p for a run-time s in [0, 192): small shifts fold one word;
-// larger ones (including the negative powers, 2^96 = -1) multiply by the
-// constant 2^s mod p, whose four partial products run on the multiplier.
-// Inside fully unrolled loops s is a constant and the branches fold away;
-// where s varies it is uniform across a warp in every caller.
+// x * 2^s mod p for a run-time s in [0, 192), cheapest route by range
+// (measured instruction counts): s < 32 folds one top word; s < 64 reduces
+// the 128-bit shifted value; s < 96 multiplies by the constant 2^s mod p;
+// s >= 96 uses 2^96 = -1 (negated smaller shift, or the constant for
+// s >= 160). Inside fully unrolled loops s is a constant and the branches fold
+// away; where s varies it is uniform across a warp in every caller.
 GL_HD u64 shl_v(u64 x, int s) {
     if (s == 0) return x;
     if (s < 32) return shl_small(x, s);
+    if (s < 64) return reduce128(x << s, x >> (64 - s));
+    if (s == 96) return neg(x);
+    if (s > 96 && s < 128) return neg(shl_small(x, s - 96));
+    if (s >= 128 && s < 160) return neg(reduce128(x << (s - 96), x >> (160 - s)));
 #if defined(__CUDA_ARCH__)
     return mul(x, c_pow2[s]);
 #else
