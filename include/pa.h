@@ -231,6 +231,42 @@ int pa_profile(int on);
  */
 int pa_profile_collect(pa_kernel_stat* stats, int cap);
 
+/* ------------------------------------------------------------------------
+ * Bit-string adapters (device). The reconciled key X arrives as a bit string
+ * and the final key Y leaves as one (Sec. 2.2); Sec. 3.2.1 packs the string
+ * into words for mpz_import with word order most- or least-significant first,
+ * and Sec. 3.2.5 exports the r most significant bits. String bit i (reading
+ * order, i < nbits) is bit (i mod 8) of byte i/8 (msb_bytes = 0) or bit
+ * 7 - (i mod 8) (msb_bytes = 1). With msb_string = 0 string bit i is integer
+ * bit i; with msb_string = 1 it is integer bit nbits - 1 - i (the first bit is
+ * the most significant).
+ *   pa_bits_to_limbs: bits (device, ceil(nbits/8) bytes) -> limbs (device,
+ *     ceil(nbits/64) words, bits >= nbits zero).
+ *   pa_limbs_to_bits: limbs (device, ceil(nbits/64) words) -> bits (device,
+ *     ceil(nbits/8) bytes, padding bits zero).
+ * PA_EINVAL for null pointers, nbits outside [1, PA_MAX_BITS], flags not 0/1.
+ * ------------------------------------------------------------------------ */
+int pa_bits_to_limbs(const uint8_t* bits, uint64_t nbits, int msb_string, int msb_bytes,
+                     uint64_t* limbs, void* stream);
+int pa_limbs_to_bits(const uint64_t* limbs, uint64_t nbits, int msb_string, int msb_bytes,
+                     uint8_t* bits, void* stream);
+
+/*
+ * pa_final_key_length: Eq. 1 (Sec. 2.2), the largest integer
+ * r <= hmin_bits - 2 log2(1/eps), where hmin_bits is the smooth min-entropy
+ * H_min^{eps/2}(rho_SE | E) of the reconciled key (an estimate supplied by the
+ * caller; the paper obtains r from GLLP theory and system parameters).
+ * PA_EINVAL if eps is not in (0, 1) or no positive r exists.
+ */
+int pa_final_key_length(double hmin_bits, double eps, uint64_t* r);
+
+/*
+ * pa_leftover_epsilon: Definition 2 (quantum leftover hash lemma), the bound
+ * eps_bar = 1/2 * 2^(-(hmin_bits - r) / 2) + eps on the distance of an r-bit
+ * key hashed with a universal_2 family from an ideal key.
+ */
+int pa_leftover_epsilon(double hmin_bits, uint64_t r, double eps, double* eps_bar);
+
 /* Largest key pa_hash_noalloc accepts: 2^20 bits (its fixed scratch size). */
 #define PA_NOALLOC_MAX_BITS (1ull << 20)
 

@@ -117,3 +117,45 @@ def raw_hash_rc(n: int, m: int) -> int:
     z = np.zeros(L, dtype=np.uint64)
     out = np.zeros(max(1, (m + 63) // 64), dtype=np.uint64)
     return _load().pa_oracle_hash(_ptr(z), _ptr(z), _ptr(z), n, m, _ptr(out), 1)
+
+
+# ---------------------------------------------------------------------------
+# Final-key length and bit strings (plain definitions)
+# ---------------------------------------------------------------------------
+
+def final_key_length(hmin_bits: float, eps: float) -> int:
+    """Eq. 1 (Sec. 2.2): the largest integer r <= H_min^{eps/2} - 2 log2(1/eps)."""
+    import math
+
+    if not (0.0 < eps < 1.0):
+        raise ValueError("eps must be in (0, 1)")
+    r = math.floor(hmin_bits - 2.0 * math.log2(1.0 / eps))
+    if r < 1:
+        raise ValueError("no positive key length")
+    return r
+
+
+def leftover_epsilon(hmin_bits: float, r: int, eps: float) -> float:
+    """Definition 2 (quantum leftover hash lemma): 1/2 * 2^(-(H_min^eps - r)/2) + eps."""
+    return 0.5 * 2.0 ** (-0.5 * (hmin_bits - r)) + eps
+
+
+def bits_to_int(data: bytes, nbits: int, msb_string: bool, msb_bytes: bool) -> int:
+    """The integer a packed bit string denotes: string bit i is bit i % 8 (or
+    7 - i % 8 with msb_bytes) of byte i // 8; it weighs 2^i, or 2^(nbits-1-i)
+    with msb_string."""
+    bits = np.unpackbits(np.frombuffer(bytes(data), dtype=np.uint8),
+                         bitorder="big" if msb_bytes else "little")[:nbits]
+    if msb_string:
+        bits = bits[::-1]
+    packed = np.packbits(bits, bitorder="little").tobytes()
+    return int.from_bytes(packed, "little")
+
+
+def int_to_bits(value: int, nbits: int, msb_string: bool, msb_bytes: bool) -> bytes:
+    """Inverse of bits_to_int for 0 <= value < 2^nbits (padding bits zero)."""
+    raw = value.to_bytes((nbits + 7) // 8, "little")
+    bits = np.unpackbits(np.frombuffer(raw, dtype=np.uint8), bitorder="little")[:nbits]
+    if msb_string:
+        bits = bits[::-1]
+    return np.packbits(bits, bitorder="big" if msb_bytes else "little").tobytes()

@@ -29,6 +29,13 @@ _SIGS = {
                        ctypes.c_int),
     "pa_hash_seeded": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_seed_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "pa_bits_to_limbs": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                          ctypes.c_void_p], ctypes.c_int),
+    "pa_limbs_to_bits": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                          ctypes.c_void_p], ctypes.c_int),
+    "pa_final_key_length": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "pa_leftover_epsilon": ([ctypes.c_double, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
@@ -137,6 +144,9 @@ def _stream_ptr(stream):
 
 def limbs(bits: int) -> int:
     return (bits + 63) // 64
+
+
+limbs_for = limbs
 
 
 def hash(key, seed_a, seed_b, n: int, m: int, out=None, stream=None):
@@ -274,6 +284,44 @@ def serve_stats() -> dict:
 
 def serve_stop():
     _check(load().pa_serve_stop(), "pa_serve_stop")
+
+
+def bits_to_limbs(bits, nbits: int, msb_string: bool, msb_bytes: bool, limbs=None, stream=None):
+    """Packed bit string (CUDA uint8 tensor) -> little-endian limbs (CUDA int64 tensor)."""
+    import torch
+
+    if limbs is None:
+        limbs = torch.empty(limbs_for(nbits), dtype=torch.int64, device=bits.device)
+    _check(load().pa_bits_to_limbs(ctypes.c_void_p(bits.data_ptr()), nbits, int(msb_string), int(msb_bytes),
+                                   _dev_ptr(limbs, limbs_for(nbits), "limbs"), _stream_ptr(stream)),
+           "pa_bits_to_limbs")
+    return limbs
+
+
+def limbs_to_bits(limbs, nbits: int, msb_string: bool, msb_bytes: bool, bits=None, stream=None):
+    """Little-endian limbs (CUDA int64 tensor) -> packed bit string (CUDA uint8 tensor)."""
+    import torch
+
+    if bits is None:
+        bits = torch.empty((nbits + 7) // 8, dtype=torch.uint8, device=limbs.device)
+    _check(load().pa_limbs_to_bits(_dev_ptr(limbs, limbs_for(nbits), "limbs"), nbits, int(msb_string),
+                                   int(msb_bytes), ctypes.c_void_p(bits.data_ptr()), _stream_ptr(stream)),
+           "pa_limbs_to_bits")
+    return bits
+
+
+def final_key_length(hmin_bits: float, eps: float) -> int:
+    """Eq. 1: largest r <= hmin - 2 log2(1/eps)."""
+    r = ctypes.c_uint64(0)
+    _check(load().pa_final_key_length(hmin_bits, eps, ctypes.byref(r)), "pa_final_key_length")
+    return int(r.value)
+
+
+def leftover_epsilon(hmin_bits: float, r: int, eps: float) -> float:
+    """Definition 2: 1/2 * 2^(-(hmin - r)/2) + eps."""
+    v = ctypes.c_double(0)
+    _check(load().pa_leftover_epsilon(hmin_bits, r, eps, ctypes.byref(v)), "pa_leftover_epsilon")
+    return float(v.value)
 
 
 def prepare(n: int):
