@@ -198,7 +198,7 @@ def alu_ops(name: str, N: int):
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
 # launch at n = 10^8), valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "ntt_contig_fused", "bytes": 261.7e6, "src_sha": "4eb4ea51b737d155",
+TRAFFIC = {"kernel": "ntt_contig_fused", "bytes": 261.2e6, "src_sha": "d27b4fe732a8ec0d",
            "profile": "profiles/k_contig_fused_n1e8.md"}
 
 
