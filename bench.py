@@ -408,12 +408,17 @@ def run_batched(args):
     ref = [o.clone() for o in outs]
     ms_p = timed(plain, steps)
     same = all(torch.equal(r, o) for r, o in zip(ref, outs))
+    graph = binding.Batch(spec)
+    ms_g = timed(graph.run, steps)
+    same = same and all(torch.equal(r, o) for r, o in zip(ref, outs))
+    graph.close()
     return {"metric": "PA input throughput (Mbps of key bits), batched blocks", "unit": UNIT,
             "workload": f"{len(blks)} blocks, n log-uniform in [1e6, 1e7] (sum {bits} bits), "
                         f"m = floor(n r), r ~ U(0.1, 0.5), seeds 1..{len(blks)}",
             "batched": {"value": round(bits / ms_b / 1e3, 1), "ms_per_batch": round(ms_b, 3)},
             "plain_single_launches": {"value": round(bits / ms_p / 1e3, 1),
                                       "ms_per_batch": round(ms_p, 3)},
+            "captured_graph": {"value": round(bits / ms_g / 1e3, 1), "ms_per_batch": round(ms_g, 3)},
             "results_identical": same, "steps": steps}
 
 

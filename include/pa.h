@@ -200,6 +200,21 @@ int pa_serve_stats(pa_serve_stats_t* out);
 int pa_serve_stop(void);
 
 /*
+ * Captured batches: for a fixed set of blocks (the same buffers hashed again
+ * and again, e.g. the slots of a post-processing pipeline), pa_batch_create
+ * runs pa_hash_batched once eagerly (building every table it needs) and then
+ * captures the same launch sequence, including its forked streams, into a CUDA
+ * graph with its own workspace (cudaMalloc, synchronous). pa_batch_run
+ * replays the graph on `stream` with one launch: every block is rehashed from
+ * the current contents of its buffers. pa_batch_destroy frees it (no replay
+ * may be in flight). Buffers must stay valid for the life of the handle.
+ */
+typedef struct pa_batch_s* pa_batch;
+int pa_batch_create(const pa_block* blocks, uint32_t count, pa_batch* out);
+int pa_batch_run(pa_batch batch, void* stream);
+int pa_batch_destroy(pa_batch batch);
+
+/*
  * pa_prepare: build the twiddle tables of the transform that serves keys of
  * n bits on the current device (synchronous). Optional: pa_hash does this
  * lazily. Call it for every key size before capturing a stream into a CUDA

@@ -36,6 +36,9 @@ _SIGS = {
     "pa_final_key_length": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "pa_leftover_epsilon": ([ctypes.c_double, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
                             ctypes.c_int),
+    "pa_batch_create": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "pa_batch_run": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "pa_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
@@ -322,6 +325,30 @@ def leftover_epsilon(hmin_bits: float, r: int, eps: float) -> float:
     v = ctypes.c_double(0)
     _check(load().pa_leftover_epsilon(hmin_bits, r, eps, ctypes.byref(v)), "pa_leftover_epsilon")
     return float(v.value)
+
+
+class Batch:
+    """A fixed set of blocks captured into a CUDA graph (pa_batch_create);
+    ``run`` replays it. The tensors must stay alive until ``close``."""
+
+    def __init__(self, blocks):
+        arr = (PaBlock * len(blocks))()
+        for i, (k, a, b, n, m, o) in enumerate(blocks):
+            L = limbs(n)
+            arr[i] = PaBlock(_dev_ptr(k, L, "key").value, _dev_ptr(a, L, "seed_a").value,
+                             _dev_ptr(b, L, "seed_b").value, n, m, _dev_ptr(o, limbs(m), "out").value)
+        h = ctypes.c_void_p(0)
+        _check(load().pa_batch_create(arr, len(blocks), ctypes.byref(h)), "pa_batch_create")
+        self.handle = h
+        self._keep = blocks
+
+    def run(self, stream=None):
+        _check(load().pa_batch_run(self.handle, _stream_ptr(stream)), "pa_batch_run")
+
+    def close(self):
+        if self.handle:
+            _check(load().pa_batch_destroy(self.handle), "pa_batch_destroy")
+            self.handle = None
 
 
 def prepare(n: int):

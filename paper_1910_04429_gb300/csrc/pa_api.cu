@@ -174,8 +174,17 @@ int side_streams(int dev) {
 // Blocks grouped by transform geometry: each group runs its passes as batched
 // launches (blocks along gridDim.y), groups on side streams forked from and
 // joined back into `st`, then one batched carry launch for every block.
+u64 batch_workspace_bytes(const pa_block* blocks, uint32_t count) {
+    u64 bytes = 0;
+    for (uint32_t i = 0; i < count; i++)
+        bytes += 2 * geom_for_bits(blocks[i].n).N * sizeof(u64) + carry_state_words(blocks[i].n) * sizeof(u32);
+    return bytes;
+}
+
+// fixed_ws: a caller-provided workspace of batch_workspace_bytes() (used for
+// captured graphs); otherwise it comes from the pool, stream-ordered.
 int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, int dev,
-                      cudaMemPool_t pool) {
+                      cudaMemPool_t pool, void* fixed_ws = nullptr) {
     int rc = side_streams(dev);
     if (rc) return rc;
     Device& d = g_dev[dev];
@@ -192,8 +201,8 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     for (auto& gr : groups) words += 2 * gr.first * gr.second.size();
     for (uint32_t i = 0; i < count; i++) carry_bytes += carry_state_words(blocks[i].n) * sizeof(u32);
     Scratch scr(st, pool);
-    void* ws;
-    if ((rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
+    void* ws = fixed_ws;
+    if (!ws && (rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
     u64* w = (u64*)ws;
     u32* cb = (u32*)(w + words);
     std::vector<CarryJob> cj(count);
@@ -426,6 +435,81 @@ int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream) {
     int rc = setup(&dev, &pool);
     if (rc) return rc;
     return hash_batch_device(blocks, count, (cudaStream_t)stream, dev, pool);
+}
+
+}  // extern "C"
+
+struct pa_batch_s {
+    int dev;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    void* ws;
+};
+
+extern "C" {
+
+int pa_batch_create(const pa_block* blocks, uint32_t count, pa_batch* out) {
+    if (!out || !count || !blocks) return fail(PA_EINVAL, "pa_batch_create: need blocks, count > 0, out");
+    for (uint32_t i = 0; i < count; i++) {
+        const pa_block& b = blocks[i];
+        if (!check_sizes(b.n, b.m) || !b.key || !b.seed_a || !b.seed_b || !b.out)
+            return fail(PA_EINVAL, "pa_batch_create: invalid block " + std::to_string(i));
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    if ((rc = side_streams(dev))) return rc;
+    void* ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, batch_workspace_bytes(blocks, count));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch workspace)");
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool prof = g_prof_on;
+    auto cleanup = [&](int code) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        cudaFree(ws);
+        g_prof_on = prof;
+        return code;
+    };
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    // one eager run first: builds every twiddle table and kernel attribute the
+    // capture will use (neither may happen during capture)
+    if ((rc = hash_batch_device(blocks, count, cs, dev, pool, ws))) return cleanup(rc);
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cleanup(cuda_fail(e, "warm-up run"));
+    g_prof_on = false;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaStreamBeginCapture"));
+    rc = hash_batch_device(blocks, count, cs, dev, pool, ws);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (rc) return cleanup(rc);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamEndCapture"));
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaGraphInstantiate"));
+    cudaStreamDestroy(cs);
+    g_prof_on = prof;
+    *out = new pa_batch_s{dev, graph, exec, ws};
+    return PA_OK;
+}
+
+int pa_batch_run(pa_batch batch, void* stream) {
+    if (!batch) return fail(PA_EINVAL, "pa_batch_run: null batch");
+    cudaError_t e = cudaGraphLaunch(batch->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? PA_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int pa_batch_destroy(pa_batch batch) {
+    if (!batch) return PA_OK;
+    cudaGraphExecDestroy(batch->exec);
+    cudaGraphDestroy(batch->graph);
+    cudaError_t e = cudaFree(batch->ws);
+    delete batch;
+    return e == cudaSuccess ? PA_OK : cuda_fail(e, "cudaFree(batch workspace)");
 }
 
 }  // extern "C"

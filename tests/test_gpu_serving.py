@@ -48,6 +48,33 @@ def test_batched_more_blocks_than_one_launch():
         np.testing.assert_array_equal(host(o), oracle.pa_hash(b.x, b.a, b.b, b.n, b.m))
 
 
+def test_captured_batch_replays_current_contents():
+    """pa_batch_create captures the batched launch sequence once; every replay
+    rehashes the blocks from the current contents of their buffers."""
+    import torch
+
+    blks = inputs.make_batch(20, 1_000, 2_000_000, seed=61)
+    t = [(dev(b.x), dev(b.a), dev(b.b)) for b in blks]
+    outs = [torch.empty((b.m + 63) // 64, dtype=torch.int64, device="cuda") for b in blks]
+    batch = binding.Batch([(x, a, bb, b.n, b.m, o) for b, (x, a, bb), o in zip(blks, t, outs)])
+    try:
+        for rnd in range(2):
+            if rnd:  # new keys in the same buffers
+                blks = [inputs.make_block(b.n, b.m, seed=900 + i) for i, b in enumerate(blks)]
+                for b, (x, a, bb) in zip(blks, t):
+                    x.copy_(dev(b.x))
+                    a.copy_(dev(b.a))
+                    bb.copy_(dev(b.b))
+            for o in outs:
+                o.fill_(-1)
+            batch.run()
+            torch.cuda.synchronize()
+            for b, o in zip(blks, outs):
+                np.testing.assert_array_equal(host(o), oracle.pa_hash(b.x, b.a, b.b, b.n, b.m))
+    finally:
+        batch.close()
+
+
 def test_served_results_equal_alone():
     import torch
 
