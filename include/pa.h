@@ -222,6 +222,25 @@ int pa_batch_destroy(pa_batch batch);
  */
 int pa_prepare(uint64_t n);
 
+/*
+ * Autotuning. Every transform length has a few equivalent plans (PA_PLAN_*
+ * bits: the odd first radix run last instead of first; forward or inverse
+ * strided passes loading their tiles directly instead of staging them with
+ * asynchronous copies). pa_autotune times the applicable plans for the
+ * transform length that keys of n bits use (reps hashes each, on synthetic
+ * data, synchronous; it allocates with cudaMalloc) and keeps the fastest for
+ * that length on the current device; later calls (single, batched, seeded,
+ * served) use it. With the environment variable PA_TUNE_CACHE naming a file,
+ * choices are saved there per GPU name and loaded on first use.
+ * pa_plan_override forces a variant for the length of n (-1 clears; for
+ * tests). Results are identical under every plan.
+ */
+#define PA_PLAN_R0_LAST 1
+#define PA_PLAN_DIRECT_FWD 2
+#define PA_PLAN_DIRECT_INV 4
+int pa_autotune(uint64_t n, int reps, int* variant_out);
+int pa_plan_override(uint64_t n, int variant);
+
 /* pa_workspace_bytes: device workspace one pa_hash of n bits draws from the pool. */
 uint64_t pa_workspace_bytes(uint64_t n);
 

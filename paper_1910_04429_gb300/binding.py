@@ -39,6 +39,8 @@ _SIGS = {
     "pa_batch_create": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "pa_batch_run": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "pa_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "pa_autotune": ([ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "pa_plan_override": ([ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
@@ -349,6 +351,18 @@ class Batch:
         if self.handle:
             _check(load().pa_batch_destroy(self.handle), "pa_batch_destroy")
             self.handle = None
+
+
+def autotune(n: int, reps: int = 5) -> int:
+    """Time the plan variants for keys of n bits and keep the fastest; returns it."""
+    v = ctypes.c_int(0)
+    _check(load().pa_autotune(n, reps, ctypes.byref(v)), "pa_autotune")
+    return int(v.value)
+
+
+def plan_override(n: int, variant: int):
+    """Force a plan variant for the transform length of n (-1 clears)."""
+    _check(load().pa_plan_override(n, variant), "pa_plan_override")
 
 
 def prepare(n: int):

@@ -1,6 +1,8 @@
 // C ABI of the library (declared in include/pa.h): argument checks, plan and
 // twiddle-table cache, stream-ordered workspace, and the launch sequence of
 // the G_{c,d} hash (Sec. 2.3 Eq. 7; pipeline of Sec. 3.2).
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -30,6 +32,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr int SIDE_STREAMS = 4;  // concurrent size classes inside one batched call
 
 struct Device {
+    bool tune_loaded = false;
+    std::unordered_map<u64, int> tuned;   // N -> plan variant chosen by pa_autotune
+    std::unordered_map<u64, int> forced;  // N -> plan variant forced by pa_plan_override
     cudaMemPool_t pool = nullptr;
     std::unordered_map<u64, u64*> tables;  // transform length N -> device twiddle tables
     cudaStream_t side[SIDE_STREAMS] = {};  // forked from the caller's stream per batch
@@ -106,6 +111,83 @@ bool check_sizes(uint64_t n, uint64_t m) { return n >= 1 && m >= 1 && m <= n && 
 
 Geom geom_for_bits(uint64_t n) { return choose_geom((n + 15) / 16); }
 
+// Plan variants that change anything for this transform length.
+int applicable_variants(const Geom& g) {
+    if (g.nstrided == 0) return 0;
+    int R0 = (g.three ? 3 : 1) << ((g.logN - LOG_TILE) % 6);
+    return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV;
+}
+
+// The plan for keys of n bits on device dev: the transform length of
+// choose_geom, with the variant forced for it, else the tuned one, else 0.
+Geom plan_for(int dev, uint64_t n) {
+    Geom base = geom_for_bits(n);
+    Device& d = g_dev[dev];
+    int v = 0;
+    auto f = d.forced.find(base.N);
+    if (f != d.forced.end()) v = f->second;
+    else {
+        auto t = d.tuned.find(base.N);
+        if (t != d.tuned.end()) v = t->second;
+    }
+    return make_geom(base.logN, base.three, v & applicable_variants(base));
+}
+
+// Tuning cache file (PA_TUNE_CACHE): lines "<gpu name>\t<N>\t<variant>".
+std::string device_name(int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string s = prop.name;
+    for (char& c : s)
+        if (c == '\t' || c == '\n') c = ' ';
+    return s;
+}
+
+void load_tune_cache(int dev) {
+    Device& d = g_dev[dev];
+    if (d.tune_loaded) return;
+    d.tune_loaded = true;
+    const char* path = getenv("PA_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    std::string name = device_name(dev);
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char* t1 = strchr(line, '\t');
+        if (!t1) continue;
+        *t1 = 0;
+        unsigned long long N = 0;
+        int v = 0;
+        if (name == line && sscanf(t1 + 1, "%llu\t%d", &N, &v) == 2 && v >= 0 && v < PLAN_VARIANTS)
+            d.tuned[(u64)N] = v;
+    }
+    fclose(f);
+}
+
+void save_tune_cache(int dev) {
+    const char* path = getenv("PA_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::string name = device_name(dev);
+    std::vector<std::string> keep;
+    if (FILE* f = fopen(path, "r")) {
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+            const char* t1 = strchr(line, '\t');
+            if (t1 && std::string((const char*)line, t1) != name) keep.push_back(line);
+        }
+        fclose(f);
+    }
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (auto& l : keep) fputs(l.c_str(), f);
+    for (auto& kv : g_dev[dev].tuned)
+        fprintf(f, "%s\t%llu\t%d\n", name.c_str(), (unsigned long long)kv.first, kv.second);
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
 uint16_t top_digit_mask(uint64_t n) {
     return (n & 15) ? (uint16_t)((1u << (n & 15)) - 1) : (uint16_t)0xFFFF;
 }
@@ -116,7 +198,7 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
                       Scratch& scr, int dev, u64** coef, bool sysmem = false) {
     u64 L = (n + 15) / 16;
     NttJob j;
-    j.geom = geom_for_bits(n);
+    j.geom = plan_for(dev, n);
     j.L = L;
     int rc = get_tables(dev, j.geom, &j.tw);
     if (rc) return rc;
@@ -212,7 +294,7 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     int used = 0;
     for (size_t g = 0; g < groups.size(); g++) {
         const auto& idx = groups[g].second;
-        Geom G = geom_for_bits(blocks[idx[0]].n);
+        Geom G = plan_for(dev, blocks[idx[0]].n);
         Twiddles tw;
         if ((rc = get_tables(dev, G, &tw))) return rc;
         std::vector<BlockIO> io(idx.size());
@@ -260,6 +342,7 @@ bool host_mapped(const void* p, void** dptr) {
 int setup(int* dev, cudaMemPool_t* pool) {
     int rc = current_device(dev);
     if (rc) return rc;
+    load_tune_cache(*dev);
     return get_pool(*dev, pool);
 }
 
@@ -532,7 +615,7 @@ int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* ou
     int rc = setup(&dev, &pool);
     if (rc) return rc;
     NttJob j;
-    j.geom = geom_for_bits(n);
+    j.geom = plan_for(dev, n);
     j.L = (n + 15) / 16;
     if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
     u64* spec = nullptr;
@@ -584,6 +667,86 @@ int pa_seed_destroy(pa_seed seed) {
     if (prev >= 0) cudaSetDevice(prev);
     delete seed;
     return e == cudaSuccess ? PA_OK : cuda_fail(e, "cudaFree(seed spectrum)");
+}
+
+int pa_plan_override(uint64_t n, int variant) {
+    if (n < 1 || n > PA_MAX_BITS || variant < -1 || variant >= PLAN_VARIANTS)
+        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 8");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    u64 N = geom_for_bits(n).N;
+    if (variant < 0) g_dev[dev].forced.erase(N);
+    else g_dev[dev].forced[N] = variant;
+    return PA_OK;
+}
+
+int pa_autotune(uint64_t n, int reps, int* variant_out) {
+    if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_autotune: need 1 <= n <= PA_MAX_BITS");
+    if (reps < 1) reps = 5;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    Device& d = g_dev[dev];
+    Geom base = geom_for_bits(n);
+    int mask = applicable_variants(base);
+    u64 m = n / 4 ? n / 4 : 1;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 0;
+    void *x = nullptr, *a = nullptr, *b = nullptr, *out = nullptr;
+    size_t in_bytes = ((n + 63) / 64) * 8, out_bytes = ((m + 63) / 64) * 8;
+    if (e == cudaSuccess) e = cudaMalloc(&x, in_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&a, in_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b, in_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&out, out_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0x5A, in_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a, 0xC3, in_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b, 0x3C, in_bytes, st);
+    bool had_force = d.forced.count(base.N) != 0;
+    int old_force = had_force ? d.forced[base.N] : 0;
+    for (int v = 0; e == cudaSuccess && rc == PA_OK && v < PLAN_VARIANTS; v++) {
+        if (v & ~mask) continue;
+        d.forced[base.N] = v;
+        for (int i = 0; i < 2 && rc == PA_OK; i++)
+            rc = hash_device((const u64*)x, (const u64*)a, (const u64*)b, n, m, (u64*)out, st, dev, pool);
+        if (rc) break;
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        for (int i = 0; i < reps && rc == PA_OK; i++)
+            rc = hash_device((const u64*)x, (const u64*)a, (const u64*)b, n, m, (u64*)out, st, dev, pool);
+        if (rc) break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (v == 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    if (had_force) d.forced[base.N] = old_force;
+    else d.forced.erase(base.N);
+    if (st) cudaStreamSynchronize(st);
+    cudaFree(x);
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "pa_autotune");
+    d.tuned[base.N] = best;
+    save_tune_cache(dev);
+    if (variant_out) *variant_out = best;
+    return PA_OK;
 }
 
 int pa_prepare(uint64_t n) {

@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     }
 }
 
-// Inverse strided pass over one tile: the tile is copied into shared memory
-// asynchronously while the inverse twiddles are computed.
-template <int RA, int RB, int C, bool LAST, int B>
+// Inverse strided pass over one tile. STAGED: the tile is copied into shared
+// memory asynchronously while the inverse twiddles are computed; otherwise the
+// first phase loads it directly (the autotuner picks per transform length).
+template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
 __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     using S = Strided<RA, RB, C>;
@@ -125,20 +126,28 @@ __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __gr
     u64* st = dsm + TILE;
     const BlockIO& io = nb.io[blockIdx.y];
     TilePos tp = S::tile(g, blockIdx.x);
-    stage_words<S::R, C>(st, io.buf_x, g, tp);
-    cp_async_commit();
-    u64 w[S::ITEMS_B][RA];
+    if (STAGED) {
+        stage_words<S::R, C>(st, io.buf_x, g, tp);
+        cp_async_commit();
+        u64 w[S::ITEMS_B][RA];
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_B; i++) {
-        int it = threadIdx.x + i * NT;
-        if (S::NB % NT == 0 || it < S::NB) S::inv_twiddles(g, tp, it, tw, w[i]);
-    }
-    cp_async_wait<0>();
-    __syncthreads();
+        for (int i = 0; i < S::ITEMS_B; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NB % NT == 0 || it < S::NB) S::inv_twiddles(g, tp, it, tw, w[i]);
+        }
+        cp_async_wait<0>();
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < S::ITEMS_B; i++) {
-        int it = threadIdx.x + i * NT;
-        if (S::NB % NT == 0 || it < S::NB) S::inv_b_staged(g, tp, it, st, sm, w[i]);
+        for (int i = 0; i < S::ITEMS_B; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NB % NT == 0 || it < S::NB) S::inv_b_staged(g, tp, it, st, sm, w[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < S::ITEMS_B; i++) {
+            int it = threadIdx.x + i * NT;
+            if (S::NB % NT == 0 || it < S::NB) S::inv_b(g, tp, it, io.buf_x, sm, tw);
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -262,10 +271,15 @@ struct Launcher {
         allow_smem(k, smem);
         k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
     }
+    bool stage_fwd, stage_inv;  // plan variant: staged or direct tile loads
+
     template <int RA, int RB, int C, int OPS>
     void fwd_ops(bool pack) const {
-        if (!pack) return fwd_k<RA, RB, C, false, true, OPS>();
-        if (stage_digits_ok) return fwd_k<RA, RB, C, true, true, OPS>();
+        if (!pack) {
+            if (stage_fwd) return fwd_k<RA, RB, C, false, true, OPS>();
+            return fwd_k<RA, RB, C, false, false, OPS>();
+        }
+        if (stage_digits_ok && stage_fwd) return fwd_k<RA, RB, C, true, true, OPS>();
         fwd_k<RA, RB, C, true, false, OPS>();
     }
     template <int RA, int RB, int C>
@@ -273,19 +287,22 @@ struct Launcher {
         if (ops == 1) return fwd_ops<RA, RB, C, 1>(pack);
         fwd_ops<RA, RB, C, 2>(pack);
     }
+    template <int RA, int RB, int C, bool LAST, bool STAGED>
+    void inv_k() const {
+        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
+        size_t smem = (TILE + (STAGED ? RA * RB * C : 0)) * sizeof(u64);
+        auto k = k_inv_strided<RA, RB, C, LAST, B, STAGED>;
+        allow_smem(k, smem);
+        k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+    }
     template <int RA, int RB, int C>
     void inv(bool last) const {
-        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
-        size_t smem = (TILE + RA * RB * C) * sizeof(u64);
         if (last) {
-            auto k = k_inv_strided<RA, RB, C, true, B>;
-            allow_smem(k, smem);
-            k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
-        } else {
-            auto k = k_inv_strided<RA, RB, C, false, B>;
-            allow_smem(k, smem);
-            k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+            if (stage_inv) return inv_k<RA, RB, C, true, true>();
+            return inv_k<RA, RB, C, true, false>();
         }
+        if (stage_inv) return inv_k<RA, RB, C, false, true>();
+        inv_k<RA, RB, C, false, false>();
     }
     void dispatch_fwd(int R, bool pack) const {
 #define PA_FWD(r, a, b, c) if (R == r) return fwd<a, b, c>(pack);
@@ -311,6 +328,7 @@ static StridedGeom strided_geom(const Geom& G, int p) {
 template <int B>
 static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatch<B>& nb,
                                 cudaStream_t st, int ops = 2) {
+    bool stage_fwd = !(G.variant & PLAN_DIRECT_FWD), stage_inv = !(G.variant & PLAN_DIRECT_INV);
     bool aligned = true;
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
@@ -318,7 +336,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned, ops}.dispatch_fwd(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv}.dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }
     dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
@@ -341,7 +359,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned, ops}.dispatch_inv(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv}.dispatch_inv(G.pass[p].R, p == 0);
         prof_end(st);
     }
     return cudaGetLastError();
@@ -366,7 +384,8 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, "ntt_seed_strided");
-        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1}.dispatch_fwd(G.pass[p].R, p == 0);
+        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1, !(G.variant & PLAN_DIRECT_FWD), true}
+            .dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }
     dim3 tiles((unsigned)(G.N / TILE), 1);

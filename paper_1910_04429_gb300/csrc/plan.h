@@ -23,27 +23,37 @@ struct Geom {
     uint64_t N = 0;
     int nstrided = 0;
     PassDesc pass[8];
+    int variant = 0; // PLAN_* bits the plan was made with
 };
+
+// Plan variants the autotuner chooses between (any order of the strided
+// radices factors the same transform; only the memory access pattern and the
+// twiddle work per pass change).
+constexpr int PLAN_R0_LAST = 1;     // the odd radix R_0 runs last among the strided passes
+constexpr int PLAN_DIRECT_FWD = 2;  // forward strided passes load their tiles directly
+constexpr int PLAN_DIRECT_INV = 4;  // inverse strided passes load their tiles directly
+constexpr int PLAN_VARIANTS = 8;
 
 // N = R_0 * 64^q * 4096 with N = 2^logN (R_0 = 2^((logN-12) mod 6), omitted when
 // 1) or N = 3 * 2^logN (R_0 = 3 * 2^((logN-12) mod 6), which must be <= 48):
 // one strided pass of radix R_0, then q strided passes of radix 64, then the
 // contiguous 4096-element pass.
-inline Geom make_geom(int logN, int three = 0) {
+inline Geom make_geom(int logN, int three = 0, int variant = 0) {
     Geom g;
     g.logN = logN;
     g.three = three;
+    g.variant = variant;
     g.N = (three ? 3ull : 1ull) << logN;
     int rem = (logN - LOG_TILE) % 6, q = (logN - LOG_TILE) / 6;
-    uint64_t M = g.N;
     int R0 = (three ? 3 : 1) << rem;
-    if (R0 > 1) {
-        g.pass[g.nstrided++] = PassDesc{R0, M, M / R0};
-        M /= R0;
-    }
-    for (int i = 0; i < q; i++) {
-        g.pass[g.nstrided++] = PassDesc{64, M, M >> 6};
-        M >>= 6;
+    int radix[8], nr = 0;
+    if (R0 > 1 && !(variant & PLAN_R0_LAST)) radix[nr++] = R0;
+    for (int i = 0; i < q; i++) radix[nr++] = 64;
+    if (R0 > 1 && (variant & PLAN_R0_LAST)) radix[nr++] = R0;
+    uint64_t M = g.N;
+    for (int i = 0; i < nr; i++) {
+        g.pass[g.nstrided++] = PassDesc{radix[i], M, M / radix[i]};
+        M /= radix[i];
     }
     return g;
 }

@@ -1,0 +1,66 @@
+"""Every plan variant the autotuner may pick gives the same bits, and the
+tuner's choice (kept in memory and in the PA_TUNE_CACHE file) stays exact."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_04429_gb300 import binding, inputs
+from tests.gpu_util import dev, gpu_hash, host
+
+pytestmark = pytest.mark.gpu
+
+# transform lengths 2^12 (no strided pass), 2^14 ([4]), 3*2^16 ([48]),
+# 2^19 ([2, 64]) and 3*2^18 ([3, 64])
+SIZES = [1000, 100_003, 1_536_000, 3_000_001, 4_800_000]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_every_plan_variant_is_exact(n):
+    blk = inputs.make_block(n, n // 3 or 1, seed=n)
+    want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m, threads=oracle.default_threads())
+    try:
+        for v in range(8):
+            binding.plan_override(n, v)
+            np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
+                                          err_msg=f"variant {v}")
+    finally:
+        binding.plan_override(n, -1)
+
+
+def test_seed_keeps_its_plan():
+    import torch
+
+    n, m = 3_000_001, 700_000
+    blk = inputs.make_block(n, m, seed=4)
+    ta = dev(blk.a)
+    binding.plan_override(n, binding_R0_LAST())
+    s = binding.Seed(ta, n)
+    binding.plan_override(n, -1)
+    try:
+        got = s.hash(dev(blk.x), dev(blk.b), m)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(got), oracle.pa_hash(blk.x, blk.a, blk.b, n, m))
+    finally:
+        s.close()
+
+
+def binding_R0_LAST():
+    return 1
+
+
+def test_autotune_choice_is_exact_and_cached(tmp_path):
+    n, m = 4_800_000, 1_000_003
+    cache = tmp_path / "tune.txt"
+    os.environ["PA_TUNE_CACHE"] = str(cache)
+    try:
+        v = binding.autotune(n, reps=2)
+    finally:
+        del os.environ["PA_TUNE_CACHE"]
+    assert 0 <= v < 8
+    lines = cache.read_text().splitlines()
+    assert any(line.split("\t")[1:] == [str(3 << 18), str(v)] for line in lines), lines
+    blk = inputs.make_block(n, m, seed=8)
+    np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, n, m),
+                                  oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads()))
