@@ -79,6 +79,7 @@ def parse():
     p.add_argument("--duration", type=float, default=60.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-profile", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
 
@@ -267,6 +268,7 @@ def run_ours(args, rank, world, local):
     outs = [torch.empty(Mo, dtype=torch.int64, device=dev) for _ in blocks]
     stream = torch.cuda.current_stream(dev)
     binding.prepare(n)
+    variant = None if args.no_autotune else binding.autotune(n, reps=5)
 
     def step(i):
         x, a, b = dblocks[i % ROTATE]
@@ -364,7 +366,7 @@ def run_ours(args, rank, world, local):
 
     ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], world, dev)
     return dict(ms_total=ms_total, e2e_ms=e2e_ms, kstats=kstats, clocks=clk,
-                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms)
+                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant)
 
 
 def run_batched(args):
@@ -617,6 +619,7 @@ def main():
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"G_cd hash, one key of n={n} bits, m={m} output bits per step",
                        "transform": f"Goldilocks NTT length {N}", "seeds": f"{ROTATE} rotating blocks",
+                       "plan_variant": res["variant"],
                        "l2": f"inputs rotate over {ROTATE} blocks ({ROTATE * 3 * ((n + 63) // 64) * 8 / 1e6:.0f}"
                              f" MB) plus {2 * N * 8 / 1e6:.0f} MB workspace per step, > 129 MB L2",
                        "parallelism": f"replicas x{world}"},
