@@ -80,6 +80,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-small", action="store_true", help="skip the 10^6-bit block measurement")
     return p.parse_args()
 
 
@@ -364,9 +365,72 @@ def run_ours(args, rank, world, local):
     if not ok:
         raise RuntimeError("host-buffer results differ from device-buffer results")
 
+    small = None if args.no_small else run_small(dev, stream)
     ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], world, dev)
     return dict(ms_total=ms_total, e2e_ms=e2e_ms, kstats=kstats, clocks=clk,
-                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant)
+                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small)
+
+
+def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
+    """The 10^6-bit block (m = 2.5e5): plain launches back to back, the time of
+    each plain launch alone (events around it, median and p99 of `launches`),
+    and one-block captured graphs replayed back to back. Everything here is
+    resident in the L2 cache (inputs 0.4 MB a block, workspace 2 MB)."""
+    import torch
+
+    from paper_1910_04429_gb300 import binding
+
+    L, Mo = (n + 63) // 64, (m + 63) // 64
+    blks = [inputs.make_block(n, m, seed=100 + s) for s in range(rotate)]
+    dv = [tuple(torch.from_numpy(getattr(b, f).view(np.int64)).to(dev) for f in "xab") for b in blks]
+    outs = [torch.empty(Mo, dtype=torch.int64, device=dev) for _ in blks]
+    binding.prepare(n)
+    tuned = binding.autotune(n, reps=20)
+
+    def step(i):
+        x, a, b = dv[i % rotate]
+        binding.hash(x, a, b, n, m, out=outs[i % rotate], stream=stream)
+
+    for i in range(20):
+        step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(launches):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b2b_ms = e0.elapsed_time(e1) / launches
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(launches)]
+    for i, (a0, a1) in enumerate(evs):
+        torch.cuda.synchronize()
+        a0.record(stream)
+        step(i)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    alone = sorted(a0.elapsed_time(a1) * 1e3 for a0, a1 in evs)
+
+    graphs = [binding.Batch([(x, a, b, n, m, outs[j])]) for j, (x, a, b) in enumerate(dv)]
+    for i in range(10):
+        graphs[i % rotate].run(stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(launches):
+        graphs[i % rotate].run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / launches
+    for g in graphs:
+        g.close()
+    return {"workload": f"G_cd hash, one key of n={n} bits, m={m}, {rotate} rotating blocks, "
+                        f"L2-resident", "plan_variant": tuned,
+            "value": round(n / b2b_ms / 1e3, 1), "unit": UNIT,
+            "note": f"plain launches back to back, {launches} steps",
+            "plain_single_launch_median_us": round(alone[len(alone) // 2], 2),
+            "plain_single_launch_p99_us": round(alone[min(len(alone) - 1, int(0.99 * len(alone)))], 2),
+            "captured_graph_value": round(n / graph_ms / 1e3, 1)}
 
 
 def run_batched(args):
@@ -629,6 +693,7 @@ def main():
             "seed_reuse": None if res["seeded_ms"] is None else {
                 "value": round(aggregate_mbps(world, 1, n, res["seeded_ms"]), 1), "unit": UNIT,
                 "note": "same workload, multiplier's transform computed once (pa_hash_seeded)"},
+            "n1e6": res["small"],
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in res["kstats"].items()},
             "roofline": roofline,
             "clocks": res["clocks"]}

@@ -22,17 +22,20 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pa_oracle.c")
+_SRC_TOE = os.path.join(_HERE, "toeplitz.c")
 _LIB = os.path.join(_HERE, "libpa_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``pa_oracle.c`` into ``libpa_oracle.so`` next to it (plain gcc)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile ``pa_oracle.c`` and ``toeplitz.c`` into ``libpa_oracle.so`` next
+    to them (plain gcc)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_TOE))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, _SRC_TOE]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -51,6 +54,12 @@ def _load():
                 f.restype = ctypes.c_int
             f = lib.pa_oracle_hash
             f.argtypes = [u64p, u64p, u64p, ctypes.c_uint64, ctypes.c_uint64, u64p, ctypes.c_int]
+            f.restype = ctypes.c_int
+            f = lib.pa_oracle_toeplitz
+            f.argtypes = [u64p, u64p, ctypes.c_uint64, ctypes.c_uint64, u64p, ctypes.c_int]
+            f.restype = ctypes.c_int
+            f = lib.pa_oracle_toeplitz_bit
+            f.argtypes = [u64p, u64p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
             f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -108,6 +117,30 @@ def mul_low(a, b, threads: int = 1) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"pa_oracle_mul_low failed with {rc}")
     return out
+
+
+def toeplitz(x, s, n: int, m: int, threads: int = 1) -> np.ndarray:
+    """Toeplitz hash y = T x over GF(2), T[i][j] = s[i - j + n - 1] (m x n, seed of
+    n + m - 1 bits), as ceil(m/64) uint64 limbs (the family surveyed in Sec. 1)."""
+    if n <= 0 or m <= 0 or m > n:
+        raise ValueError(f"invalid sizes n={n} m={m}")
+    xs = _limbs(x, (n + 63) // 64)
+    ss = _limbs(s, (n + m - 1 + 63) // 64)
+    out = np.zeros((m + 63) // 64, dtype=np.uint64)
+    rc = _load().pa_oracle_toeplitz(_ptr(xs), _ptr(ss), n, m, _ptr(out), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"pa_oracle_toeplitz failed with {rc}")
+    return out
+
+
+def toeplitz_bit(x, s, n: int, m: int, i: int) -> int:
+    """Output bit i of the Toeplitz hash (row i of T against x), O(n)."""
+    xs = _limbs(x, (n + 63) // 64)
+    ss = _limbs(s, (n + m - 1 + 63) // 64)
+    r = _load().pa_oracle_toeplitz_bit(_ptr(xs), _ptr(ss), n, m, i)
+    if r < 0:
+        raise ValueError(f"invalid arguments n={n} m={m} i={i}")
+    return r
 
 
 def raw_hash_rc(n: int, m: int) -> int:

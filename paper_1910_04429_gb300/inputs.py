@@ -67,6 +67,29 @@ def make_block(n: int, m: int, seed: int = 1) -> Block:
     return Block(n, m, x, a, b, seed)
 
 
+@dataclass
+class ToeplitzBlock:
+    """One Toeplitz-hash problem: key x of n bits, seed s of n + m - 1 bits."""
+
+    n: int
+    m: int
+    x: np.ndarray
+    s: np.ndarray
+    seed: int
+
+
+def make_toeplitz_block(n: int, m: int, seed: int = 1) -> ToeplitzBlock:
+    """Uniform x (n bits) then s (n + m - 1 bits) from SplitMix64(seed)."""
+    if n <= 0 or m <= 0 or m > n:
+        raise ValueError(f"invalid sizes n={n} m={m}")
+    Lx, Ls = (n + 63) // 64, (n + m - 1 + 63) // 64
+    r = splitmix64(seed ^ 0x70E9_0000_0000_0001, 0, Lx + Ls)
+    x, s = r[:Lx].copy(), r[Lx:].copy()
+    _mask_top(x, n)
+    _mask_top(s, n + m - 1)
+    return ToeplitzBlock(n, m, x, s, seed)
+
+
 def uniforms(seed: int, count: int) -> np.ndarray:
     """``count`` doubles in [0, 1) from the top 53 bits of SplitMix64(seed)."""
     return (splitmix64(seed, 0, count) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
