@@ -81,6 +81,7 @@ def parse():
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-small", action="store_true", help="skip the 10^6-bit block measurement")
+    p.add_argument("--no-toeplitz", action="store_true", help="skip the Toeplitz-hash measurement")
     return p.parse_args()
 
 
@@ -366,9 +367,70 @@ def run_ours(args, rank, world, local):
         raise RuntimeError("host-buffer results differ from device-buffer results")
 
     small = None if args.no_small else run_small(dev, stream)
+    toep = None if args.no_toeplitz else run_toeplitz(dev, stream, args)
     ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], world, dev)
     return dict(ms_total=ms_total, e2e_ms=e2e_ms, kstats=kstats, clocks=clk,
-                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small)
+                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small,
+                toeplitz=toep)
+
+
+def run_toeplitz(dev, stream, args, sizes=((100_000_000, 25_000_000, 20), (1_000_000, 250_000, 200))):
+    """Toeplitz-hash PA (the family the paper compares against) on the same NTT
+    engine: plain pa_toeplitz back to back over 2 rotating keys, and with the
+    seed's transform reused (pa_toeplitz_seeded), per size; plus the oracle's
+    rate on a 10^6-bit block on the host cores."""
+    import torch
+
+    from paper_1910_04429_gb300 import binding
+
+    res = {}
+    for n, m, steps in sizes:
+        blks = [inputs.make_toeplitz_block(n, m, seed=1 + i) for i in range(2)]
+        dv = [(torch.from_numpy(b.x.view(np.int64)).to(dev), torch.from_numpy(b.s.view(np.int64)).to(dev))
+              for b in blks]
+        outs = [torch.empty((m + 63) // 64, dtype=torch.int64, device=dev) for _ in blks]
+
+        def step(i):
+            x, sd = dv[i % 2]
+            binding.toeplitz(x, sd, n, m, out=outs[i % 2], stream=stream)
+
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        seed = binding.ToeplitzSeed(dv[0][1], n, m, stream=stream)
+        for i in range(3):
+            seed.hash(dv[i % 2][0], out=outs[i % 2], stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(steps):
+            seed.hash(dv[i % 2][0], out=outs[i % 2], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seeded = e0.elapsed_time(e1) / steps
+        seed.close()
+        res[f"n{n:.0e}".replace("+0", "")] = {
+            "n": n, "m": m, "transform": binding.toeplitz_workspace_bytes(n, m) // 16,
+            "value": round(n / ms / 1e3, 1), "ms_per_block": round(ms, 4),
+            "seed_reuse_value": round(n / ms_seeded / 1e3, 1), "unit": UNIT}
+        del dv, outs
+    if not args.no_cpu_baseline:
+        import oracle
+
+        b = inputs.make_toeplitz_block(1_000_000, 250_000, seed=1)
+        th = oracle.default_threads()
+        t0 = time.perf_counter()
+        oracle.toeplitz(b.x, b.s, b.n, b.m, threads=th)
+        dt = time.perf_counter() - t0
+        res["cpu_oracle"] = {"value": round(b.n / dt / 1e6, 3), "unit": UNIT, "cores": th,
+                             "sample": f"one n=1e6, m=2.5e5 block, column-by-column GF(2) product, {dt:.2f} s"}
+    return res
 
 
 def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
@@ -694,6 +756,7 @@ def main():
                 "value": round(aggregate_mbps(world, 1, n, res["seeded_ms"]), 1), "unit": UNIT,
                 "note": "same workload, multiplier's transform computed once (pa_hash_seeded)"},
             "n1e6": res["small"],
+            "toeplitz": res["toeplitz"],
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in res["kstats"].items()},
             "roofline": roofline,
             "clocks": res["clocks"]}

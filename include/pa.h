@@ -244,6 +244,42 @@ int pa_plan_override(uint64_t n, int variant);
 /* pa_workspace_bytes: device workspace one pa_hash of n bits draws from the pool. */
 uint64_t pa_workspace_bytes(uint64_t n);
 
+/*
+ * Toeplitz-hash privacy amplification on the same NTT engine: the hash family
+ * the paper surveys (Sec. 1) as the usual PA choice, there computed by FFT or
+ * NTT, and the comparison workload for the modular hash. The paper does not
+ * restate the family; these calls use the usual random-Toeplitz-matrix form:
+ * an (n + m - 1)-bit seed s defines the m x n matrix over GF(2)
+ *     T[i][j] = s[i - j + n - 1],      0 <= i < m, 0 <= j < n,
+ * and the hash of an n-bit key x is the m-bit vector y = T x,
+ *     y[i] = XOR_{j<n} s[i + n - 1 - j] AND x[j].
+ * Bit vectors use the limb layout above (bit i of a vector = bit i mod 64 of
+ * limb i/64); key bits >= n and seed bits >= n + m - 1 are ignored and output
+ * bits >= m are written as zero.
+ *
+ * pa_toeplitz(key, seed, n, m, out, stream):
+ *   key  : device, ceil(n/64) limbs          seed : device, ceil((n+m-1)/64) limbs
+ *   out  : device, ceil(m/64) limbs (written)
+ *   1 <= m <= n and n + m - 1 <= PA_TOEPLITZ_MAX_BITS, else PA_EINVAL.
+ * Method: the integer convolution of the seed's and the key's bits (one bit per
+ * GF(p) coefficient, every count <= n < p, cyclic length N >= n + m - 1), whose
+ * coefficient n - 1 + i has the parity y[i]. Workspace: pa_toeplitz_workspace_bytes
+ * from the library's pool, stream-ordered as for pa_hash.
+ *
+ * Seed reuse (both parties hash with one public seed): pa_toeplitz_seed_create
+ * transforms the seed once into a pa_seed handle (ownership, streams and
+ * pa_seed_destroy as for pa_seed_create); pa_toeplitz_seeded(seed, key, out,
+ * stream) then equals pa_toeplitz for the handle's n and m. A Toeplitz handle
+ * passed to pa_hash_seeded, or a modular-hash handle passed to
+ * pa_toeplitz_seeded, is rejected with PA_EINVAL.
+ */
+#define PA_TOEPLITZ_MAX_BITS (1ull << 28) /* bound on n + m - 1 */
+int pa_toeplitz(const uint64_t* key, const uint64_t* seed, uint64_t n, uint64_t m, uint64_t* out,
+                void* stream);
+uint64_t pa_toeplitz_workspace_bytes(uint64_t n, uint64_t m);
+int pa_toeplitz_seed_create(const uint64_t* seed, uint64_t n, uint64_t m, void* stream, pa_seed* out);
+int pa_toeplitz_seeded(pa_seed seed, const uint64_t* key, uint64_t* out, void* stream);
+
 /* Per-kernel device time, aggregated by kernel name (see pa_profile). */
 typedef struct {
     char name[32];

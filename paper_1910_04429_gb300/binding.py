@@ -18,6 +18,7 @@ from . import build as _build
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_EAGAIN, PA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PA_MAX_BITS = 1 << 31
 PA_FAULT_CARRY_WAIT = 1
+PA_TOEPLITZ_MAX_BITS = 1 << 28
 
 _lock = threading.Lock()
 _lib = None
@@ -29,6 +30,11 @@ _SIGS = {
                        ctypes.c_int),
     "pa_hash_seeded": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_seed_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "pa_toeplitz": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_toeplitz_workspace_bytes": ([ctypes.c_uint64] * 2, ctypes.c_uint64),
+    "pa_toeplitz_seed_create": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "pa_toeplitz_seeded": ([ctypes.c_void_p] * 4, ctypes.c_int),
     "pa_bits_to_limbs": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                           ctypes.c_void_p], ctypes.c_int),
     "pa_limbs_to_bits": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -198,6 +204,48 @@ class Seed:
         _check(load().pa_hash_seeded(self.handle, _dev_ptr(key, limbs(self.n), "key"),
                                      _dev_ptr(seed_b, limbs(self.n), "seed_b"), m,
                                      _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)), "pa_hash_seeded")
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(load().pa_seed_destroy(self.handle), "pa_seed_destroy")
+            self.handle = None
+
+
+def toeplitz(key, seed, n: int, m: int, out=None, stream=None):
+    """Toeplitz hash y = T key over GF(2), T[i][j] = seed[i - j + n - 1] (m x n,
+    seed of n + m - 1 bits), on the GPU (asynchronous)."""
+    import torch
+
+    if out is None:
+        out = torch.empty(limbs(m), dtype=torch.int64, device=key.device)
+    _check(load().pa_toeplitz(_dev_ptr(key, limbs(n), "key"), _dev_ptr(seed, limbs(n + m - 1), "seed"),
+                              n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)), "pa_toeplitz")
+    return out
+
+
+def toeplitz_workspace_bytes(n: int, m: int) -> int:
+    return int(load().pa_toeplitz_workspace_bytes(n, m))
+
+
+class ToeplitzSeed:
+    """A Toeplitz seed transformed once (pa_toeplitz_seed_create); hash keys of
+    n bits to m bits against it with ``hash``. Free with ``close``."""
+
+    def __init__(self, seed, n: int, m: int, stream=None):
+        h = ctypes.c_void_p(0)
+        _check(load().pa_toeplitz_seed_create(_dev_ptr(seed, limbs(n + m - 1), "seed"), n, m,
+                                              _stream_ptr(stream), ctypes.byref(h)), "pa_toeplitz_seed_create")
+        self.handle, self.n, self.m = h, n, m
+
+    def hash(self, key, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(limbs(self.m), dtype=torch.int64, device=key.device)
+        _check(load().pa_toeplitz_seeded(self.handle, _dev_ptr(key, limbs(self.n), "key"),
+                                         _dev_ptr(out, limbs(self.m), "out"), _stream_ptr(stream)),
+               "pa_toeplitz_seeded")
         return out
 
     def close(self):

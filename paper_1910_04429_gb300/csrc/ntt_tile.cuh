@@ -51,13 +51,15 @@ GL_HD u64 omega_n(const Twiddles& tw, u64 e) {  // w_N^(+-e), e < N
 // ---------------------------------------------------------------------------
 struct Digits {
     const uint16_t* src;  // little-endian limbs viewed as 16-bit digits
-    u64 L;                // live digits: ceil(n / 16)
-    uint16_t top_mask;    // mask of digit L-1 (bits >= n cleared)
+    u64 L;                // live digits: ceil(n / 16), or n with one_bit
+    uint16_t top_mask;    // mask of digit L-1 (bits >= n cleared); unused with one_bit
     uint16_t sysmem;      // 1: src is host memory mapped into the device (read with plain loads)
+    uint16_t one_bit;     // 1: every bit is a digit (GF(2) vectors as 0/1 coefficients)
 };
 
 GL_HD u64 digit_at(const Digits& d, u64 pos) {
     if (pos >= d.L) return 0;  // zero fill (Algorithm 1, step 1)
+    if (d.one_bit) return (d.src[pos >> 4] >> (pos & 15)) & 1u;
     uint16_t v = d.src[pos];
     if (pos == d.L - 1) v &= d.top_mask;
     return v;

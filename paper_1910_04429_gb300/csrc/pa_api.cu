@@ -118,10 +118,9 @@ int applicable_variants(const Geom& g) {
     return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV;
 }
 
-// The plan for keys of n bits on device dev: the transform length of
-// choose_geom, with the variant forced for it, else the tuned one, else 0.
-Geom plan_for(int dev, uint64_t n) {
-    Geom base = geom_for_bits(n);
+// The plan for a transform length on device dev: base's length, with the
+// variant forced for it, else the tuned one, else 0.
+Geom plan_for_base(int dev, const Geom& base) {
     Device& d = g_dev[dev];
     int v = 0;
     auto f = d.forced.find(base.N);
@@ -131,6 +130,20 @@ Geom plan_for(int dev, uint64_t n) {
         if (t != d.tuned.end()) v = t->second;
     }
     return make_geom(base.logN, base.three, v & applicable_variants(base));
+}
+
+// ... for keys of n bits (the modular hash)
+Geom plan_for(int dev, uint64_t n) { return plan_for_base(dev, geom_for_bits(n)); }
+
+// ... for Toeplitz hashes of n key bits and m output bits
+bool check_toeplitz(uint64_t n, uint64_t m) {
+    return n >= 1 && m >= 1 && m <= n && n + m - 1 <= PA_TOEPLITZ_MAX_BITS;
+}
+Geom toeplitz_base(uint64_t n, uint64_t m) { return choose_geom_len(n + m - 1); }
+
+// The key's (and seed's) bits as one-bit digits of the convolution.
+Digits bit_digits(const uint64_t* v, uint64_t bits) {
+    return Digits{reinterpret_cast<const uint16_t*>(v), bits, 0xFFFF, 0, 1};
 }
 
 // Tuning cache file (PA_TUNE_CACHE): lines "<gpu name>\t<N>\t<variant>".
@@ -602,6 +615,8 @@ struct pa_seed_s {
     uint64_t n;
     Geom G;
     u64* spec;  // the seed's spectrum, N words (tile register order, times N^-1)
+    uint64_t m = 0;         // Toeplitz handles: output bits
+    bool toeplitz = false;  // a Toeplitz seed (one-bit digits, n + m - 1 bits)
 };
 
 extern "C" {
@@ -634,6 +649,7 @@ int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* ou
 int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, uint64_t m,
                    uint64_t* out, void* stream) {
     if (!seed || !key || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_seeded: null pointer");
+    if (seed->toeplitz) return fail(PA_EINVAL, "pa_hash_seeded: a Toeplitz seed handle");
     if (m < 1 || m > seed->n) return fail(PA_EINVAL, "pa_hash_seeded: need 1 <= m <= n");
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
@@ -656,6 +672,97 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
     cudaError_t e = launch_convolution_seeded(j, st);
     if (e != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
     return queue_carry(j.buf_x, j.L, seed_b, seed->n, m, out, st, scr);
+}
+
+int pa_toeplitz(const uint64_t* key, const uint64_t* seed, uint64_t n, uint64_t m, uint64_t* out,
+                void* stream) {
+    if (!check_toeplitz(n, m))
+        return fail(PA_EINVAL, "pa_toeplitz: need 1 <= m <= n, n + m - 1 <= PA_TOEPLITZ_MAX_BITS");
+    if (!key || !seed || !out) return fail(PA_EINVAL, "pa_toeplitz: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch scr(st, pool);
+    NttJob j;
+    j.geom = plan_for_base(dev, toeplitz_base(n, m));
+    j.L = n + m - 1;  // the last inverse pass keeps coefficients below n + m - 1
+    if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+    void *bx, *ba;
+    if ((rc = scr.get(j.geom.N * sizeof(u64), &bx)) || (rc = scr.get(j.geom.N * sizeof(u64), &ba))) return rc;
+    j.buf_x = (u64*)bx;
+    j.buf_a = j.ahat = (u64*)ba;
+    j.dx = bit_digits(key, n);
+    j.da = bit_digits(seed, n + m - 1);
+    cudaError_t e = launch_convolution(j, st);
+    if (e != cudaSuccess) return cuda_fail(e, "Toeplitz NTT launch");
+    if ((e = launch_parity_extract(j.buf_x, n - 1, m, out, st)) != cudaSuccess)
+        return cuda_fail(e, "parity launch");
+    return PA_OK;
+}
+
+uint64_t pa_toeplitz_workspace_bytes(uint64_t n, uint64_t m) {
+    if (!check_toeplitz(n, m)) return 0;
+    return 2 * toeplitz_base(n, m).N * sizeof(u64);
+}
+
+int pa_toeplitz_seed_create(const uint64_t* seed, uint64_t n, uint64_t m, void* stream, pa_seed* out) {
+    if (!check_toeplitz(n, m))
+        return fail(PA_EINVAL, "pa_toeplitz_seed_create: need 1 <= m <= n, n + m - 1 <= PA_TOEPLITZ_MAX_BITS");
+    if (!seed || !out) return fail(PA_EINVAL, "pa_toeplitz_seed_create: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    NttJob j;
+    j.geom = plan_for_base(dev, toeplitz_base(n, m));
+    j.L = n + m - 1;
+    if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+    u64* spec = nullptr;
+    cudaError_t e = cudaMalloc(&spec, j.geom.N * sizeof(u64));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(seed spectrum)");
+    j.buf_x = j.buf_a = j.ahat = spec;
+    j.da = j.dx = bit_digits(seed, n + m - 1);
+    if ((e = launch_seed_spectrum(j, (cudaStream_t)stream)) != cudaSuccess) {
+        cudaFree(spec);
+        return cuda_fail(e, "seed transform launch");
+    }
+    pa_seed_s* h = new pa_seed_s{dev, n, j.geom, spec};
+    h->m = m;
+    h->toeplitz = true;
+    *out = h;
+    return PA_OK;
+}
+
+int pa_toeplitz_seeded(pa_seed seed, const uint64_t* key, uint64_t* out, void* stream) {
+    if (!seed || !key || !out) return fail(PA_EINVAL, "pa_toeplitz_seeded: null pointer");
+    if (!seed->toeplitz) return fail(PA_EINVAL, "pa_toeplitz_seeded: a modular-hash seed handle");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    if (dev != seed->dev) return fail(PA_EINVAL, "pa_toeplitz_seeded: seed made on another device");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch scr(st, pool);
+    const uint64_t n = seed->n, m = seed->m;
+    NttJob j;
+    j.geom = seed->G;
+    j.L = n + m - 1;
+    if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+    void* bx;
+    if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
+    j.buf_x = (u64*)bx;
+    j.buf_a = j.ahat = seed->spec;
+    j.dx = j.da = bit_digits(key, n);
+    cudaError_t e = launch_convolution_seeded(j, st);
+    if (e != cudaSuccess) return cuda_fail(e, "seeded Toeplitz NTT launch");
+    if ((e = launch_parity_extract(j.buf_x, n - 1, m, out, st)) != cudaSuccess)
+        return cuda_fail(e, "parity launch");
+    return PA_OK;
 }
 
 int pa_seed_destroy(pa_seed seed) {

@@ -77,6 +77,10 @@ void fault_inject_carry();
 // Sticky device status bits (PA_STATUS_*); synchronous.
 cudaError_t read_device_status(u32* out, bool clear);
 
+// Toeplitz hash, last step: out bit i = coef[first + i] mod 2 for i < m,
+// ceil(m/64) little-endian limbs (bits >= m zero).
+cudaError_t launch_parity_extract(const u64* coef, u64 first, u64 m, u64* out, cudaStream_t st);
+
 // Per-kernel timing with CUDA events on the launching stream (off unless
 // pa_profile(1) was called). prof_begin/prof_end bracket one launch.
 void prof_begin(cudaStream_t st, const char* name);

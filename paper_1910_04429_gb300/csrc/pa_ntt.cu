@@ -332,7 +332,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     bool aligned = true;
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
-                  !nb.io[i].dx.sysmem && !nb.io[i].da.sysmem;
+                  !nb.io[i].dx.sysmem && !nb.io[i].da.sysmem && !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
@@ -379,7 +379,7 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;
     nb.io[0] = BlockIO{j.buf_a, j.buf_a, j.da, j.da, j.L};
-    bool aligned = (uintptr_t)j.da.src % 16 == 0;
+    bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.sysmem && !j.da.one_bit;
     const Geom& G = j.geom;
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, p);

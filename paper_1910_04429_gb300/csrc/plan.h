@@ -69,16 +69,19 @@ inline int logn_for_digits(uint64_t L) {
 }
 
 // The shortest transform, 2^k or 3 * 2^k (with a first radix of at most 48),
-// that holds the linear convolution of two L-digit operands.
-inline Geom choose_geom(uint64_t L) {
-    uint64_t need = 2 * L - 1;
-    int k = logn_for_digits(L);
+// of at least `need` points (and at least one 4096-point tile).
+inline Geom choose_geom_len(uint64_t need) {
+    int k = LOG_TILE;
+    while ((1ull << k) < need) k++;
     for (int j = LOG_TILE; j < k; j++) {
         bool fits = (3ull << j) >= need && (3ull << j) < (1ull << k);
         if (fits && (j - LOG_TILE) % 6 <= 4) return make_geom(j, 1);
     }
     return make_geom(k, 0);
 }
+
+// ... that holds the linear convolution of two L-digit operands.
+inline Geom choose_geom(uint64_t L) { return choose_geom_len(2 * L - 1); }
 
 // A primitive (3 * 2^32)-th root of unity R with R^(2^26) = 2: every
 // w_N = R^(3 * 2^32 / N) then satisfies w_N^(N/192) = 2 when 192 | N and

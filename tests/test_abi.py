@@ -107,6 +107,16 @@ def test_argument_checks_without_gpu():
     assert lib.pa_seed_create(p, 0, null, ctypes.byref(h)) == binding.PA_EINVAL
     assert lib.pa_hash_seeded(null, p, p, 10, p, null) == binding.PA_EINVAL
     assert lib.pa_seed_destroy(null) == binding.PA_OK
+    # Toeplitz: 1 <= m <= n, n + m - 1 <= PA_TOEPLITZ_MAX_BITS, non-null pointers
+    cap = binding.PA_TOEPLITZ_MAX_BITS
+    for n, m in ((0, 1), (10, 0), (10, 11), (cap, 2), (cap + 1, 1)):
+        assert lib.pa_toeplitz(p, p, n, m, p, null) == binding.PA_EINVAL
+        assert lib.pa_toeplitz_seed_create(p, n, m, null, ctypes.byref(h)) == binding.PA_EINVAL
+        assert lib.pa_toeplitz_workspace_bytes(n, m) == 0
+    assert lib.pa_toeplitz(p, null, 10, 5, p, null) == binding.PA_EINVAL
+    assert lib.pa_toeplitz(p, p, 10, 5, null, null) == binding.PA_EINVAL
+    assert lib.pa_toeplitz_seed_create(null, 10, 5, null, ctypes.byref(h)) == binding.PA_EINVAL
+    assert lib.pa_toeplitz_seeded(null, p, p, null) == binding.PA_EINVAL
     # the fixed-scratch entry point refuses keys beyond its scratch size
     assert lib.pa_hash_noalloc(p, p, p, (1 << 20) + 1, 1, p, null) == binding.PA_EINVAL
     assert b"PA_NOALLOC_MAX_BITS" in lib.pa_last_error()
@@ -131,3 +141,12 @@ def test_workspace_bytes(n, N):
     tiles = -(-(-(-n // 64)) // 1024)
     assert binding.workspace_bytes(n) == 2 * N * 8 + 4 * (tiles + 1)
     assert binding.workspace_bytes(0) == 0
+
+
+@pytest.mark.parametrize("n,m,N", [(1, 1, 4096), (2048, 2049 - 2048, 4096), (3000, 1097, 4096),
+                                   (3000, 1098, 8192), (1_000_000, 250_000, 3 << 19),
+                                   (100_000_000, 25_000_000, 1 << 27)])
+def test_toeplitz_workspace_bytes(n, m, N):
+    """Toeplitz transform length: smallest 2^k or 3 * 2^k (first radix <= 48)
+    that is >= max(4096, n + m - 1); two N-word buffers."""
+    assert binding.toeplitz_workspace_bytes(n, m) == 2 * N * 8
