@@ -17,10 +17,13 @@
 // and addend limbs in shared memory with coalesced loads, scans its (g, p)
 // pairs, publishes the tile aggregate, walks back over the published states of
 // earlier tiles to obtain its carry-in, publishes its inclusive prefix, and
-// writes its output bits. Warp 0 reads 32 predecessor states per round, so a
-// tile does not wait for the inclusive prefix of its neighbour. Every wait on another tile is bounded: when the
+// writes its output bits. Warp 0 reads 32 predecessor states per round and
+// stops at the latest one that fixes its carry out (an inclusive prefix, or an
+// aggregate with P = 0, which random data gives almost always): a tile rarely
+// waits for more than its neighbour's aggregate. Every wait on another tile is bounded: when the
 // limit runs out the kernel records PA_STATUS_TIMEOUT in the device status word
 // and carries on with a carry-in of 0, so it always terminates.
+#include "cp_async.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -43,6 +46,7 @@ constexpr int HALO_LO = 2, HALO_HI = 1;                       // extra limbs bef
 constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 1024
 constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 1027
 constexpr int SM_COEF = 4 * SM_LIMBS;                         // 4108
+constexpr int SM_LIMBS_PAD = SM_LIMBS + 1;                    // whole 16-byte chunks
 
 struct Limb {
     u64 lo;   // u_j mod 2^64
@@ -124,11 +128,23 @@ __device__ __forceinline__ u32 observe(const u32* p) {
     return v;
 }
 
-template <int B>
+// Words [w0, w0 + 2 * chunks) of src (count words live) into dst with 16-byte
+// copies; words outside [0, count) read as zero. Needs src 16-byte aligned and
+// w0 even.
+__device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long w0, int chunks, u64 count) {
+    for (int ch = threadIdx.x; ch < chunks; ch += CARRY_THREADS) {
+        long long k = w0 + 2 * ch;
+        int live = (k < 0 || (u64)k >= count) ? 0 : ((u64)k + 1 < count ? 2 : 1);
+        cp_async16(dst + 2 * ch, live ? src + k : src, 8 * live);
+    }
+}
+
+// VEC: coef and b are 16-byte aligned (staged with cp.async), else plain loads.
+template <int B, bool VEC>
 __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
                                                          u32 ticket_start, u32 spin_limit) {
-    __shared__ u64 cs[SM_COEF];
-    __shared__ u64 bs[SM_LIMBS];
+    __shared__ __align__(16) u64 cs[SM_COEF];
+    __shared__ __align__(16) u64 bs[SM_LIMBS_PAD];
     __shared__ u32 tile_sh;
     __shared__ int carry_in_sh;
     const CarryJob& c = cb.job[blockIdx.y];
@@ -141,13 +157,20 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
 
     // stage digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS), J0 = 1024 t - 2
     const long long J0 = (long long)t * TILE_LIMBS - HALO_LO;
-    for (int i = threadIdx.x; i < SM_COEF; i += CARRY_THREADS) {
-        long long k = 4 * J0 + i;
-        cs[i] = (k >= 0 && (u64)k < c.L) ? c.coef[k] : 0;
-    }
-    for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
-        long long j = J0 + i;
-        bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
+    if (VEC) {
+        stage_pairs(cs, c.coef, 4 * J0, SM_COEF / 2, c.L);
+        stage_pairs(bs, c.b, J0, SM_LIMBS_PAD / 2, Ly);
+        cp_async_commit();
+        cp_async_wait<0>();
+    } else {
+        for (int i = threadIdx.x; i < SM_COEF; i += CARRY_THREADS) {
+            long long k = 4 * J0 + i;
+            cs[i] = (k >= 0 && (u64)k < c.L) ? c.coef[k] : 0;
+        }
+        for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
+            long long j = J0 + i;
+            bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
+        }
     }
     __syncthreads();
 
@@ -188,7 +211,9 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
                         s = observe(&state[i]);
                     }
                 }
-                unsigned inc = __ballot_sync(0xffffffffu, (s & ST_INC) != 0);
+                // a tile whose state fixes its carry out whatever comes before it: an
+                // inclusive prefix, or an aggregate that does not propagate (P = 0)
+                unsigned inc = __ballot_sync(0xffffffffu, (s & ST_INC) != 0 || !(s & 2u));
                 int stop = inc ? __ffs(inc) - 1 : 31;  // lanes 0 .. stop take part
                 int v = lane <= stop ? (int)(s & 3u) : GP_IDENTITY;
                 // lane 0 ends with tiles (base - stop .. base) composed in tile order
@@ -251,9 +276,15 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     u32 start = g_inject_ticket;
     u32 limit = start ? 1000u : CARRY_SPIN_LIMIT;
     g_inject_ticket = 0;
+    bool vec = true;
+    for (int i = 0; i < cb.count; i++)
+        vec = vec && (uintptr_t)cb.job[i].coef % 16 == 0 && (uintptr_t)cb.job[i].b % 16 == 0;
     dim3 grid((unsigned)tiles, (unsigned)cb.count);
     prof_begin(st, "carry_lookback");
-    k_carry<B><<<grid, CARRY_THREADS, 0, st>>>(cb, start, limit);
+    if (vec)
+        k_carry<B, true><<<grid, CARRY_THREADS, 0, st>>>(cb, start, limit);
+    else
+        k_carry<B, false><<<grid, CARRY_THREADS, 0, st>>>(cb, start, limit);
     prof_end(st);
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <unordered_set>
 
+#include "cp_async.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -15,15 +16,6 @@ namespace pa {
 // ---------------------------------------------------------------------------
 // asynchronous staging of tile inputs (cp.async, 16-byte chunks)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Words of a tile (R rows at stride S, C columns) into stage[d * C + c]. Tile
 // bases and strides are even, so every 16-byte chunk is aligned.
 template <int R, int C>
