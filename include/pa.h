@@ -75,15 +75,26 @@ int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
 
 /*
  * pa_hash_host: pa_hash on HOST buffers (same shapes); returns with `out`
- * filled (it waits for `stream`). key and seed_a are copied to device staging
- * buffers from the library's pool first; seed_b is copied on a second stream
- * while the transforms run. If `out` is pinned (page-locked and mapped, e.g.
+ * filled (it waits for `stream`). key and seed_a are copied into device
+ * staging buffers from the library's pool on the library's copy stream, and
+ * seed_b behind them, so b's copy overlaps the transforms; the hash waits on
+ * each copy with an event. If `out` is pinned (page-locked and mapped, e.g.
  * cudaHostAlloc) the last kernel writes the result into it directly (over
- * NVLink-C2C on Grace systems); otherwise it is copied back. Pinned inputs
- * make the copies asynchronous; pageable memory also works.
+ * NVLink-C2C on Grace systems); otherwise it is copied back on `stream`.
+ * Pinned inputs make the copies asynchronous; pageable memory also works.
+ *
+ * pa_hash_host_async: the same, returning once everything is queued. The
+ * copy stream runs at most two calls ahead of the hashes (staging memory is
+ * bounded to three calls' inputs), so back-to-back calls overlap one call's
+ * input copies with the previous call's transforms. The caller must keep key,
+ * seed_a, seed_b and out valid, leave the inputs unmodified and not read out
+ * until `stream` has passed the call (e.g. cudaStreamSynchronize). With
+ * pageable buffers the copies block the host and nothing overlaps.
  */
 int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
                  uint64_t n, uint64_t m, uint64_t* out, void* stream);
+int pa_hash_host_async(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
+                       uint64_t n, uint64_t m, uint64_t* out, void* stream);
 
 /*
  * pa_convolve16: the digit product of Algorithm 1 steps 1-5 (zero fill,

@@ -48,6 +48,7 @@ _SIGS = {
     "pa_autotune": ([ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pa_plan_override": ([ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
+    "pa_hash_host_async": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_carry_extract": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
@@ -254,19 +255,39 @@ class ToeplitzSeed:
             self.handle = None
 
 
-def hash_host(key: np.ndarray, seed_a: np.ndarray, seed_b: np.ndarray, n: int, m: int,
-              out: np.ndarray | None = None, stream=None) -> np.ndarray:
+def _host_ptr(v, count: int, name: str):
+    """Address of a host buffer: a contiguous uint64 numpy array, or a CPU
+    int64/uint64 torch tensor (e.g. pinned)."""
+    if isinstance(v, np.ndarray):
+        if v.dtype != np.uint64 or not v.flags.c_contiguous or v.size < count:
+            raise ValueError(f"{name} must be a contiguous uint64 array of >= {count} limbs")
+        return ctypes.c_void_p(v.ctypes.data)
+    import torch
+
+    if not isinstance(v, torch.Tensor) or v.is_cuda or v.dtype not in (torch.int64, torch.uint64) \
+            or not v.is_contiguous() or v.numel() < count:
+        raise ValueError(f"{name} must be a contiguous host uint64 array or int64 tensor of >= {count} limbs")
+    return ctypes.c_void_p(v.data_ptr())
+
+
+def hash_host(key, seed_a, seed_b, n: int, m: int, out=None, stream=None):
     """pa_hash_host: host arrays in, host array out (synchronous)."""
     L = limbs(n)
-    arrs = []
-    for name, v in (("key", key), ("seed_a", seed_a), ("seed_b", seed_b)):
-        if v.dtype != np.uint64 or not v.flags.c_contiguous or v.size < L:
-            raise ValueError(f"{name} must be a contiguous uint64 array of >= {L} limbs")
-        arrs.append(ctypes.c_void_p(v.ctypes.data))
+    arrs = [_host_ptr(v, L, nm) for nm, v in (("key", key), ("seed_a", seed_a), ("seed_b", seed_b))]
     if out is None:
         out = np.zeros(limbs(m), dtype=np.uint64)
     st = ctypes.c_void_p(0) if stream is None else _stream_ptr(stream)
-    _check(load().pa_hash_host(*arrs, n, m, ctypes.c_void_p(out.ctypes.data), st), "pa_hash_host")
+    _check(load().pa_hash_host(*arrs, n, m, _host_ptr(out, limbs(m), "out"), st), "pa_hash_host")
+    return out
+
+
+def hash_host_async(key, seed_a, seed_b, n: int, m: int, out, stream=None):
+    """pa_hash_host_async: queued host-buffer hash (pinned buffers overlap with
+    earlier calls); ``out`` is valid once ``stream`` has passed the call."""
+    L = limbs(n)
+    arrs = [_host_ptr(v, L, nm) for nm, v in (("key", key), ("seed_a", seed_a), ("seed_b", seed_b))]
+    st = ctypes.c_void_p(0) if stream is None else _stream_ptr(stream)
+    _check(load().pa_hash_host_async(*arrs, n, m, _host_ptr(out, limbs(m), "out"), st), "pa_hash_host_async")
     return out
 
 

@@ -39,6 +39,11 @@ struct Device {
     std::unordered_map<u64, u64*> tables;  // transform length N -> device twiddle tables
     cudaStream_t side[SIDE_STREAMS] = {};  // forked from the caller's stream per batch
     cudaEvent_t fork = nullptr, join[SIDE_STREAMS] = {};
+    // host-buffer calls: input copies run on `copy`, at most two calls ahead
+    // of the hashes (done[i % 2] marks the end of call i's hash and frees)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t xa_ready = nullptr, b_ready = nullptr, done[2] = {};
+    u64 host_calls = 0;
 };
 
 std::mutex g_mu;
@@ -61,6 +66,11 @@ int get_pool(int dev, cudaMemPool_t* out) {
         if (e != cudaSuccess) { d.pool = nullptr; return cuda_fail(e, "cudaMemPoolCreate"); }
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        // reuse across streams only along event dependencies (or when the free has
+        // completed): an allocation on the copy stream never gains a hidden wait
+        // on a hash stream
+        int no = 0;
+        cudaMemPoolSetAttribute(d.pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
     *out = d.pool;
     return PA_OK;
@@ -259,6 +269,10 @@ int side_streams(int dev) {
         e = cudaStreamCreateWithFlags(&d.side[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.join[i], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d.copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.xa_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.b_ready, cudaEventDisableTiming);
+    for (int i = 0; e == cudaSuccess && i < 2; i++) e = cudaEventCreateWithFlags(&d.done[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         d.fork = nullptr;
         return cuda_fail(e, "side stream set-up");
@@ -359,6 +373,63 @@ int setup(int* dev, cudaMemPool_t* pool) {
     return get_pool(*dev, pool);
 }
 
+// Host buffers in, host buffer out, queued without waiting: x and a are copied
+// on the device's copy stream (two calls at most ahead of the hashes, so the
+// next call's copies overlap this call's transforms), b behind them, the hash
+// runs on st after each copy's event, and a pinned result buffer is written in
+// place by the carry kernel (else copied back on st).
+int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
+                    uint64_t m, uint64_t* out, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev, rc;
+    cudaMemPool_t pool;
+    if ((rc = setup(&dev, &pool))) return rc;
+    if ((rc = side_streams(dev))) return rc;
+    Device& d = g_dev[dev];
+    size_t in_bytes = ((n + 63) / 64) * sizeof(u64), out_bytes = ((m + 63) / 64) * sizeof(u64);
+    cudaEvent_t done = d.done[d.host_calls & 1];  // recorded by the call two before this one
+    cudaError_t e = cudaSuccess;
+    if (d.host_calls >= 2) e = cudaStreamWaitEvent(d.copy, done, 0);
+    void *dx = nullptr, *da = nullptr, *db = nullptr;
+    if (!e) e = cudaMallocFromPoolAsync(&dx, in_bytes, pool, d.copy);
+    if (!e) e = cudaMallocFromPoolAsync(&da, in_bytes, pool, d.copy);
+    if (!e) e = cudaMallocFromPoolAsync(&db, in_bytes, pool, d.copy);
+    if (!e) e = cudaMemcpyAsync(dx, key, in_bytes, cudaMemcpyHostToDevice, d.copy);
+    if (!e) e = cudaMemcpyAsync(da, seed_a, in_bytes, cudaMemcpyHostToDevice, d.copy);
+    if (!e) e = cudaEventRecord(d.xa_ready, d.copy);
+    if (!e) e = cudaMemcpyAsync(db, seed_b, in_bytes, cudaMemcpyHostToDevice, d.copy);
+    // b's event is recorded even after a failure, so that st can order the frees
+    cudaError_t eb = cudaEventRecord(d.b_ready, d.copy);
+    if (!e) e = eb;
+    {
+        Scratch scr(st, pool);  // frees the inputs and the workspace on st, in order
+        for (void* p : {dx, da, db})
+            if (p) scr.ptrs.push_back(p);
+        if (e) {
+            cudaStreamWaitEvent(st, d.b_ready, 0);
+            return cuda_fail(e, "host-buffer copies");
+        }
+        void* mo = nullptr;
+        bool out_mapped = host_mapped(out, &mo);
+        if ((e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
+            cudaStreamWaitEvent(st, d.b_ready, 0);
+            return cuda_fail(e, "cudaStreamWaitEvent");
+        }
+        u64* coef = nullptr;
+        rc = queue_convolution((const u64*)dx, (const u64*)da, n, st, scr, dev, &coef);
+        if ((e = cudaStreamWaitEvent(st, d.b_ready, 0))) return cuda_fail(e, "cudaStreamWaitEvent");
+        if (rc) return rc;
+        if (!out_mapped && (rc = scr.get(out_bytes, &mo))) return rc;
+        if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr))) return rc;
+        if (!out_mapped && (e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
+            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    }
+    if ((e = cudaEventRecord(done, st))) return cuda_fail(e, "cudaEventRecord");
+    d.host_calls++;
+    return PA_OK;
+}
+
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -447,40 +518,18 @@ int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* se
     if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_hash_host: need 1 <= m <= n <= PA_MAX_BITS");
     if (!key || !seed_a || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_host: null pointer");
     cudaStream_t st = (cudaStream_t)stream;
-    int rc;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        int dev;
-        cudaMemPool_t pool;
-        if ((rc = setup(&dev, &pool))) return rc;
-        if ((rc = side_streams(dev))) return rc;
-        Device& d = g_dev[dev];
-        Scratch scr(st, pool);
-        size_t in_bytes = ((n + 63) / 64) * sizeof(u64), out_bytes = ((m + 63) / 64) * sizeof(u64);
-        void *dx, *da, *db, *mo = nullptr;
-        if ((rc = scr.get(in_bytes, &dx)) || (rc = scr.get(in_bytes, &da)) || (rc = scr.get(in_bytes, &db)))
-            return rc;
-        // a pinned result buffer is written in place by the carry kernel
-        bool out_mapped = host_mapped(out, &mo);
-        if (!out_mapped && (rc = scr.get(out_bytes, &mo))) return rc;
-        cudaError_t e;
-        // x and a first (the transforms need them); b on a side stream while they run
-        if ((e = cudaEventRecord(d.fork, st)) || (e = cudaStreamWaitEvent(d.side[0], d.fork, 0)) ||
-            (e = cudaMemcpyAsync(dx, key, in_bytes, cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(da, seed_a, in_bytes, cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(db, seed_b, in_bytes, cudaMemcpyHostToDevice, d.side[0])) ||
-            (e = cudaEventRecord(d.join[0], d.side[0])))
-            return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-        u64* coef = nullptr;
-        if ((rc = queue_convolution((const u64*)dx, (const u64*)da, n, st, scr, dev, &coef))) return rc;
-        if ((e = cudaStreamWaitEvent(st, d.join[0], 0))) return cuda_fail(e, "cudaStreamWaitEvent");
-        if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr))) return rc;
-        if (!out_mapped && (e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
-            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
-    }
+    int rc = queue_hash_host(key, seed_a, seed_b, n, m, out, st);
+    if (rc) return rc;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return PA_OK;
+}
+
+int pa_hash_host_async(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
+                       uint64_t n, uint64_t m, uint64_t* out, void* stream) {
+    if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_hash_host_async: need 1 <= m <= n <= PA_MAX_BITS");
+    if (!key || !seed_a || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_host_async: null pointer");
+    return queue_hash_host(key, seed_a, seed_b, n, m, out, (cudaStream_t)stream);
 }
 
 int pa_convolve16(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t* coef,

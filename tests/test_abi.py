@@ -84,6 +84,7 @@ def test_argument_checks_without_gpu():
     for n, m in ((0, 1), (10, 0), (10, 11), (binding.PA_MAX_BITS + 64, 1)):
         assert lib.pa_hash(p, p, p, n, m, p, null) == binding.PA_EINVAL
         assert lib.pa_hash_host(p, p, p, n, m, p, null) == binding.PA_EINVAL
+        assert lib.pa_hash_host_async(p, p, p, n, m, p, null) == binding.PA_EINVAL
         assert lib.pa_carry_extract(p, 1, p, n, m, p, null) == binding.PA_EINVAL
     # null pointers
     assert lib.pa_hash(null, p, p, 10, 5, p, null) == binding.PA_EINVAL

@@ -185,6 +185,36 @@ def test_hash_host_pinned_zero_copy(n, m):
         np.testing.assert_array_equal(out.numpy().view(np.uint64), want)
 
 
+def test_hash_host_async_pipeline():
+    """Back-to-back pa_hash_host_async calls (pinned and pageable buffers, one
+    stream and two alternating streams): every result equals the oracle's once
+    the streams are synchronised; the copy stream's run-ahead limit is crossed."""
+    import torch
+
+    sizes = [(3_000_017, 800_001), (1000, 333), (10_000_000, 2_500_000), (65_536, 65_536),
+             (3_000_017, 1), (1_536_001, 700_000), (777_777, 77_777)]
+    blks = [inputs.make_block(n, m, seed=40 + i) for i, (n, m) in enumerate(sizes)]
+    want = [oracle.pa_hash(b.x, b.a, b.b, b.n, b.m, threads=oracle.default_threads()) for b in blks]
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    for pinned in (True, False):
+        for nstreams in (1, 2):
+            ins, outs = [], []
+            for i, b in enumerate(blks):
+                if pinned:
+                    v = [torch.from_numpy(a.view(np.int64)).pin_memory() for a in (b.x, b.a, b.b)]
+                    o = torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64).pin_memory()
+                else:
+                    v = [b.x, b.a, b.b]
+                    o = np.full((b.m + 63) // 64, 7, dtype=np.uint64)
+                ins.append(v)
+                outs.append(o)
+                binding.hash_host_async(*v, b.n, b.m, o, stream=streams[i % nstreams])
+            torch.cuda.synchronize()
+            for o, w in zip(outs, want):
+                got = o.numpy().view(np.uint64) if pinned else o
+                np.testing.assert_array_equal(got, w)
+
+
 def test_nondefault_streams_and_repeat():
     import torch
 
