@@ -165,38 +165,30 @@ def load_peaks():
 # instruction every second cycle per scheduler) x the maximum SM clock.
 SMS, ALU_LANES_PER_SM = 152, 64
 
-# Cost model: int32 ALU-pipe instructions of the minimal exact sequences for
-# one Goldilocks operation (values kept in [0, p]): modular add = 64-bit add,
-# add of 2^64 mod p, select (6); modular sub = 64-bit sub, borrow-masked fix
-# (5); multiply by a constant 2^s = 96-bit shift + fold of the top word (its
-# product on the FMA pipe) + carry fix + canonical select (11); general
-# modmul = reduction of the 128-bit product (4 IMAD.WIDE on the FMA pipe,
-# not counted) (15).
-COST = {"add": 6, "sub": 5, "shl": 11, "mul": 15}
-
-
-def contig_ops_per_word(seed: bool) -> dict:
-    """Operation counts per transform word of the 4096-point tile transform
-    (64 x 64, each 64-point DFT as 8 x 8 with length-8 DFTs of 12 butterflies
-    and 5 root multiplies, 49 non-trivial middle roots, 3969 non-trivial
-    w_4096 twiddles per tile): seed = forward + scale by N^-1; fused =
-    forward + pointwise product + inverse."""
-    per64 = {"add": 192, "sub": 192, "shl": 16 * 5 + 49}
-    t = {k: 128 * v / 4096 for k, v in per64.items()}
-    t["mul"] = 3969 / 4096
-    if seed:
-        return {"add": t["add"], "sub": t["sub"], "shl": t["shl"], "mul": t["mul"] + 1}
-    return {"add": 2 * t["add"], "sub": 2 * t["sub"], "shl": 2 * t["shl"], "mul": 2 * t["mul"] + 1}
+# Roofline work model. The algorithmic work of a length-N transform is
+# (N/2) log2 N radix-2 butterflies, each one Goldilocks modmul plus one modular
+# add and one modular sub; its cost is counted in ALU-pipe instructions of the
+# exact sequences, as measured per primitive with ncu pipe counters on a
+# chained probe: modmul 11 (its four 32 x 32 products and folds run on the FMA
+# pipe and are not counted), add 5 (the sub of p - b), sub 3. Pointwise
+# products and the N^-1 scaling are one modmul per word. (The kernels replace
+# most butterfly modmuls by multiplies by powers of two, 1-8 ALU instructions
+# each, so a kernel may do this work in fewer instructions than counted.)
+COST = {"add": 5, "sub": 3, "mul": 11}
+BUTTERFLY = COST["add"] + COST["sub"] + COST["mul"]
 
 
 def alu_ops(name: str, N: int):
+    """Butterfly-model ALU operations of one launch of the contiguous-tile
+    kernels: the 4096-point tile transform is 12 radix-2 stages; seed = one
+    forward tile transform + N^-1 scaling, fused = forward + pointwise product
+    + inverse."""
+    stage = N // 2 * BUTTERFLY
     if name == "ntt_contig_fused":
-        ops = contig_ops_per_word(False)
-    elif name == "ntt_contig_seed":
-        ops = contig_ops_per_word(True)
-    else:
-        return None
-    return N * sum(COST[k] * v for k, v in ops.items())
+        return 2 * 12 * stage + N * COST["mul"]
+    if name == "ntt_contig_seed":
+        return 12 * stage + N * COST["mul"]
+    return None
 
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
@@ -731,8 +723,9 @@ def main():
                              "unit": "Tops/s", "frac": round(achieved / alu_peak, 4),
                              "peak_source": f"derived: {SMS} SMs x {ALU_LANES_PER_SM} int32 ALU lanes x "
                                             f"{mhz:.0f} MHz ({src} max clock)",
-                             "ops_model": "ALU-pipe int32 ops: add 6, sub 5, shift-multiply 11, "
-                                          "modmul 15 per Goldilocks operation"})
+                             "ops_model": "radix-2 butterflies ((N/2) log2 N per transform) x (modmul 11 + "
+                                          "add 5 + sub 3 ALU instructions, measured sequences) + 11 per "
+                                          "pointwise product"})
         else:
             roofline.update({"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak,
                              "unit": "GB/s", "frac": round(hbm_achieved / hbm_peak, 4)})

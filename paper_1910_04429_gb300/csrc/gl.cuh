@@ -146,60 +146,6 @@ GL_HD u64 pow(u64 b, u64 e) {
 
 namespace gl {
 
-// 2^s mod p for s in [0, 192)
-#if defined(__CUDACC__)
-static __constant__ u64 c_pow2[192] = {  // 2^s mod p, s = 0 .. 191
-    0x0000000000000001ull, 0x0000000000000002ull, 0x0000000000000004ull, 0x0000000000000008ull,
-    0x0000000000000010ull, 0x0000000000000020ull, 0x0000000000000040ull, 0x0000000000000080ull,
-    0x0000000000000100ull, 0x0000000000000200ull, 0x0000000000000400ull, 0x0000000000000800ull,
-    0x0000000000001000ull, 0x0000000000002000ull, 0x0000000000004000ull, 0x0000000000008000ull,
-    0x0000000000010000ull, 0x0000000000020000ull, 0x0000000000040000ull, 0x0000000000080000ull,
-    0x0000000000100000ull, 0x0000000000200000ull, 0x0000000000400000ull, 0x0000000000800000ull,
-    0x0000000001000000ull, 0x0000000002000000ull, 0x0000000004000000ull, 0x0000000008000000ull,
-    0x0000000010000000ull, 0x0000000020000000ull, 0x0000000040000000ull, 0x0000000080000000ull,
-    0x0000000100000000ull, 0x0000000200000000ull, 0x0000000400000000ull, 0x0000000800000000ull,
-    0x0000001000000000ull, 0x0000002000000000ull, 0x0000004000000000ull, 0x0000008000000000ull,
-    0x0000010000000000ull, 0x0000020000000000ull, 0x0000040000000000ull, 0x0000080000000000ull,
-    0x0000100000000000ull, 0x0000200000000000ull, 0x0000400000000000ull, 0x0000800000000000ull,
-    0x0001000000000000ull, 0x0002000000000000ull, 0x0004000000000000ull, 0x0008000000000000ull,
-    0x0010000000000000ull, 0x0020000000000000ull, 0x0040000000000000ull, 0x0080000000000000ull,
-    0x0100000000000000ull, 0x0200000000000000ull, 0x0400000000000000ull, 0x0800000000000000ull,
-    0x1000000000000000ull, 0x2000000000000000ull, 0x4000000000000000ull, 0x8000000000000000ull,
-    0x00000000ffffffffull, 0x00000001fffffffeull, 0x00000003fffffffcull, 0x00000007fffffff8ull,
-    0x0000000ffffffff0ull, 0x0000001fffffffe0ull, 0x0000003fffffffc0ull, 0x0000007fffffff80ull,
-    0x000000ffffffff00ull, 0x000001fffffffe00ull, 0x000003fffffffc00ull, 0x000007fffffff800ull,
-    0x00000ffffffff000ull, 0x00001fffffffe000ull, 0x00003fffffffc000ull, 0x00007fffffff8000ull,
-    0x0000ffffffff0000ull, 0x0001fffffffe0000ull, 0x0003fffffffc0000ull, 0x0007fffffff80000ull,
-    0x000ffffffff00000ull, 0x001fffffffe00000ull, 0x003fffffffc00000ull, 0x007fffffff800000ull,
-    0x00ffffffff000000ull, 0x01fffffffe000000ull, 0x03fffffffc000000ull, 0x07fffffff8000000ull,
-    0x0ffffffff0000000ull, 0x1fffffffe0000000ull, 0x3fffffffc0000000ull, 0x7fffffff80000000ull,
-    0xffffffff00000000ull, 0xfffffffeffffffffull, 0xfffffffefffffffdull, 0xfffffffefffffff9ull,
-    0xfffffffefffffff1ull, 0xfffffffeffffffe1ull, 0xfffffffeffffffc1ull, 0xfffffffeffffff81ull,
-    0xfffffffeffffff01ull, 0xfffffffefffffe01ull, 0xfffffffefffffc01ull, 0xfffffffefffff801ull,
-    0xfffffffefffff001ull, 0xfffffffeffffe001ull, 0xfffffffeffffc001ull, 0xfffffffeffff8001ull,
-    0xfffffffeffff0001ull, 0xfffffffefffe0001ull, 0xfffffffefffc0001ull, 0xfffffffefff80001ull,
-    0xfffffffefff00001ull, 0xfffffffeffe00001ull, 0xfffffffeffc00001ull, 0xfffffffeff800001ull,
-    0xfffffffeff000001ull, 0xfffffffefe000001ull, 0xfffffffefc000001ull, 0xfffffffef8000001ull,
-    0xfffffffef0000001ull, 0xfffffffee0000001ull, 0xfffffffec0000001ull, 0xfffffffe80000001ull,
-    0xfffffffe00000001ull, 0xfffffffd00000001ull, 0xfffffffb00000001ull, 0xfffffff700000001ull,
-    0xffffffef00000001ull, 0xffffffdf00000001ull, 0xffffffbf00000001ull, 0xffffff7f00000001ull,
-    0xfffffeff00000001ull, 0xfffffdff00000001ull, 0xfffffbff00000001ull, 0xfffff7ff00000001ull,
-    0xffffefff00000001ull, 0xffffdfff00000001ull, 0xffffbfff00000001ull, 0xffff7fff00000001ull,
-    0xfffeffff00000001ull, 0xfffdffff00000001ull, 0xfffbffff00000001ull, 0xfff7ffff00000001ull,
-    0xffefffff00000001ull, 0xffdfffff00000001ull, 0xffbfffff00000001ull, 0xff7fffff00000001ull,
-    0xfeffffff00000001ull, 0xfdffffff00000001ull, 0xfbffffff00000001ull, 0xf7ffffff00000001ull,
-    0xefffffff00000001ull, 0xdfffffff00000001ull, 0xbfffffff00000001ull, 0x7fffffff00000001ull,
-    0xfffffffe00000002ull, 0xfffffffd00000003ull, 0xfffffffb00000005ull, 0xfffffff700000009ull,
-    0xffffffef00000011ull, 0xffffffdf00000021ull, 0xffffffbf00000041ull, 0xffffff7f00000081ull,
-    0xfffffeff00000101ull, 0xfffffdff00000201ull, 0xfffffbff00000401ull, 0xfffff7ff00000801ull,
-    0xffffefff00001001ull, 0xffffdfff00002001ull, 0xffffbfff00004001ull, 0xffff7fff00008001ull,
-    0xfffeffff00010001ull, 0xfffdffff00020001ull, 0xfffbffff00040001ull, 0xfff7ffff00080001ull,
-    0xffefffff00100001ull, 0xffdfffff00200001ull, 0xffbfffff00400001ull, 0xff7fffff00800001ull,
-    0xfeffffff01000001ull, 0xfdffffff02000001ull, 0xfbffffff04000001ull, 0xf7ffffff08000001ull,
-    0xefffffff10000001ull, 0xdfffffff20000001ull, 0xbfffffff40000001ull, 0x7fffffff80000001ull,
-};
-#endif
-
 GL_HD constexpr u64 pow2_mod(int s) {
     // 2^s for s < 64, folded with 2^64 = EPS, 2^96 = -1 (constexpr, host and device)
     u64 r = 1;
@@ -225,24 +171,64 @@ GL_HD u64 shl_small(u64 x, int s) {
 #endif
 }
 
-// x * 2^s mod p for a run-time s in [0, 192), cheapest route by range
-// (measured instruction counts): s < 32 folds one top word; s < 64 reduces
-// the 128-bit shifted value; s < 96 multiplies by the constant 2^s mod p;
-// s >= 96 uses 2^96 = -1 (negated smaller shift, or the constant for
-// s >= 160). Inside fully unrolled loops s is a constant and the branches fold
-// away; where s varies it is uniform across a warp in every caller.
+// t * EPS = t * 2^64 mod p for t < 2^32: one 32 x 32 -> 64 product (FMA pipe),
+// at most (2^32 - 1)^2 < p.
+GL_HD u64 mul_eps(u32 t) {
+#if defined(__CUDA_ARCH__)
+    u64 r;
+    asm("mul.wide.u32 %0, %1, 4294967295;" : "=l"(r) : "r"(t));
+    return r;
+#else
+    return (u64)t * EPS;
+#endif
+}
+
+// x * 2^s mod p for s in [32, 64). With k = 96 - s in (32, 64], x = q 2^k + r:
+// x 2^s = q 2^96 + r 2^s = -q + u 2^32, u = r 2^(s-32) = x << (s - 32) (mod 2^64,
+// the bits of q shift out). With u = uh 2^32 + ul, u 2^32 = uh 2^64 + ul 2^32
+// = uh EPS + ul 2^32 = (uh + ul) 2^32 - uh, and a carry out of uh + ul is one
+// more 2^64 = EPS. That value is below p and q < 2^31, so one field sub ends it.
+GL_HD u64 shl_mid(u64 x, int s) {
+    u64 u = x << (s - 32);
+    u32 uh = (u32)(u >> 32), ul = (u32)u;
+    u64 q = s == 32 ? 0 : x >> (96 - s);
+#if defined(__CUDA_ARCH__)
+    u32 w, c;
+    asm("add.cc.u32 %0, %2, %3;\n\t"
+        "addc.u32 %1, 0, 0;"
+        : "=r"(w), "=r"(c)
+        : "r"(uh), "r"(ul));
+    u64 v = ((u64)w << 32) - uh;
+    asm("mad.wide.u32 %0, %1, 4294967295, %0;" : "+l"(v) : "r"(c));
+#else
+    u64 wide = (u64)uh + ul;
+    u64 v = ((wide & 0xFFFFFFFFull) << 32) - uh + ((wide >> 32) ? EPS : 0);
+#endif
+    return sub(v, q);
+}
+
+// x * 2^s mod p for s in [64, 96). With k = 96 - s in (0, 32], x = q 2^k + r:
+// x 2^s = q 2^96 + r 2^s = -q + t 2^64 = t EPS - q, t = r 2^(s-64) < 2^32
+// (the low 32 bits of x shifted by s - 64; bits above k shift out).
+GL_HD u64 shl_hi(u64 x, int s) { return sub(mul_eps((u32)x << (s - 64)), x >> (96 - s)); }
+
+// x * 2^s mod p for s in [160, 192): 2^s = -2^(s-96), the negation of shl_hi.
+GL_HD u64 shl_top(u64 x, int s) { return sub(x >> (192 - s), mul_eps((u32)x << (s - 160))); }
+
+// x * 2^s mod p for a run-time s in [0, 192), by range: s < 32 folds one top
+// word; s < 64 and s < 96 split x at bit 96 - s (2^96 = -1); s >= 96 negates a
+// smaller shift, and s >= 160 splits like s < 96. Inside fully unrolled loops s
+// is a constant and the branches fold away; where s varies it is uniform across
+// a warp in every caller.
 GL_HD u64 shl_v(u64 x, int s) {
     if (s == 0) return x;
     if (s < 32) return shl_small(x, s);
-    if (s < 64) return reduce128(x << s, x >> (64 - s));
+    if (s < 64) return shl_mid(x, s);
+    if (s < 96) return shl_hi(x, s);
     if (s == 96) return neg(x);
-    if (s > 96 && s < 128) return neg(shl_small(x, s - 96));
-    if (s >= 128 && s < 160) return neg(reduce128(x << (s - 96), x >> (160 - s)));
-#if defined(__CUDA_ARCH__)
-    return mul(x, c_pow2[s]);
-#else
-    return mul(x, pow2_mod(s));
-#endif
+    if (s < 128) return neg(shl_small(x, s - 96));
+    if (s < 160) return neg(shl_mid(x, s - 96));
+    return shl_top(x, s);
 }
 
 // Shift for w^e where w = 2^(192/R) is the R-th root of unity used by every
@@ -253,10 +239,28 @@ GL_HD int root_shift(int e) {
     return INV ? (192 - s) % 192 : s;
 }
 
+template <int R>
+GL_HD void dft_fwd(u64* v);
+
 // In-register DFT of length R in {1, 2, 3, 4, 6, 8}, natural order in and out:
 // v[k] <- sum_j v[j] w^(jk), w = 2^(192/R) (or its inverse), no 1/R scaling.
+// The inverse is the forward DFT read backwards (sum_j v[j] w^(-jk) is the
+// forward output R - k), which keeps every root a cheap forward shift.
 template <int R, bool INV>
 GL_HD void dft(u64* v) {
+    dft_fwd<R>(v);
+    if constexpr (INV) {
+#pragma unroll
+        for (int k = 1; k < R - k; k++) {
+            u64 t = v[k];
+            v[k] = v[R - k];
+            v[R - k] = t;
+        }
+    }
+}
+
+template <int R>
+GL_HD void dft_fwd(u64* v) {
     if constexpr (R == 1) {
         (void)v;
     } else if constexpr (R == 2) {
@@ -267,7 +271,7 @@ GL_HD void dft(u64* v) {
         // w = 2^48 (forward); w^2 = -1
         u64 a = add(v[0], v[2]), b = sub(v[0], v[2]);
         u64 c = add(v[1], v[3]);
-        u64 d = shl_v(sub(v[1], v[3]), root_shift<4, INV>(1));
+        u64 d = shl_v(sub(v[1], v[3]), root_shift<4, false>(1));
         v[0] = add(a, c);
         v[2] = sub(a, c);
         v[1] = add(b, d);
@@ -276,7 +280,7 @@ GL_HD void dft(u64* v) {
         // w = 2^64 (forward), w^2 = -1 - w:
         // X0 = a + b + c, X1 = (a - c) + w (b - c), X2 = (a - b) - w (b - c)
         u64 a = v[0], b = v[1], c = v[2];
-        u64 t = shl_v(sub(b, c), root_shift<3, INV>(1));
+        u64 t = shl_v(sub(b, c), root_shift<3, false>(1));
         v[0] = add(add(a, b), c);
         v[1] = add(sub(a, c), t);
         v[2] = sub(sub(a, b), t);
@@ -286,10 +290,10 @@ GL_HD void dft(u64* v) {
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             s[i] = add(v[i], v[i + 3]);
-            t[i] = shl_v(sub(v[i], v[i + 3]), root_shift<6, INV>(i));
+            t[i] = shl_v(sub(v[i], v[i + 3]), root_shift<6, false>(i));
         }
-        dft<3, INV>(s);
-        dft<3, INV>(t);
+        dft_fwd<3>(s);
+        dft_fwd<3>(t);
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             v[2 * k] = s[k];
@@ -302,10 +306,10 @@ GL_HD void dft(u64* v) {
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             s[i] = add(v[i], v[i + 4]);
-            t[i] = shl_v(sub(v[i], v[i + 4]), root_shift<8, INV>(i));
+            t[i] = shl_v(sub(v[i], v[i + 4]), root_shift<8, false>(i));
         }
-        dft<4, INV>(s);
-        dft<4, INV>(t);
+        dft_fwd<4>(s);
+        dft_fwd<4>(t);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             v[2 * k] = s[k];
