@@ -193,7 +193,7 @@ def alu_ops(name: str, N: int):
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
 # launch at n = 10^8), valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "ntt_contig_fused", "bytes": 261.2e6, "src_sha": "d27b4fe732a8ec0d",
+TRAFFIC = {"kernel": "ntt_contig_fused", "bytes": 261.4e6, "src_sha": "bf3a7aeb2a82c9e7",
            "profile": "profiles/k_contig_fused_n1e8.md"}
 
 
