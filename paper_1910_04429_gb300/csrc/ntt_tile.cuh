@@ -30,6 +30,8 @@ constexpr int NT = 512;  // threads per tile CTA
 // ---------------------------------------------------------------------------
 // twiddles
 // ---------------------------------------------------------------------------
+constexpr int MAX_PASSES = 8;  // strided passes of a plan
+
 struct Twiddles {
     const u64* w4096;   // w_4096^t, t < 4096
     const u64* w4096i;  // w_4096^-t
@@ -37,6 +39,11 @@ struct Twiddles {
     const u64* wloi;
     const u64* whi;     // w_N^(4096 t), t < N / 4096
     const u64* whii;
+    // Strided pass p of the plan (sub-problem size M = R S): its inter-pass
+    // twiddles w_M^(j k) at [k S + j] (j < S, k < R) and w_M^-(j k) likewise.
+    // Null: computed from wlo / whi at run time.
+    const u64* passf[MAX_PASSES];
+    const u64* passi[MAX_PASSES];
 };
 
 template <bool INV>
@@ -69,8 +76,10 @@ GL_HD u64 digit_at(const Digits& d, u64 pos) {
 // strided pass, radix R = RA * RB in {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}
 // ---------------------------------------------------------------------------
 struct StridedGeom {
-    u64 N, M, S;    // transform length, sub-problem size, stride (= M / R)
-    int log_tpb;    // log2 of the tiles per sub-problem, (S / C)
+    u64 N, M, S;     // transform length, sub-problem size, stride (= M / R)
+    u32 tpb;         // tiles per sub-problem, S / C
+    const u64* twf;  // this pass's twiddle tables (Twiddles::passf / passi), or null
+    const u64* twi;
 };
 
 // Where tile t of a strided pass sits: sub-problem b, first column jl0.
@@ -91,8 +100,8 @@ struct Strided {
     static_assert(R * C <= TILE, "tile larger than shared memory");
 
     static GL_HD TilePos tile(const StridedGeom& g, u64 t) {
-        u64 b = t >> g.log_tpb, cg = t & ((1ull << g.log_tpb) - 1);
-        return TilePos{b * g.M + cg * C, cg * C};
+        u32 b = (u32)t / g.tpb, cg = (u32)t - b * g.tpb;  // the grid has fewer than 2^31 tiles
+        return TilePos{b * g.M + (u64)cg * C, (u64)cg * C};
     }
 
     // forward, step 1: length-RB DFT over j1 of digits j0 + RA*j1, twiddle w_R^(j0 kr)
@@ -136,13 +145,21 @@ struct Strided {
             sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
     }
 
+    // inter-pass twiddle w_M^(+-jl k) of column jl, digit k: the pass's table, or
+    // w_N^(e k) with e = (N / M) jl from the transform's tables
+    template <bool INV>
+    static GL_HD u64 pass_twiddle(const StridedGeom& g, const Twiddles& tw, u64 jl, u64 k) {
+        const u64* t = INV ? g.twi : g.twf;
+        if (t) return t[k * g.S + jl];
+        return omega_n<INV>(tw, (g.N / g.M) * jl * k);
+    }
+
     // inverse inter-pass twiddles w_M^-(jl k) of one phase-B item, k = RB ks + kr
     static GL_HD void inv_twiddles(const StridedGeom& g, const TilePos& tp, int it, const Twiddles& tw,
                                    u64* w) {
         int kr = it / C, c = it % C;
-        u64 e = (g.N / g.M) * (tp.jl0 + c);
 #pragma unroll
-        for (int ks = 0; ks < RA; ks++) w[ks] = omega_n<true>(tw, e * (u64)(RB * ks + kr));
+        for (int ks = 0; ks < RA; ks++) w[ks] = pass_twiddle<true>(g, tw, tp.jl0 + c, (u64)(RB * ks + kr));
     }
 
     // inv_b reading the tile from a [R][C] staging copy, with its twiddles given
@@ -161,9 +178,8 @@ struct Strided {
     static GL_HD void twiddles(const StridedGeom& g, const TilePos& tp, int it, const Twiddles& tw,
                                u64* w) {
         int kr = it / C, c = it % C;
-        u64 e = (g.N / g.M) * (tp.jl0 + c);
 #pragma unroll
-        for (int ks = 0; ks < RA; ks++) w[ks] = omega_n<false>(tw, e * (u64)(RB * ks + kr));
+        for (int ks = 0; ks < RA; ks++) w[ks] = pass_twiddle<false>(g, tw, tp.jl0 + c, (u64)(RB * ks + kr));
     }
 
     // forward, step 2: length-RA DFT over j0, times the twiddles, store digit k = RB ks + kr
@@ -184,11 +200,10 @@ struct Strided {
                             const Twiddles& tw) {
         int kr = it / C, c = it % C;
         u64 w[RA];
-        u64 e = (g.N / g.M) * (tp.jl0 + c);
 #pragma unroll
         for (int ks = 0; ks < RA; ks++) {
             u64 k = RB * ks + kr;
-            w[ks] = gl::mul(buf[tp.base + c + g.S * k], omega_n<true>(tw, e * k));
+            w[ks] = gl::mul(buf[tp.base + c + g.S * k], pass_twiddle<true>(g, tw, tp.jl0 + c, k));
         }
         gl::dft<RA, true>(w);
 #pragma unroll

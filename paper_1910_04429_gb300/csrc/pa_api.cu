@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -37,6 +38,8 @@ struct Device {
     std::unordered_map<u64, int> forced;  // N -> plan variant forced by pa_plan_override
     cudaMemPool_t pool = nullptr;
     std::unordered_map<u64, u64*> tables;  // transform length N -> device twiddle tables
+    std::map<std::pair<u64, u64>, u64*> pass_tables;  // (M, S) -> a strided pass's twiddles
+    cudaStream_t table_stream = nullptr;   // private stream of the table builds
     cudaStream_t side[SIDE_STREAMS] = {};  // forked from the caller's stream per batch
     cudaEvent_t fork = nullptr, join[SIDE_STREAMS] = {};
     // host-buffer calls: input copies run on `copy`, at most two calls ahead
@@ -92,12 +95,34 @@ int get_tables(int dev, const Geom& G, Twiddles* tw) {
         p = it->second;
     }
     u64 nh = G.N >> 12;
+    *tw = Twiddles{};
     tw->w4096 = p;
     tw->w4096i = p + 4096;
     tw->wlo = p + 8192;
     tw->wloi = p + 12288;
     tw->whi = p + 16384;
     tw->whii = p + 16384 + nh;
+    // per strided pass: full tables of its inter-pass twiddles (2 M words),
+    // built once on the device and waited for
+    for (int i = 0; i < G.nstrided && i < MAX_PASSES; i++) {
+        std::pair<u64, u64> key{G.pass[i].M, G.pass[i].S};
+        auto pt = d.pass_tables.find(key);
+        u64* q = nullptr;
+        if (pt == d.pass_tables.end()) {
+            cudaError_t e = cudaSuccess;
+            if (!d.table_stream) e = cudaStreamCreateWithFlags(&d.table_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaMalloc(&q, 2 * key.first * sizeof(u64));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(pass twiddles)");
+            e = launch_pass_twiddles(*tw, G.N, key.first, key.second, q, d.table_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(d.table_stream);
+            if (e != cudaSuccess) { cudaFree(q); return cuda_fail(e, "pass twiddles"); }
+            d.pass_tables[key] = q;
+        } else {
+            q = pt->second;
+        }
+        tw->passf[i] = q;
+        tw->passi[i] = q + key.first;
+    }
     return PA_OK;
 }
 
@@ -913,7 +938,7 @@ int pa_prepare(uint64_t n) {
     int rc = setup(&dev, &pool);
     if (rc) return rc;
     Twiddles tw;
-    return get_tables(dev, geom_for_bits(n), &tw);
+    return get_tables(dev, plan_for(dev, n), &tw);
 }
 
 uint64_t pa_workspace_bytes(uint64_t n) {
@@ -929,6 +954,14 @@ int pa_shutdown(void) {
     for (auto& kv : g_dev) {
         cudaSetDevice(kv.first);
         for (auto& t : kv.second.tables) cudaFree(t.second);
+        for (auto& t : kv.second.pass_tables) cudaFree(t.second);
+        if (kv.second.table_stream) cudaStreamDestroy(kv.second.table_stream);
+        if (kv.second.copy) {
+            cudaStreamDestroy(kv.second.copy);
+            cudaEventDestroy(kv.second.xa_ready);
+            cudaEventDestroy(kv.second.b_ready);
+            for (cudaEvent_t ev : kv.second.done) cudaEventDestroy(ev);
+        }
         if (kv.second.pool) cudaMemPoolDestroy(kv.second.pool);
         if (kv.second.fork) {
             cudaEventDestroy(kv.second.fork);

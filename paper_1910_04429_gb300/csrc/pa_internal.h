@@ -77,6 +77,10 @@ void fault_inject_carry();
 // Sticky device status bits (PA_STATUS_*); synchronous.
 cudaError_t read_device_status(u32* out, bool clear);
 
+// Inter-pass twiddle tables of a strided pass (M = sub-problem size, S =
+// stride): out[0 .. M) = w_M^(j k) at k S + j, out[M .. 2M) = w_M^-(j k).
+cudaError_t launch_pass_twiddles(const Twiddles& tw, u64 N, u64 M, u64 S, u64* out, cudaStream_t st);
+
 // Toeplitz hash, last step: out bit i = coef[first + i] mod 2 for i < m,
 // ceil(m/64) little-endian limbs (bits >= m zero).
 cudaError_t launch_parity_extract(const u64* coef, u64 first, u64 m, u64* out, cudaStream_t st);

@@ -308,11 +308,27 @@ struct Launcher {
     }
 };
 
-static StridedGeom strided_geom(const Geom& G, int p) {
+static StridedGeom strided_geom(const Geom& G, const Twiddles& tw, int p) {
     u64 C = (u64)strided_columns(G.pass[p].R);
-    int log_tpb = 0;
-    while ((C << log_tpb) < G.pass[p].S) log_tpb++;
-    return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, log_tpb};
+    return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, (u32)(G.pass[p].S / C), tw.passf[p], tw.passi[p]};
+}
+
+// Inter-pass twiddle tables of one strided pass (sub-problem size M, stride S):
+// fwd[k S + j] = w_M^(j k), inv[k S + j] = w_M^-(j k), from the transform's
+// w_N tables (w_M = w_N^(N/M)).
+__global__ void k_pass_twiddles(Twiddles tw, u64 N, u64 M, u64 S, u64* fwd, u64* inv) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (u64)gridDim.x * blockDim.x) {
+        u64 k = i / S, j = i - k * S;
+        u64 e = (N / M) * j * k;  // < N
+        fwd[i] = omega_n<false>(tw, e);
+        inv[i] = omega_n<true>(tw, e);
+    }
+}
+
+cudaError_t launch_pass_twiddles(const Twiddles& tw, u64 N, u64 M, u64 S, u64* out, cudaStream_t st) {
+    u64 blocks = (M + 255) / 256;
+    k_pass_twiddles<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(tw, N, M, S, out, out + M);
+    return cudaGetLastError();
 }
 
 // ops = 2: transform x and a and build a's spectrum; ops = 1: x only, each
@@ -326,7 +342,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
                   !nb.io[i].dx.sysmem && !nb.io[i].da.sysmem && !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
     for (int p = 0; p < G.nstrided; p++) {
-        StridedGeom g = strided_geom(G, p);
+        StridedGeom g = strided_geom(G, tw, p);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
         Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv}.dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
@@ -349,7 +365,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
         k_contig_fused<false, B><<<tiles, NT, 0, st>>>(nb, tw);
     prof_end(st);
     for (int p = G.nstrided - 1; p >= 0; p--) {
-        StridedGeom g = strided_geom(G, p);
+        StridedGeom g = strided_geom(G, tw, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
         Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv}.dispatch_inv(G.pass[p].R, p == 0);
         prof_end(st);
@@ -374,7 +390,7 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.sysmem && !j.da.one_bit;
     const Geom& G = j.geom;
     for (int p = 0; p < G.nstrided; p++) {
-        StridedGeom g = strided_geom(G, p);
+        StridedGeom g = strided_geom(G, j.tw, p);
         prof_begin(st, "ntt_seed_strided");
         Launcher<1>{&g, &nb, &j.tw, st, aligned, 1, !(G.variant & PLAN_DIRECT_FWD), true}
             .dispatch_fwd(G.pass[p].R, p == 0);

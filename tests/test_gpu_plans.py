@@ -12,8 +12,9 @@ from tests.gpu_util import dev, gpu_hash, host
 pytestmark = pytest.mark.gpu
 
 # transform lengths 2^12 (no strided pass), 2^14 ([4]), 3*2^16 ([48]),
-# 2^19 ([2, 64]) and 3*2^18 ([3, 64])
-SIZES = [1000, 100_003, 1_536_000, 3_000_001, 4_800_000]
+# 2^19 ([2, 64]), 3*2^18 ([3, 64]) and 3*2^24 ([3, 64, 64]; with the odd radix
+# last, [64, 64, 3], the middle pass has 64 sub-problems of 192 tiles each)
+SIZES = [1000, 100_003, 1_536_000, 3_000_001, 4_800_000, 300_000_017]
 
 
 @pytest.mark.parametrize("n", SIZES)
