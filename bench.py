@@ -181,9 +181,11 @@ BUTTERFLY = COST["add"] + COST["sub"] + COST["mul"]
 def alu_ops(name: str, N: int):
     """Butterfly-model ALU operations of one launch of the contiguous-tile
     kernels: the 4096-point tile transform is 12 radix-2 stages; seed = one
-    forward tile transform + N^-1 scaling, fused = forward + pointwise product
-    + inverse."""
+    forward tile transform + N^-1 scaling; fused = forward + pointwise product
+    + inverse; both = seed + fused in one kernel (a's spectrum kept on chip)."""
     stage = N // 2 * BUTTERFLY
+    if name == "ntt_contig_both":
+        return 3 * 12 * stage + 2 * N * COST["mul"]
     if name == "ntt_contig_fused":
         return 2 * 12 * stage + N * COST["mul"]
     if name == "ntt_contig_seed":
@@ -223,6 +225,7 @@ def kernel_bytes(name: str, n: int, m: int, N: int) -> float:
         "ntt_fwd_strided_r64": 2 * (2 * N * w),               # both operands, read + write
         "ntt_contig_seed": 2 * N * w,
         "ntt_contig_fused": 3 * N * w,                        # x tile, a spectrum in; product out
+        "ntt_contig_both": 3 * N * w,                         # x and a tiles in; product out
         "ntt_inv_strided_r64": 2 * N * w,
         "ntt_inv_strided_last": N * w + L * w,                # only digits k < L written
         "carry_lookback": L * w + Ly * w + Mo * w,

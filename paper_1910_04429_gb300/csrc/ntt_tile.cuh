@@ -44,6 +44,7 @@ struct Twiddles {
     // Null: computed from wlo / whi at run time.
     const u64* passf[MAX_PASSES];
     const u64* passi[MAX_PASSES];
+    const u64* w4096s;  // w_4096^t * N^-1 (a forward tile pass that also scales), or null
 };
 
 template <bool INV>
@@ -257,13 +258,14 @@ GL_HD void c_fwd_col_a(int t, const u64* src, const Digits& dig, u64 base, u64* 
 }
 
 // F3: kr = u: length-8 DFT over j0, twiddle w_4096^(c k) with k = 8 ks + kr (regs only)
-GL_HD void c_fwd_col_b_load(int t, const u64* sm, const Twiddles& tw, u64* v) {
+// (w4096: the w_4096 powers, or those powers times N^-1 to scale the result)
+GL_HD void c_fwd_col_b_load(int t, const u64* sm, const u64* w4096, u64* v) {
     Lane ln = lane_of(t);
 #pragma unroll
     for (int j0 = 0; j0 < 8; j0++) v[j0] = sm[sidx(ln.u * 8 + j0, ln.idx)];
     gl::dft<8, false>(v);
 #pragma unroll
-    for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(v[ks], tw.w4096[ln.idx * (8 * ks + ln.u)]);
+    for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(v[ks], w4096[ln.idx * (8 * ks + ln.u)]);
 }
 // F4: row k of the tile receives column c's output k
 GL_HD void c_fwd_col_b_store(int t, u64* sm, const u64* v) {

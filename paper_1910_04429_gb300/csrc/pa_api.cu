@@ -83,9 +83,14 @@ int get_tables(int dev, const Geom& G, Twiddles* tw) {
     Device& d = g_dev[dev];
     auto it = d.tables.find(G.N);
     u64* p = nullptr;
+    size_t base_words = table_words_n(G.N);
     if (it == d.tables.end()) {
         std::vector<u64> host;
         make_tables(G.logN, host, G.three);
+        // then w_4096^t * N^-1: the seed's tile pass scales by N^-1 through its twiddles
+        u64 ninv = n_inverse(G.logN, G.three);
+        host.resize(base_words + 4096);
+        for (size_t i = 0; i < 4096; i++) host[base_words + i] = gl::mul(host[i], ninv);
         cudaError_t e = cudaMalloc(&p, host.size() * sizeof(u64));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(twiddles)");
         e = cudaMemcpy(p, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
@@ -102,6 +107,7 @@ int get_tables(int dev, const Geom& G, Twiddles* tw) {
     tw->wloi = p + 12288;
     tw->whi = p + 16384;
     tw->whii = p + 16384 + nh;
+    tw->w4096s = p + base_words;
     // per strided pass: full tables of its inter-pass twiddles (2 M words),
     // built once on the device and waited for
     for (int i = 0; i < G.nstrided && i < MAX_PASSES; i++) {

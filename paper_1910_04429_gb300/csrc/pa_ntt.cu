@@ -150,13 +150,14 @@ __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __gr
 }
 
 // Forward contiguous pass of one tile; leaves the spectrum in registers.
+// w4096: the middle twiddles (times N^-1 when the result is to be scaled).
 template <bool PACK>
 __device__ __forceinline__ void contig_forward(const u64* src, const Digits& d, u64 base,
-                                               const Twiddles& tw, u64* sm, u64* v) {
+                                               const u64* w4096, u64* sm, u64* v) {
     int t = threadIdx.x;
     c_fwd_col_a<PACK>(t, src, d, base, sm);
     __syncthreads();
-    c_fwd_col_b_load(t, sm, tw, v);
+    c_fwd_col_b_load(t, sm, w4096, v);
     __syncthreads();
     c_fwd_col_b_store(t, sm, v);
     __syncthreads();
@@ -177,11 +178,18 @@ __global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttB
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
     u64 v[8];
-    contig_forward<PACK>(io.buf_a + base, io.da, base, tw, sm, v);
+    // with the scaled middle twiddles every word is multiplied by N^-1 once there
+    const bool scaled = tw.w4096s != nullptr;
+    contig_forward<PACK>(io.buf_a + base, io.da, base, scaled ? tw.w4096s : tw.w4096, sm, v);
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(io.buf_a + base + 8 * threadIdx.x);
+    if (scaled) {
 #pragma unroll
-    for (int k = 0; k < 4; k++)
-        dst[k] = make_ulonglong2(gl::mul(v[2 * k], ninv), gl::mul(v[2 * k + 1], ninv));
+        for (int k = 0; k < 4; k++) dst[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            dst[k] = make_ulonglong2(gl::mul(v[2 * k], ninv), gl::mul(v[2 * k + 1], ninv));
+    }
 }
 
 // Forward contiguous pass of x, pointwise product with a's spectrum (Algorithm 1
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ Ntt
     u64 base = (u64)blockIdx.x * TILE;
     int t = threadIdx.x;
     u64 v[8];
-    contig_forward<PACK>(io.buf_x + base, io.dx, base, tw, sm, v);
+    contig_forward<PACK>(io.buf_x + base, io.dx, base, tw.w4096, sm, v);
     const ulonglong2* src = reinterpret_cast<const ulonglong2*>(io.buf_a + base + 8 * t);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -203,6 +211,43 @@ __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ Ntt
         v[2 * k] = gl::mul(v[2 * k], w.x);
         v[2 * k + 1] = gl::mul(v[2 * k + 1], w.y);
     }
+    __syncthreads();
+    c_inv_row_b_store(t, sm, v);
+    __syncthreads();
+    c_inv_row_a_load(t, sm, v);
+    __syncthreads();
+    c_inv_row_a_store(t, sm, v);
+    __syncthreads();
+    c_inv_col_b_load(t, sm, tw, v);
+    __syncthreads();
+    c_inv_col_b_store(t, sm, v);
+    __syncthreads();
+    c_inv_col_a(t, sm, io.buf_x + base, base, PACK ? io.L : ~0ull);
+}
+
+// Both operands of one tile in one CTA: a's forward contiguous pass (times N^-1)
+// parked in shared memory, then x's forward pass, the pointwise product and the
+// inverse contiguous pass, as k_contig_seed followed by k_contig_fused but
+// without a's spectrum going through global memory. Dynamic shared memory: the
+// working tile, then a's spectrum word-interleaved by thread ([k * NT + t]).
+template <bool PACK, int B>
+__global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ NttBatch<B> nb, u64 ninv,
+                                                    Twiddles tw) {
+    extern __shared__ __align__(16) u64 dsm[];
+    u64* sm = dsm;
+    u64* ah = dsm + TILE;
+    const BlockIO& io = nb.io[blockIdx.y];
+    u64 base = (u64)blockIdx.x * TILE;
+    int t = threadIdx.x;
+    u64 v[8];
+    const bool scaled = tw.w4096s != nullptr;
+    contig_forward<PACK>(io.buf_a + base, io.da, base, scaled ? tw.w4096s : tw.w4096, sm, v);
+#pragma unroll
+    for (int k = 0; k < 8; k++) ah[k * NT + t] = scaled ? v[k] : gl::mul(v[k], ninv);
+    __syncthreads();  // every thread is done reading sm
+    contig_forward<PACK>(io.buf_x + base, io.dx, base, tw.w4096, sm, v);
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = gl::mul(v[k], ah[k * NT + t]);
     __syncthreads();
     c_inv_row_b_store(t, sm, v);
     __syncthreads();
@@ -351,19 +396,25 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
     u64 ninv = n_inverse(G.logN, G.three);
     if (ops == 2) {
-        prof_begin(st, "ntt_contig_seed");
+        // both operands' tile passes in one kernel (a's spectrum stays on chip)
+        constexpr size_t smem = 2 * TILE * sizeof(u64);
+        prof_begin(st, "ntt_contig_both");
+        if (pack) {
+            allow_smem(k_contig_both<true, B>, smem);
+            k_contig_both<true, B><<<tiles, NT, smem, st>>>(nb, ninv, tw);
+        } else {
+            allow_smem(k_contig_both<false, B>, smem);
+            k_contig_both<false, B><<<tiles, NT, smem, st>>>(nb, ninv, tw);
+        }
+        prof_end(st);
+    } else {
+        prof_begin(st, "ntt_contig_fused");
         if (pack)
-            k_contig_seed<true, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
+            k_contig_fused<true, B><<<tiles, NT, 0, st>>>(nb, tw);
         else
-            k_contig_seed<false, B><<<tiles, NT, 0, st>>>(nb, ninv, tw);
+            k_contig_fused<false, B><<<tiles, NT, 0, st>>>(nb, tw);
         prof_end(st);
     }
-    prof_begin(st, "ntt_contig_fused");
-    if (pack)
-        k_contig_fused<true, B><<<tiles, NT, 0, st>>>(nb, tw);
-    else
-        k_contig_fused<false, B><<<tiles, NT, 0, st>>>(nb, tw);
-    prof_end(st);
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, tw, p);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
