@@ -17,10 +17,12 @@
 // and addend limbs in shared memory with coalesced loads, scans its (g, p)
 // pairs, publishes the tile aggregate, walks back over the published states of
 // earlier tiles to obtain its carry-in, publishes its inclusive prefix, and
-// writes its output bits. Warp 0 reads 32 predecessor states per round and
-// stops at the latest one that fixes its carry out (an inclusive prefix, or an
-// aggregate with P = 0, which random data gives almost always): a tile rarely
-// waits for more than its neighbour's aggregate. Every wait on another tile is bounded: when the
+// writes its output bits. The carry into a tile is decided by the last limbs
+// before it unless they propagate (u = 2^64 - 1): the tile stages a four-limb
+// halo and resolves it from the two limbs before it, with no wait on any other
+// tile. Only when both propagate does warp 0 read 32 predecessor states per
+// round, stopping at the latest one that fixes its carry out (an inclusive
+// prefix, or an aggregate with P = 0). Every wait on another tile is bounded: when the
 // limit runs out the kernel records PA_STATUS_TIMEOUT in the device status word
 // and carries on with a carry-in of 0, so it always terminates.
 #include "cp_async.cuh"
@@ -42,10 +44,10 @@ constexpr int GP_IDENTITY = 2;
 // (2 << 2 | gp) = inclusive prefix from tile 0 through the tile
 constexpr u32 ST_AGG = 1u << 2, ST_INC = 2u << 2;
 
-constexpr int HALO_LO = 2, HALO_HI = 1;                       // extra limbs before / after a tile
+constexpr int HALO_LO = 4, HALO_HI = 1;                       // extra limbs before / after a tile
 constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 1024
-constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 1027
-constexpr int SM_COEF = 4 * SM_LIMBS;                         // 4108
+constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 1029
+constexpr int SM_COEF = 4 * SM_LIMBS;                         // 4116
 constexpr int SM_LIMBS_PAD = SM_LIMBS + 1;                    // whole 16-byte chunks
 
 struct Limb {
@@ -117,14 +119,14 @@ __device__ __forceinline__ int block_exclusive(int v, int* total) {
     return compose(wpre, exc);
 }
 
+// tile states: release store / acquire load at GPU scope
 __device__ __forceinline__ void publish(u32* p, u32 v) {
-    __threadfence();
-    atomicExch(p, v);
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ u32 observe(const u32* p) {
-    u32 v = *(const volatile u32*)p;
-    __threadfence();
+    u32 v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -140,6 +142,8 @@ __device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long 
 }
 
 // VEC: coef and b are 16-byte aligned (staged with cp.async), else plain loads.
+// ticket_start > 0 (fault injection) leaves the first tiles unprocessed and
+// makes every tile take the look-back path, so that the wait on them runs out.
 template <int B, bool VEC>
 __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
                                                          u32 ticket_start, u32 spin_limit) {
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     const u64 t = tile_sh;
     if (t >= tiles) return;
 
-    // stage digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS), J0 = 1024 t - 2
+    // stage digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS), J0 = 1024 t - 4
     const long long J0 = (long long)t * TILE_LIMBS - HALO_LO;
     if (VEC) {
         stage_pairs(cs, c.coef, 4 * J0, SM_COEF / 2, c.L);
@@ -186,13 +190,21 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     int pre = block_exclusive(acc, &total);
 
     if (threadIdx.x < 32) {
-        // warp 0: publish the aggregate, then look back 32 predecessors at a time
+        // warp 0: publish the aggregate; the carry into the tile from the two limbs
+        // before it when they decide it (the common case: no wait on any other
+        // tile), else look back over the published states 32 at a time
         const int lane = threadIdx.x;
-        int excl = GP_IDENTITY;  // prefix of tiles 0 .. t-1 applied in order
-        if (t == 0) {
-            if (lane == 0) publish(&state[0], ST_INC | (u32)total);
-        } else {
-            if (lane == 0) publish(&state[t], ST_AGG | (u32)total);
+        if (lane == 0) publish(&state[t], (t == 0 ? ST_INC : ST_AGG) | (u32)total);
+        int decided = 0, cin = 0;
+        if (lane == 0 && ticket_start == 0) {
+            Limb h[2];  // limbs 1024 t - 2 and 1024 t - 1 (zero below limb 0)
+            limbs_u<2>(cs, bs, HALO_LO - 2, h);
+            if (!(h[1].gp & 2)) decided = 1, cin = h[1].gp & 1;  // generate or kill
+            else if (!(h[0].gp & 2)) decided = 1, cin = h[0].gp & 1;
+        }
+        decided = __shfl_sync(0xffffffffu, decided, 0);
+        cin = __shfl_sync(0xffffffffu, cin, 0);
+        if (!decided) {
             long long base = (long long)t - 1;  // lane l looks at tile base - l
             int later = GP_IDENTITY;            // tiles after the current window, composed
             while (true) {
@@ -227,12 +239,13 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
                 if (inc) break;
                 base -= 32;
             }
-            excl = later;
-            if (lane == 0) publish(&state[t], ST_INC | (u32)compose(excl, total));
+            cin = later & 1;
         }
-        if (lane == 0) carry_in_sh = excl & 1;  // carry into the tile (the chain starts with 0)
+        if (lane == 0) carry_in_sh = cin;  // carry into the tile (the chain starts with 0)
     }
     __syncthreads();
+    // the inclusive prefix for tiles that look back past this one
+    if (threadIdx.x == 0 && t > 0) publish(&state[t], ST_INC | (u32)compose(carry_in_sh, total));
     int carry = (pre & 1) | ((pre >> 1) & carry_in_sh);
     u64 y[CARRY_LIMBS + 1];
 #pragma unroll

@@ -159,6 +159,35 @@ def test_carry_extract(pattern):
     assert to_int(host(out)) == _carry_ref(coef, to_int(b), n, m)
 
 
+@pytest.mark.parametrize("pattern", ["gen_prop", "gen_prop_prop", "kill_prop_prop"])
+def test_carry_decided_at_tile_boundaries(pattern):
+    """Carries into the carry tiles at limbs T = 1024 t: limb T-2 generates and
+    T-1 propagates (the tile's own halo decides), or T-3 generates / kills and
+    T-2, T-1 propagate (the tile must look back at its predecessor)."""
+    import torch
+
+    n = 64 * 1024 * 5 + 48
+    m = n - 5
+    L, Ly = (n + 15) // 16, (n + 63) // 64
+    coef = np.zeros(L, dtype=np.uint64)
+    b = np.zeros(Ly, dtype=np.uint64)
+    ones = np.uint64(0xFFFFFFFFFFFFFFFF)
+    for T in (1024, 2048, 4096):
+        if pattern == "gen_prop":
+            g = T - 2  # u_g = 2^64: f_(g-1) = 1 (hi(V_(g-2)) = 1, lo(V_(g-1)) = 2^64 - 1), e_g = 2^64 - 1
+            coef[4 * (g - 2) + 3] = 65536
+            b[g - 1] = b[g] = b[T - 1] = ones
+        elif pattern == "gen_prop_prop":
+            g = T - 3
+            coef[4 * (g - 2) + 3] = 65536
+            b[g - 1] = b[g] = b[T - 2] = b[T - 1] = ones
+        else:
+            b[T - 2] = b[T - 1] = ones
+    out = binding.carry_extract(dev(coef), dev(b), n, m)
+    torch.cuda.synchronize()
+    assert to_int(host(out)) == _carry_ref(coef, to_int(b), n, m)
+
+
 def test_hash_host_buffers():
     blk = inputs.make_block(3_000_000, 700_001, seed=11)
     got = binding.hash_host(blk.x, blk.a, blk.b, blk.n, blk.m)
