@@ -237,7 +237,9 @@ int pa_prepare(uint64_t n);
  * Autotuning. Every transform length has a few equivalent plans (PA_PLAN_*
  * bits: the odd first radix run last instead of first; forward or inverse
  * strided passes loading their tiles directly instead of staging them with
- * asynchronous copies). pa_autotune times the applicable plans for the
+ * asynchronous copies; for transforms of at most 64 tiles with one strided
+ * pass, single-block tiles of a quarter of the columns, four times the CTAs).
+ * Variants are 0 .. 15. pa_autotune times the applicable plans for the
  * transform length that keys of n bits use (reps hashes each, on synthetic
  * data, synchronous; it allocates with cudaMalloc) and keeps the fastest for
  * that length on the current device; later calls (single, batched, seeded,
@@ -249,6 +251,7 @@ int pa_prepare(uint64_t n);
 #define PA_PLAN_R0_LAST 1
 #define PA_PLAN_DIRECT_FWD 2
 #define PA_PLAN_DIRECT_INV 4
+#define PA_PLAN_NARROW 8
 int pa_autotune(uint64_t n, int reps, int* variant_out);
 int pa_plan_override(uint64_t n, int variant);
 

@@ -156,7 +156,8 @@ Geom geom_for_bits(uint64_t n) { return choose_geom((n + 15) / 16); }
 int applicable_variants(const Geom& g) {
     if (g.nstrided == 0) return 0;
     int R0 = (g.three ? 3 : 1) << ((g.logN - LOG_TILE) % 6);
-    return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV;
+    return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV |
+           (g.nstrided == 1 && g.N / TILE <= 64 ? PLAN_NARROW : 0);
 }
 
 // The plan for a transform length on device dev: base's length, with the
@@ -858,7 +859,7 @@ int pa_seed_destroy(pa_seed seed) {
 
 int pa_plan_override(uint64_t n, int variant) {
     if (n < 1 || n > PA_MAX_BITS || variant < -1 || variant >= PLAN_VARIANTS)
-        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 8");
+        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 16");
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
     cudaMemPool_t pool;

@@ -1,362 +1,9 @@
-// NTT multiply kernels: zero fill + split into 16-bit digits, forward
-// transforms, pointwise product and inverse transform (Algorithm 1, steps
-// 1-5, Sec. 3.2.2), as tile kernels over GF(p), p = 2^64 - 2^32 + 1.
-//
-// Every kernel serves a batch of independent blocks that share one transform
-// geometry: blockIdx.x is the tile, blockIdx.y the block, and the per-block
-// buffers and digit sources arrive in a __grid_constant__ parameter array.
-#include <mutex>
-#include <unordered_set>
-
-#include "cp_async.cuh"
-#include "pa_internal.h"
+// Single-block entry points of the NTT multiply (Algorithm 1, steps 1-5,
+// Sec. 3.2.2) and the per-pass twiddle tables; the kernels and the launch
+// sequence are in ntt_kernels.cuh.
+#include "ntt_kernels.cuh"
 
 namespace pa {
-
-// ---------------------------------------------------------------------------
-// asynchronous staging of tile inputs (cp.async, 16-byte chunks)
-// ---------------------------------------------------------------------------
-// Words of a tile (R rows at stride S, C columns) into stage[d * C + c]. Tile
-// bases and strides are even, so every 16-byte chunk is aligned.
-template <int R, int C>
-__device__ __forceinline__ void stage_words(u64* stage, const u64* buf, const StridedGeom& g,
-                                            const TilePos& tp) {
-    constexpr int CH = R * C / 2;
-    for (int ch = threadIdx.x; ch < CH; ch += NT) {
-        int d = ch / (C / 2), c = (ch % (C / 2)) * 2;
-        cp_async16(stage + d * C + c, buf + tp.base + c + g.S * (u64)d, 16);
-    }
-}
-
-// 16-bit digits of a tile into stage[d * C + c]; digits at positions >= L are
-// zero-filled by the copy (and never read from memory). The caller checks
-// that the digit source is 16-byte aligned.
-template <int R, int C>
-__device__ __forceinline__ void stage_digits(uint16_t* stage, const Digits& dig, const StridedGeom& g,
-                                             const TilePos& tp) {
-    constexpr int CH = R * C / 8;
-    for (int ch = threadIdx.x; ch < CH; ch += NT) {
-        int d = ch / (C / 8), c = (ch % (C / 8)) * 8;
-        u64 pos = tp.base + c + g.S * (u64)d;
-        u64 live = pos < dig.L ? dig.L - pos : 0;
-        int n = live >= 8 ? 8 : (int)live;
-        cp_async16(stage + d * C + c, n ? dig.src + pos : dig.src, 2 * n);
-    }
-}
-
-template <int R, int C, bool PACK>
-struct StageSize {
-    static constexpr int WORDS = PACK ? R * C / 4 : R * C;  // one staged tile, in 8-byte words
-    static constexpr size_t BYTES = (size_t)(TILE + 2 * WORDS) * sizeof(u64);
-};
-
-// Strided pass over one tile of both operands (OPS = 2: x and a; OPS = 1: x
-// only, when a's spectrum is reused): the twiddles computed for x are kept in
-// registers and reused for a. STAGED: the operands' tiles are copied into
-// shared memory asynchronously first, so a's loads overlap x's arithmetic.
-template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS>
-__global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
-                                                       Twiddles tw) {
-    using S = Strided<RA, RB, C>;
-    using SZ = StageSize<S::R, C, PACK>;
-    extern __shared__ __align__(16) u64 dsm[];
-    u64* sm = dsm;
-    u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
-    const BlockIO& io = nb.io[blockIdx.y];
-    TilePos tp = S::tile(g, blockIdx.x);
-    if (STAGED) {
-#pragma unroll
-        for (int op = 0; op < OPS; op++) {
-            if (PACK) stage_digits<S::R, C>((uint16_t*)st[op], op ? io.da : io.dx, g, tp);
-            else stage_words<S::R, C>(st[op], op ? io.buf_a : io.buf_x, g, tp);
-            cp_async_commit();
-        }
-    }
-    u64 w[S::ITEMS_B][RA];
-#pragma unroll
-    for (int i = 0; i < S::ITEMS_B; i++) {
-        int it = threadIdx.x + i * NT;
-        if (S::NB % NT == 0 || it < S::NB) S::twiddles(g, tp, it, tw, w[i]);
-    }
-#pragma unroll
-    for (int op = 0; op < OPS; op++) {
-        u64* buf = op ? io.buf_a : io.buf_x;
-        const Digits& d = op ? io.da : io.dx;
-        if (STAGED) {
-            if (op || OPS == 1) cp_async_wait<0>();
-            else cp_async_wait<1>();
-        }
-        __syncthreads();  // staged tile complete; the previous tile is out of sm
-#pragma unroll
-        for (int i = 0; i < S::ITEMS_A; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NA % NT == 0 || it < S::NA) {
-                if (STAGED)
-                    S::template fwd_a_staged<PACK>(g, tp, it, st[op], (const uint16_t*)st[op], d, sm);
-                else
-                    S::template fwd_a<PACK>(g, tp, it, buf, d, sm);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < S::ITEMS_B; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NB % NT == 0 || it < S::NB) S::fwd_b(g, tp, it, buf, sm, w[i]);
-        }
-    }
-}
-
-// Inverse strided pass over one tile. STAGED: the tile is copied into shared
-// memory asynchronously while the inverse twiddles are computed; otherwise the
-// first phase loads it directly (the autotuner picks per transform length).
-template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
-__global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
-                                                       Twiddles tw) {
-    using S = Strided<RA, RB, C>;
-    extern __shared__ __align__(16) u64 dsm[];
-    u64* sm = dsm;
-    u64* st = dsm + TILE;
-    const BlockIO& io = nb.io[blockIdx.y];
-    TilePos tp = S::tile(g, blockIdx.x);
-    if (STAGED) {
-        stage_words<S::R, C>(st, io.buf_x, g, tp);
-        cp_async_commit();
-        u64 w[S::ITEMS_B][RA];
-#pragma unroll
-        for (int i = 0; i < S::ITEMS_B; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NB % NT == 0 || it < S::NB) S::inv_twiddles(g, tp, it, tw, w[i]);
-        }
-        cp_async_wait<0>();
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < S::ITEMS_B; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NB % NT == 0 || it < S::NB) S::inv_b_staged(g, tp, it, st, sm, w[i]);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < S::ITEMS_B; i++) {
-            int it = threadIdx.x + i * NT;
-            if (S::NB % NT == 0 || it < S::NB) S::inv_b(g, tp, it, io.buf_x, sm, tw);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < S::ITEMS_A; i++) {
-        int it = threadIdx.x + i * NT;
-        if (S::NA % NT == 0 || it < S::NA) S::template inv_a<LAST>(g, tp, it, io.buf_x, sm, io.L);
-    }
-}
-
-// Forward contiguous pass of one tile; leaves the spectrum in registers.
-// w4096: the middle twiddles (times N^-1 when the result is to be scaled).
-template <bool PACK>
-__device__ __forceinline__ void contig_forward(const u64* src, const Digits& d, u64 base,
-                                               const u64* w4096, u64* sm, u64* v) {
-    int t = threadIdx.x;
-    c_fwd_col_a<PACK>(t, src, d, base, sm);
-    __syncthreads();
-    c_fwd_col_b_load(t, sm, w4096, v);
-    __syncthreads();
-    c_fwd_col_b_store(t, sm, v);
-    __syncthreads();
-    c_fwd_row_a_load(t, sm, v);
-    __syncthreads();
-    c_fwd_row_a_store(t, sm, v);
-    __syncthreads();
-    c_fwd_row_b_load(t, sm, v);
-}
-
-// Spectrum of a, scaled by N^-1 (the inverse transform's normalisation),
-// stored over buf_a in register order: thread t of tile T owns words
-// T*4096 + 8t .. +7. Each tile is read completely before it is overwritten.
-template <bool PACK, int B>
-__global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttBatch<B> nb, u64 ninv,
-                                                    Twiddles tw) {
-    __shared__ u64 sm[TILE];
-    const BlockIO& io = nb.io[blockIdx.y];
-    u64 base = (u64)blockIdx.x * TILE;
-    u64 v[8];
-    // with the scaled middle twiddles every word is multiplied by N^-1 once there
-    const bool scaled = tw.w4096s != nullptr;
-    contig_forward<PACK>(io.buf_a + base, io.da, base, scaled ? tw.w4096s : tw.w4096, sm, v);
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(io.buf_a + base + 8 * threadIdx.x);
-    if (scaled) {
-#pragma unroll
-        for (int k = 0; k < 4; k++) dst[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            dst[k] = make_ulonglong2(gl::mul(v[2 * k], ninv), gl::mul(v[2 * k + 1], ninv));
-    }
-}
-
-// Forward contiguous pass of x, pointwise product with a's spectrum (Algorithm 1
-// step 4) and the inverse contiguous pass, in one tile-resident kernel. With
-// PACK (a single-tile transform) this is also the last inverse pass, which keeps
-// only the digits below io.L.
-template <bool PACK, int B>
-__global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ NttBatch<B> nb, Twiddles tw) {
-    __shared__ u64 sm[TILE];
-    const BlockIO& io = nb.io[blockIdx.y];
-    u64 base = (u64)blockIdx.x * TILE;
-    int t = threadIdx.x;
-    u64 v[8];
-    contig_forward<PACK>(io.buf_x + base, io.dx, base, tw.w4096, sm, v);
-    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(io.buf_a + base + 8 * t);
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        ulonglong2 w = src[k];
-        v[2 * k] = gl::mul(v[2 * k], w.x);
-        v[2 * k + 1] = gl::mul(v[2 * k + 1], w.y);
-    }
-    __syncthreads();
-    c_inv_row_b_store(t, sm, v);
-    __syncthreads();
-    c_inv_row_a_load(t, sm, v);
-    __syncthreads();
-    c_inv_row_a_store(t, sm, v);
-    __syncthreads();
-    c_inv_col_b_load(t, sm, tw, v);
-    __syncthreads();
-    c_inv_col_b_store(t, sm, v);
-    __syncthreads();
-    c_inv_col_a(t, sm, io.buf_x + base, base, PACK ? io.L : ~0ull);
-}
-
-// Both operands of one tile in one CTA: a's forward contiguous pass (times N^-1)
-// parked in shared memory, then x's forward pass, the pointwise product and the
-// inverse contiguous pass, as k_contig_seed followed by k_contig_fused but
-// without a's spectrum going through global memory. Dynamic shared memory: the
-// working tile, then a's spectrum word-interleaved by thread ([k * NT + t]).
-template <bool PACK, int B>
-__global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ NttBatch<B> nb, u64 ninv,
-                                                    Twiddles tw) {
-    extern __shared__ __align__(16) u64 dsm[];
-    u64* sm = dsm;
-    u64* ah = dsm + TILE;
-    const BlockIO& io = nb.io[blockIdx.y];
-    u64 base = (u64)blockIdx.x * TILE;
-    int t = threadIdx.x;
-    u64 v[8];
-    const bool scaled = tw.w4096s != nullptr;
-    contig_forward<PACK>(io.buf_a + base, io.da, base, scaled ? tw.w4096s : tw.w4096, sm, v);
-#pragma unroll
-    for (int k = 0; k < 8; k++) ah[k * NT + t] = scaled ? v[k] : gl::mul(v[k], ninv);
-    __syncthreads();  // every thread is done reading sm
-    contig_forward<PACK>(io.buf_x + base, io.dx, base, tw.w4096, sm, v);
-#pragma unroll
-    for (int k = 0; k < 8; k++) v[k] = gl::mul(v[k], ah[k * NT + t]);
-    __syncthreads();
-    c_inv_row_b_store(t, sm, v);
-    __syncthreads();
-    c_inv_row_a_load(t, sm, v);
-    __syncthreads();
-    c_inv_row_a_store(t, sm, v);
-    __syncthreads();
-    c_inv_col_b_load(t, sm, tw, v);
-    __syncthreads();
-    c_inv_col_b_store(t, sm, v);
-    __syncthreads();
-    c_inv_col_a(t, sm, io.buf_x + base, base, PACK ? io.L : ~0ull);
-}
-
-// ---------------------------------------------------------------------------
-// launch helpers
-// ---------------------------------------------------------------------------
-
-// radix -> (RA, RB, columns per tile)
-#define PA_RADIX_TABLE(X)                                                                  \
-    X(2, 1, 2, 2048) X(4, 2, 2, 1024) X(8, 2, 4, 512) X(16, 4, 4, 256) X(32, 4, 8, 128)     \
-    X(64, 8, 8, 64) X(3, 3, 1, 1024) X(6, 3, 2, 512) X(12, 3, 4, 256) X(24, 3, 8, 128)      \
-    X(48, 6, 8, 64)
-
-int strided_columns(int R) {
-#define PA_COLS(r, a, b, c) if (R == r) return c;
-    PA_RADIX_TABLE(PA_COLS)
-#undef PA_COLS
-    return 0;
-}
-
-// Opt a kernel into the dynamic shared memory it needs (once per kernel).
-template <typename K>
-static void allow_smem(K kernel, size_t bytes) {
-    static std::mutex mu;
-    static std::unordered_set<const void*> done;
-    if (bytes <= 48 * 1024) return;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done.insert((const void*)kernel).second)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int B>
-struct Launcher {
-    const StridedGeom* g;
-    const NttBatch<B>* nb;
-    const Twiddles* tw;
-    cudaStream_t st;
-    bool stage_digits_ok;  // every digit source 16-byte aligned
-
-    int ops;               // 2: transform x and a; 1: x only (a's spectrum reused)
-
-    template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS>
-    void fwd_k() const {
-        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
-        size_t smem = STAGED ? StageSize<RA * RB, C, PACK>::BYTES : TILE * sizeof(u64);
-        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS>;
-        allow_smem(k, smem);
-        k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
-    }
-    bool stage_fwd, stage_inv;  // plan variant: staged or direct tile loads
-
-    template <int RA, int RB, int C, int OPS>
-    void fwd_ops(bool pack) const {
-        if (!pack) {
-            if (stage_fwd) return fwd_k<RA, RB, C, false, true, OPS>();
-            return fwd_k<RA, RB, C, false, false, OPS>();
-        }
-        if (stage_digits_ok && stage_fwd) return fwd_k<RA, RB, C, true, true, OPS>();
-        fwd_k<RA, RB, C, true, false, OPS>();
-    }
-    template <int RA, int RB, int C>
-    void fwd(bool pack) const {
-        if (ops == 1) return fwd_ops<RA, RB, C, 1>(pack);
-        fwd_ops<RA, RB, C, 2>(pack);
-    }
-    template <int RA, int RB, int C, bool LAST, bool STAGED>
-    void inv_k() const {
-        dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
-        size_t smem = (TILE + (STAGED ? RA * RB * C : 0)) * sizeof(u64);
-        auto k = k_inv_strided<RA, RB, C, LAST, B, STAGED>;
-        allow_smem(k, smem);
-        k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
-    }
-    template <int RA, int RB, int C>
-    void inv(bool last) const {
-        if (last) {
-            if (stage_inv) return inv_k<RA, RB, C, true, true>();
-            return inv_k<RA, RB, C, true, false>();
-        }
-        if (stage_inv) return inv_k<RA, RB, C, false, true>();
-        inv_k<RA, RB, C, false, false>();
-    }
-    void dispatch_fwd(int R, bool pack) const {
-#define PA_FWD(r, a, b, c) if (R == r) return fwd<a, b, c>(pack);
-        PA_RADIX_TABLE(PA_FWD)
-#undef PA_FWD
-    }
-    void dispatch_inv(int R, bool last) const {
-#define PA_INV(r, a, b, c) if (R == r) return inv<a, b, c>(last);
-        PA_RADIX_TABLE(PA_INV)
-#undef PA_INV
-    }
-};
-
-static StridedGeom strided_geom(const Geom& G, const Twiddles& tw, int p) {
-    u64 C = (u64)strided_columns(G.pass[p].R);
-    return StridedGeom{G.N, G.pass[p].M, G.pass[p].S, (u32)(G.pass[p].S / C), tw.passf[p], tw.passi[p]};
-}
 
 // Inter-pass twiddle tables of one strided pass (sub-problem size M, stride S):
 // fwd[k S + j] = w_M^(j k), inv[k S + j] = w_M^-(j k), from the transform's
@@ -376,54 +23,6 @@ cudaError_t launch_pass_twiddles(const Twiddles& tw, u64 N, u64 M, u64 S, u64* o
     return cudaGetLastError();
 }
 
-// ops = 2: transform x and a and build a's spectrum; ops = 1: x only, each
-// block's buf_a already holds a's spectrum (tile register order, times N^-1).
-template <int B>
-static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatch<B>& nb,
-                                cudaStream_t st, int ops = 2) {
-    bool stage_fwd = !(G.variant & PLAN_DIRECT_FWD), stage_inv = !(G.variant & PLAN_DIRECT_INV);
-    bool aligned = true;
-    for (int i = 0; i < nb.count; i++)
-        aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
-                  !nb.io[i].dx.sysmem && !nb.io[i].da.sysmem && !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
-    for (int p = 0; p < G.nstrided; p++) {
-        StridedGeom g = strided_geom(G, tw, p);
-        prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv}.dispatch_fwd(G.pass[p].R, p == 0);
-        prof_end(st);
-    }
-    dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
-    bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
-    u64 ninv = n_inverse(G.logN, G.three);
-    if (ops == 2) {
-        // both operands' tile passes in one kernel (a's spectrum stays on chip)
-        constexpr size_t smem = 2 * TILE * sizeof(u64);
-        prof_begin(st, "ntt_contig_both");
-        if (pack) {
-            allow_smem(k_contig_both<true, B>, smem);
-            k_contig_both<true, B><<<tiles, NT, smem, st>>>(nb, ninv, tw);
-        } else {
-            allow_smem(k_contig_both<false, B>, smem);
-            k_contig_both<false, B><<<tiles, NT, smem, st>>>(nb, ninv, tw);
-        }
-        prof_end(st);
-    } else {
-        prof_begin(st, "ntt_contig_fused");
-        if (pack)
-            k_contig_fused<true, B><<<tiles, NT, 0, st>>>(nb, tw);
-        else
-            k_contig_fused<false, B><<<tiles, NT, 0, st>>>(nb, tw);
-        prof_end(st);
-    }
-    for (int p = G.nstrided - 1; p >= 0; p--) {
-        StridedGeom g = strided_geom(G, tw, p);
-        prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv}.dispatch_inv(G.pass[p].R, p == 0);
-        prof_end(st);
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;
@@ -440,10 +39,11 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     nb.io[0] = BlockIO{j.buf_a, j.buf_a, j.da, j.da, j.L};
     bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.sysmem && !j.da.one_bit;
     const Geom& G = j.geom;
+    bool narrow = narrow_plan<1>(G);
     for (int p = 0; p < G.nstrided; p++) {
-        StridedGeom g = strided_geom(G, j.tw, p);
+        StridedGeom g = strided_geom(G, j.tw, p, narrow);
         prof_begin(st, "ntt_seed_strided");
-        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1, !(G.variant & PLAN_DIRECT_FWD), true}
+        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1, !(G.variant & PLAN_DIRECT_FWD), true, narrow}
             .dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }
@@ -463,18 +63,6 @@ cudaError_t launch_convolution_seeded(const NttJob& j, cudaStream_t st) {
     nb.count = 1;
     nb.io[0] = BlockIO{j.buf_x, j.buf_a, j.dx, j.da, j.L};
     return launch_batch<1>(j.geom, j.tw, nb, st, 1);
-}
-
-cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const BlockIO* io,
-                                     int count, cudaStream_t st) {
-    for (int i = 0; i < count; i += MAX_BATCH) {
-        NttBatch<MAX_BATCH> nb;
-        nb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
-        for (int k = 0; k < nb.count; k++) nb.io[k] = io[i + k];
-        cudaError_t e = launch_batch<MAX_BATCH>(G, tw, nb, st);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
 }
 
 }  // namespace pa

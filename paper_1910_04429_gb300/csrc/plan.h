@@ -32,7 +32,8 @@ struct Geom {
 constexpr int PLAN_R0_LAST = 1;     // the odd radix R_0 runs last among the strided passes
 constexpr int PLAN_DIRECT_FWD = 2;  // forward strided passes load their tiles directly
 constexpr int PLAN_DIRECT_INV = 4;  // inverse strided passes load their tiles directly
-constexpr int PLAN_VARIANTS = 8;
+constexpr int PLAN_NARROW = 8;      // single-pass plans, single blocks: tiles of a quarter of the columns
+constexpr int PLAN_VARIANTS = 16;
 
 // N = R_0 * 64^q * 4096 with N = 2^logN (R_0 = 2^((logN-12) mod 6), omitted when
 // 1) or N = 3 * 2^logN (R_0 = 3 * 2^((logN-12) mod 6), which must be <= 48):

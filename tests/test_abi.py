@@ -101,7 +101,7 @@ def test_argument_checks_without_gpu():
     assert lib.pa_prepare(0) == binding.PA_EINVAL
     assert lib.pa_fault_inject(99) == binding.PA_EINVAL
     assert lib.pa_plan_override(0, 0) == binding.PA_EINVAL
-    assert lib.pa_plan_override(1000, 8) == binding.PA_EINVAL
+    assert lib.pa_plan_override(1000, 16) == binding.PA_EINVAL
     assert lib.pa_autotune(0, 1, None) == binding.PA_EINVAL
     h = ctypes.c_void_p(0)
     assert lib.pa_seed_create(null, 100, null, ctypes.byref(h)) == binding.PA_EINVAL

@@ -11,10 +11,11 @@ from tests.gpu_util import dev, gpu_hash, host
 
 pytestmark = pytest.mark.gpu
 
-# transform lengths 2^12 (no strided pass), 2^14 ([4]), 3*2^16 ([48]),
-# 2^19 ([2, 64]), 3*2^18 ([3, 64]) and 3*2^24 ([3, 64, 64]; with the odd radix
-# last, [64, 64, 3], the middle pass has 64 sub-problems of 192 tiles each)
-SIZES = [1000, 100_003, 1_536_000, 3_000_001, 4_800_000, 300_000_017]
+# transform lengths 2^12 (no strided pass), 2^14 ([4]), 2^17 ([32]), 3*2^16
+# ([48]), 2^19 ([2, 64]), 3*2^18 ([3, 64]) and 3*2^24 ([3, 64, 64]; with the
+# odd radix last, [64, 64, 3], the middle pass has 64 sub-problems of 192 tiles
+# each); the single-pass lengths also run with narrow tiles (variants 8 .. 15)
+SIZES = [1000, 100_003, 1_000_000, 1_536_000, 3_000_001, 4_800_000, 300_000_017]
 
 
 @pytest.mark.parametrize("n", SIZES)
@@ -22,7 +23,7 @@ def test_every_plan_variant_is_exact(n):
     blk = inputs.make_block(n, n // 3 or 1, seed=n)
     want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m, threads=oracle.default_threads())
     try:
-        for v in range(8):
+        for v in range(16):
             binding.plan_override(n, v)
             np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
                                           err_msg=f"variant {v}")
