@@ -12,6 +12,7 @@
 #include <unordered_set>
 
 #include "cp_async.cuh"
+#include "pdl.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -60,6 +61,7 @@ struct StageSize {
 template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
+    pdl_begin();
     using S = Strided<RA, RB, C>;
     using SZ = StageSize<S::R, C, PACK>;
     extern __shared__ __align__(16) u64 dsm[];
@@ -115,6 +117,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
 template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
 __global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
+    pdl_begin();
     using S = Strided<RA, RB, C>;
     extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
@@ -176,6 +179,7 @@ __device__ __forceinline__ void contig_forward(const u64* src, const Digits& d, 
 template <bool PACK, int B>
 __global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttBatch<B> nb, u64 ninv,
                                                     Twiddles tw) {
+    pdl_begin();
     __shared__ u64 sm[TILE];
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
@@ -200,6 +204,7 @@ __global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttB
 // only the digits below io.L.
 template <bool PACK, int B>
 __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ NttBatch<B> nb, Twiddles tw) {
+    pdl_begin();
     __shared__ u64 sm[TILE];
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ Ntt
 template <bool PACK, int B>
 __global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ NttBatch<B> nb, u64 ninv,
                                                     Twiddles tw) {
+    pdl_begin();
     extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
     u64* ah = dsm + TILE;
@@ -275,6 +281,7 @@ __device__ __forceinline__ void bar_sync_half() {  // named barrier 1 over NT th
 // at the same block barriers. Shared memory: two working tiles, a's spectrum.
 static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_constant__ NttBatch<1> nb, u64 ninv,
                                                           Twiddles tw) {
+    pdl_begin();
     extern __shared__ __align__(16) u64 dsm[];
     const int h = threadIdx.x / NT, t = threadIdx.x % NT;  // half 0: a, half 1: x
     u64* sm = dsm + h * TILE;
@@ -352,7 +359,7 @@ struct Launcher {
         size_t smem = STAGED ? StageSize<RA * RB, C, PACK>::BYTES : TILE * sizeof(u64);
         auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS>;
         allow_smem(k, smem);
-        k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+        launch_pdl(k, grid, dim3(NT), smem, st, *g, *nb, *tw);
     }
     bool stage_fwd, stage_inv;  // plan variant: staged or direct tile loads
 
@@ -376,7 +383,7 @@ struct Launcher {
         size_t smem = (TILE + (STAGED ? RA * RB * C : 0)) * sizeof(u64);
         auto k = k_inv_strided<RA, RB, C, LAST, B, STAGED>;
         allow_smem(k, smem);
-        k<<<grid, NT, smem, st>>>(*g, *nb, *tw);
+        launch_pdl(k, grid, dim3(NT), smem, st, *g, *nb, *tw);
     }
     template <int RA, int RB, int C>
     void inv(bool last) const {
@@ -468,7 +475,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
             constexpr size_t smem = 3 * TILE * sizeof(u64);
             prof_begin(st, "ntt_contig_both");
             allow_smem(k_contig_pair, smem);
-            k_contig_pair<<<tiles, 2 * NT, smem, st>>>(nb, ninv, tw);
+            launch_pdl(k_contig_pair, tiles, dim3(2 * NT), smem, st, nb, ninv, tw);
             prof_end(st);
             paired = true;
         }
@@ -479,18 +486,18 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
         prof_begin(st, "ntt_contig_both");
         if (pack) {
             allow_smem(k_contig_both<true, B>, smem);
-            k_contig_both<true, B><<<tiles, NT, smem, st>>>(nb, ninv, tw);
+            launch_pdl(k_contig_both<true, B>, tiles, dim3(NT), smem, st, nb, ninv, tw);
         } else {
             allow_smem(k_contig_both<false, B>, smem);
-            k_contig_both<false, B><<<tiles, NT, smem, st>>>(nb, ninv, tw);
+            launch_pdl(k_contig_both<false, B>, tiles, dim3(NT), smem, st, nb, ninv, tw);
         }
         prof_end(st);
     } else if (!paired) {
         prof_begin(st, "ntt_contig_fused");
         if (pack)
-            k_contig_fused<true, B><<<tiles, NT, 0, st>>>(nb, tw);
+            launch_pdl(k_contig_fused<true, B>, tiles, dim3(NT), 0, st, nb, tw);
         else
-            k_contig_fused<false, B><<<tiles, NT, 0, st>>>(nb, tw);
+            launch_pdl(k_contig_fused<false, B>, tiles, dim3(NT), 0, st, nb, tw);
         prof_end(st);
     }
     for (int p = G.nstrided - 1; p >= 0; p--) {

@@ -272,12 +272,29 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
     return PA_OK;
 }
 
+// The carry step's scratch states, cleared on st now: queued before the
+// transforms, so that no memset sits between the last transform kernel and the
+// carry kernel (which then follows it by programmatic dependent launch).
+int carry_states(uint64_t n, cudaStream_t st, Scratch& scr, u32** state) {
+    void* p;
+    int rc = scr.get(carry_state_words(n) * sizeof(u32), &p);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(p, 0, carry_state_words(n) * sizeof(u32), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
+    *state = (u32*)p;
+    return PA_OK;
+}
+
 int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint64_t m,
-                uint64_t* out, cudaStream_t st, Scratch& scr) {
-    void* state;
+                uint64_t* out, cudaStream_t st, Scratch& scr, u32* zeroed_state = nullptr) {
+    u32* state = zeroed_state;
     int rc;
-    if ((rc = scr.get(carry_state_words(n) * sizeof(u32), &state))) return rc;
-    CarryJob c{coef, L, seed_b, n, m, out, (u32*)state};
+    if (!state) {
+        void* p;
+        if ((rc = scr.get(carry_state_words(n) * sizeof(u32), &p))) return rc;
+        state = (u32*)p;
+    }
+    CarryJob c{coef, L, seed_b, n, m, out, state, zeroed_state != nullptr};
     cudaError_t e = launch_carry(c, st);
     if (e != cudaSuccess) return cuda_fail(e, "carry launch");
     return PA_OK;
@@ -287,10 +304,12 @@ int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* see
                 uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool,
                 bool sysmem = false) {
     Scratch scr(st, pool);
-    u64* coef = nullptr;
-    int rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef, sysmem);
+    u32* state = nullptr;
+    int rc = carry_states(n, st, scr, &state);
     if (rc) return rc;
-    return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr);
+    u64* coef = nullptr;
+    if ((rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef, sysmem))) return rc;
+    return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr, state);
 }
 
 int side_streams(int dev) {
@@ -348,7 +367,10 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     u32* cb = (u32*)(w + words);
     std::vector<CarryJob> cj(count);
 
-    cudaError_t e = cudaEventRecord(d.fork, st);
+    // every block's carry states cleared at once, before the transforms
+    cudaError_t e = cudaMemsetAsync(cb, 0, carry_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
+    e = cudaEventRecord(d.fork, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(fork)");
     int used = 0;
     for (size_t g = 0; g < groups.size(); g++) {
@@ -363,7 +385,7 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
             uint16_t top = top_digit_mask(b.n);
             io[k] = BlockIO{w, w + G.N, Digits{(const uint16_t*)b.key, L, top},
                             Digits{(const uint16_t*)b.seed_a, L, top}, L};
-            cj[idx[k]] = CarryJob{w, L, b.seed_b, b.n, b.m, b.out, cb};
+            cj[idx[k]] = CarryJob{w, L, b.seed_b, b.n, b.m, b.out, cb, true};
             cb += carry_state_words(b.n);
             w += 2 * G.N;
         }
@@ -443,16 +465,17 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
         }
         void* mo = nullptr;
         bool out_mapped = host_mapped(out, &mo);
-        if ((e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
+        u32* state = nullptr;
+        if ((rc = carry_states(n, st, scr, &state)) || (e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
             cudaStreamWaitEvent(st, d.b_ready, 0);
-            return cuda_fail(e, "cudaStreamWaitEvent");
+            return rc ? rc : cuda_fail(e, "cudaStreamWaitEvent");
         }
         u64* coef = nullptr;
         rc = queue_convolution((const u64*)dx, (const u64*)da, n, st, scr, dev, &coef);
         if ((e = cudaStreamWaitEvent(st, d.b_ready, 0))) return cuda_fail(e, "cudaStreamWaitEvent");
         if (rc) return rc;
         if (!out_mapped && (rc = scr.get(out_bytes, &mo))) return rc;
-        if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr))) return rc;
+        if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr, state))) return rc;
         if (!out_mapped && (e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "cudaMemcpyAsync(D2H)");
     }
@@ -744,6 +767,8 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
     j.geom = seed->G;
     j.L = (seed->n + 15) / 16;
     if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+    u32* state = nullptr;
+    if ((rc = carry_states(seed->n, st, scr, &state))) return rc;
     void* bx;
     if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
     j.buf_x = (u64*)bx;
@@ -752,7 +777,7 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
     j.da = j.dx;
     cudaError_t e = launch_convolution_seeded(j, st);
     if (e != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
-    return queue_carry(j.buf_x, j.L, seed_b, seed->n, m, out, st, scr);
+    return queue_carry(j.buf_x, j.L, seed_b, seed->n, m, out, st, scr, state);
 }
 
 int pa_toeplitz(const uint64_t* key, const uint64_t* seed, uint64_t n, uint64_t m, uint64_t* out,

@@ -27,6 +27,7 @@
 // and carries on with a carry-in of 0, so it always terminates.
 #include "cp_async.cuh"
 #include "pa_internal.h"
+#include "pdl.cuh"
 
 namespace pa {
 
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     __shared__ __align__(16) u64 bs[SM_LIMBS_PAD];
     __shared__ u32 tile_sh;
     __shared__ int carry_in_sh;
+    pdl_begin();
     const CarryJob& c = cb.job[blockIdx.y];
     const u64 Ly = (c.n + 63) / 64, tiles = carry_tiles(c.n);
     u32* state = c.state;  // tiles words, then the ticket counter
@@ -283,6 +285,7 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     for (int i = 0; i < cb.count; i++) {
         u64 tt = carry_tiles(cb.job[i].n);
         tiles = tt > tiles ? tt : tiles;
+        if (cb.job[i].zeroed) continue;  // the caller cleared the states earlier on the stream
         cudaError_t e = cudaMemsetAsync(cb.job[i].state, 0, (tt + 1) * sizeof(u32), st);
         if (e != cudaSuccess) return e;
     }
@@ -294,12 +297,10 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
         vec = vec && (uintptr_t)cb.job[i].coef % 16 == 0 && (uintptr_t)cb.job[i].b % 16 == 0;
     dim3 grid((unsigned)tiles, (unsigned)cb.count);
     prof_begin(st, "carry_lookback");
-    if (vec)
-        k_carry<B, true><<<grid, CARRY_THREADS, 0, st>>>(cb, start, limit);
-    else
-        k_carry<B, false><<<grid, CARRY_THREADS, 0, st>>>(cb, start, limit);
+    cudaError_t e = vec ? launch_pdl(k_carry<B, true>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)
+                        : launch_pdl(k_carry<B, false>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit);
     prof_end(st);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_carry(const CarryJob& c, cudaStream_t st) {

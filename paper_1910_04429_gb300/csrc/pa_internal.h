@@ -53,7 +53,8 @@ struct CarryJob {
     const u64* b;     // addend limbs, ceil(n/64)
     u64 n, m;
     u64* out;         // ceil(m/64) limbs
-    u32* state;       // scratch, carry_state_words(n) words, 4-byte aligned (zeroed by the launch)
+    u32* state;       // scratch, carry_state_words(n) words, 4-byte aligned
+    bool zeroed;      // state already cleared earlier on the stream; else the launch clears it
 };
 template <int B>
 struct CarryBatch {

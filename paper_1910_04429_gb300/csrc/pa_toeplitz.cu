@@ -11,12 +11,14 @@
 // This file holds the last step: the parity of m consecutive coefficients,
 // packed into little-endian 64-bit limbs.
 #include "pa_internal.h"
+#include "pdl.cuh"
 
 namespace pa {
 
 // One warp per output limb: lane t takes coefficients 64q + t and 64q + 32 + t,
 // and two ballots gather their low bits (coalesced 256-byte reads).
 __global__ void k_parity_extract(const u64* __restrict__ coef, u64 first, u64 m, u64* __restrict__ out) {
+    pdl_begin();
     const u64 limbs = (m + 63) / 64;
     const int lane = threadIdx.x & 31;
     const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
@@ -35,9 +37,9 @@ cudaError_t launch_parity_extract(const u64* coef, u64 first, u64 m, u64* out, c
     u64 blocks = (limbs + WARPS - 1) / WARPS;
     unsigned grid = (unsigned)(blocks < 152 * 16 ? blocks : 152 * 16);
     prof_begin(st, "toeplitz_parity");
-    k_parity_extract<<<grid, THREADS, 0, st>>>(coef, first, m, out);
+    cudaError_t e = launch_pdl(k_parity_extract, dim3(grid), dim3(THREADS), 0, st, coef, first, m, out);
     prof_end(st);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace pa
