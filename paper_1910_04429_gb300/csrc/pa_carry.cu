@@ -12,17 +12,20 @@
 // chain: carry_{j+1} = [u_j + carry_j >= 2^64], whose generate / propagate
 // pairs (g_j = [u_j = 2^64], p_j = [u_j = 2^64 - 1]) compose associatively.
 //
-// One kernel, decoupled look-back: each CTA takes the next tile of 1024 limbs
-// from an atomic ticket (so every earlier tile has started), stages its digits
-// and addend limbs in shared memory with coalesced loads, scans its (g, p)
-// pairs, publishes the tile aggregate, walks back over the published states of
-// earlier tiles to obtain its carry-in, publishes its inclusive prefix, and
-// writes its output bits. The carry into a tile is decided by the last limbs
-// before it unless they propagate (u = 2^64 - 1): the tile stages a four-limb
-// halo and resolves it from the two limbs before it, with no wait on any other
-// tile. Only when both propagate does warp 0 read 32 predecessor states per
-// round, stopping at the latest one that fixes its carry out (an inclusive
-// prefix, or an aggregate with P = 0). Every wait on another tile is bounded: when the
+// One kernel over the tiles of 1024 limbs that hold output limbs (from limb
+// (n - m) / 64 up; the limbs below matter only through the carry into the
+// first of them). Each CTA takes the next such tile from an atomic ticket (so
+// every earlier tile has started), stages its digits and addend limbs in
+// shared memory with coalesced loads, scans its (g, p) pairs and publishes the
+// tile aggregate. The carry into a tile is decided by the last limbs before it
+// unless they propagate (u = 2^64 - 1): a four-limb halo resolves it from the
+// two limbs before the tile, with no wait on any other tile. Otherwise the
+// first output tile composes the tiles below it, one whole-CTA tile at a time,
+// until one does not propagate (or limb 0); a later tile has warp 0 read 32
+// predecessor states per round, down to the first output tile at most,
+// stopping at the latest one that fixes its carry out (an inclusive prefix,
+// or an aggregate with P = 0). The tile then publishes its inclusive prefix
+// and writes its output bits. Every wait on another tile is bounded: when the
 // limit runs out the kernel records PA_STATUS_TIMEOUT in the device status word
 // and carries on with a carry-in of 0, so it always terminates.
 #include "cp_async.cuh"
@@ -143,26 +146,11 @@ __device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long 
 }
 
 // VEC: coef and b are 16-byte aligned (staged with cp.async), else plain loads.
-// ticket_start > 0 (fault injection) leaves the first tiles unprocessed and
-// makes every tile take the look-back path, so that the wait on them runs out.
-template <int B, bool VEC>
-__global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
-                                                         u32 ticket_start, u32 spin_limit) {
-    __shared__ __align__(16) u64 cs[SM_COEF];
-    __shared__ __align__(16) u64 bs[SM_LIMBS_PAD];
-    __shared__ u32 tile_sh;
-    __shared__ int carry_in_sh;
-    pdl_begin();
-    const CarryJob& c = cb.job[blockIdx.y];
-    const u64 Ly = (c.n + 63) / 64, tiles = carry_tiles(c.n);
-    u32* state = c.state;  // tiles words, then the ticket counter
-    if (threadIdx.x == 0) tile_sh = atomicAdd(&state[tiles], 1u) + ticket_start;
-    __syncthreads();
-    const u64 t = tile_sh;
-    if (t >= tiles) return;
-
-    // stage digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS), J0 = 1024 t - 4
-    const long long J0 = (long long)t * TILE_LIMBS - HALO_LO;
+// Digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS) of tile tt
+// (J0 = 1024 tt - 4) into cs / bs; positions outside the operands read 0.
+template <bool VEC>
+__device__ __forceinline__ void stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs) {
+    const long long J0 = tt * TILE_LIMBS - HALO_LO;
     if (VEC) {
         stage_pairs(cs, c.coef, 4 * J0, SM_COEF / 2, c.L);
         stage_pairs(bs, c.b, J0, SM_LIMBS_PAD / 2, Ly);
@@ -178,6 +166,32 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
             bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
         }
     }
+}
+
+// Only the tiles that hold output limbs (bits [n - m, n)) are processed: the
+// limbs below matter only through the carry into the first of them. Grid:
+// carry_tiles(n) - first_out_tile(n, m) CTAs per block (the widest block's
+// count along x). ticket_start > 0 (fault injection) leaves the first output
+// tiles unprocessed and makes every tile take the look-back path, so that the
+// wait on them runs out.
+template <int B, bool VEC>
+__global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
+                                                         u32 ticket_start, u32 spin_limit) {
+    __shared__ __align__(16) u64 cs[SM_COEF];
+    __shared__ __align__(16) u64 bs[SM_LIMBS_PAD];
+    __shared__ u32 tile_sh;
+    __shared__ int decided_sh, carry_in_sh;
+    pdl_begin();
+    const CarryJob& c = cb.job[blockIdx.y];
+    const u64 Ly = (c.n + 63) / 64, tiles = carry_tiles(c.n);
+    const u64 t0 = first_out_tile(c.n, c.m);
+    u32* state = c.state;  // tiles words, then the ticket counter
+    if (threadIdx.x == 0) tile_sh = atomicAdd(&state[tiles], 1u) + ticket_start;
+    __syncthreads();
+    const u64 t = t0 + tile_sh;
+    if (t >= tiles) return;
+
+    stage_tile<VEC>(c, Ly, (long long)t, cs, bs);
     __syncthreads();
 
     const int l0 = HALO_LO + CARRY_LIMBS * threadIdx.x;  // shared position of the thread's first limb
@@ -191,31 +205,63 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     int total;
     int pre = block_exclusive(acc, &total);
 
-    if (threadIdx.x < 32) {
-        // warp 0: publish the aggregate; the carry into the tile from the two limbs
-        // before it when they decide it (the common case: no wait on any other
-        // tile), else look back over the published states 32 at a time
-        const int lane = threadIdx.x;
-        if (lane == 0) publish(&state[t], (t == 0 ? ST_INC : ST_AGG) | (u32)total);
+    // publish the aggregate; the carry into the tile from the two limbs before
+    // it when they decide it (the common case: no wait and no more reads)
+    if (threadIdx.x == 0) {
+        publish(&state[t], (t == 0 ? ST_INC : ST_AGG) | (u32)total);
         int decided = 0, cin = 0;
-        if (lane == 0 && ticket_start == 0) {
+        if (ticket_start == 0) {
             Limb h[2];  // limbs 1024 t - 2 and 1024 t - 1 (zero below limb 0)
             limbs_u<2>(cs, bs, HALO_LO - 2, h);
             if (!(h[1].gp & 2)) decided = 1, cin = h[1].gp & 1;  // generate or kill
             else if (!(h[0].gp & 2)) decided = 1, cin = h[0].gp & 1;
         }
-        decided = __shfl_sync(0xffffffffu, decided, 0);
-        cin = __shfl_sync(0xffffffffu, cin, 0);
-        if (!decided) {
+        decided_sh = decided;
+        carry_in_sh = cin;
+    }
+    __syncthreads();
+    if (!decided_sh) {
+        if (t == t0 && ticket_start == 0) {
+            // the first output tile: compose the tiles below it, one whole-CTA
+            // tile at a time, until one does not propagate (or limb 0)
+            int later = GP_IDENTITY, cin = 0;
+            for (long long tc = (long long)t0 - 1;; tc--) {
+                if (tc < 0) {
+                    cin = later & 1;  // the chain starts with carry 0
+                    break;
+                }
+                __syncthreads();  // cs / bs free again
+                stage_tile<VEC>(c, Ly, tc, cs, bs);
+                __syncthreads();
+                Limb w[CARRY_LIMBS];
+                limbs_u<CARRY_LIMBS>(cs, bs, l0, w);
+                int a = GP_IDENTITY;
+#pragma unroll
+                for (int i = 0; i < CARRY_LIMBS; i++) a = compose(a, w[i].gp);  // below tile t: all < Ly
+                int tot;
+                block_exclusive(a, &tot);
+                later = compose(tot, later);
+                if (!(tot & 2)) {
+                    cin = later & 1;
+                    break;
+                }
+            }
+            if (threadIdx.x == 0) carry_in_sh = cin;
+        } else if (threadIdx.x < 32) {
+            // a later output tile: look back over the published states 32 at a
+            // time, down to the first output tile at most (which publishes a
+            // state that fixes its carry out: an inclusive prefix, or P = 0)
+            const int lane = threadIdx.x;
             long long base = (long long)t - 1;  // lane l looks at tile base - l
             int later = GP_IDENTITY;            // tiles after the current window, composed
             while (true) {
                 long long i = base - lane;
-                u32 s = ST_INC;  // below tile 0: the chain starts with carry 0
-                if (i >= 0) {
+                u32 s = ST_INC;  // below the first output tile: never reached (see above)
+                if (i >= (long long)t0) {
                     s = observe(&state[i]);
                     u32 spins = 0;
-                    while (!(s & (ST_AGG | ST_INC))) {
+                    while (!(i == (long long)t0 ? ((s & ST_INC) || ((s & ST_AGG) && !(s & 2u)))
+                                                 : (s & (ST_AGG | ST_INC)) != 0)) {
                         if (++spins > spin_limit) {
                             atomicOr(&g_status, PA_STATUS_TIMEOUT);
                             s = ST_INC;  // give up: treat as an inclusive prefix (0, 0)
@@ -241,11 +287,10 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
                 if (inc) break;
                 base -= 32;
             }
-            cin = later & 1;
+            if (lane == 0) carry_in_sh = later & 1;  // carry into the tile
         }
-        if (lane == 0) carry_in_sh = cin;  // carry into the tile (the chain starts with 0)
+        __syncthreads();
     }
-    __syncthreads();
     // the inclusive prefix for tiles that look back past this one
     if (threadIdx.x == 0 && t > 0) publish(&state[t], ST_INC | (u32)compose(carry_in_sh, total));
     int carry = (pre & 1) | ((pre >> 1) & carry_in_sh);
@@ -284,7 +329,8 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     u64 tiles = 0;
     for (int i = 0; i < cb.count; i++) {
         u64 tt = carry_tiles(cb.job[i].n);
-        tiles = tt > tiles ? tt : tiles;
+        u64 out_tiles = tt - first_out_tile(cb.job[i].n, cb.job[i].m);
+        tiles = out_tiles > tiles ? out_tiles : tiles;
         if (cb.job[i].zeroed) continue;  // the caller cleared the states earlier on the stream
         cudaError_t e = cudaMemsetAsync(cb.job[i].state, 0, (tt + 1) * sizeof(u32), st);
         if (e != cudaSuccess) return e;

@@ -68,6 +68,8 @@ constexpr u32 CARRY_SPIN_LIMIT = 1u << 20;  // polls of a predecessor tile befor
 constexpr u32 PA_STATUS_TIMEOUT = 1u;       // device status bit: a bounded wait ran out
 GL_HD u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
 GL_HD u64 carry_state_words(u64 n) { return carry_tiles(n) + 1; }  // tile states + ticket
+// the first carry tile holding output limbs (limb (n - m) / 64 onwards)
+GL_HD u64 first_out_tile(u64 n, u64 m) { return ((n - m) / 64) / CARRY_TILE_LIMBS; }
 cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
 // Carry steps of `count` independent blocks (any sizes), MAX_BATCH per launch.
 cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st);

@@ -188,6 +188,30 @@ def test_carry_decided_at_tile_boundaries(pattern):
     assert to_int(host(out)) == _carry_ref(coef, to_int(b), n, m)
 
 
+@pytest.mark.parametrize("case", ["generate_deep", "killed", "no_generate", "mid_tile"])
+def test_carry_walk_back_below_output(case):
+    """Only the carry tiles holding output limbs run; the first of them composes
+    the tiles below it when its halo propagates. b all ones (every limb
+    propagates) with a generate at limb 5: the carry ripples through seven
+    tiles into the output; a kill at limb 3000 stops it; no generate at all
+    walks back to limb 0; and an output range starting mid-tile."""
+    import torch
+
+    n = 64 * 1024 * 8 + 17
+    m = 64 * 1024 + 3 if case != "mid_tile" else 64 * 1024 * 3 + 40 * 64 + 9
+    L, Ly = (n + 15) // 16, (n + 63) // 64
+    coef = np.zeros(L, dtype=np.uint64)
+    b = np.full(Ly, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64)
+    if case != "no_generate":
+        g = 5
+        coef[4 * (g - 2) + 3] = 65536  # hi(V_(g-2)) = 1: limb g generates
+    if case == "killed":
+        b[3000] = 0
+    out = binding.carry_extract(dev(coef), dev(b), n, m)
+    torch.cuda.synchronize()
+    assert to_int(host(out)) == _carry_ref(coef, to_int(b), n, m)
+
+
 def test_hash_host_buffers():
     blk = inputs.make_block(3_000_000, 700_001, seed=11)
     got = binding.hash_host(blk.x, blk.a, blk.b, blk.n, blk.m)
