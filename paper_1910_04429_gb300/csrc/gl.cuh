@@ -239,6 +239,26 @@ GL_HD int root_shift(int e) {
     return INV ? (192 - s) % 192 : s;
 }
 
+// v[k] <- v[k] * w^(j k) for 0 < k < K, w = 2^(192/R) (or its inverse), for a
+// run-time row j < J that is uniform across a warp: one branch on j picks a
+// copy in which every shift amount is a compile-time constant and takes its
+// fixed route (a run-time amount would pay a range dispatch per shift).
+template <int R, bool INV, int K, int J>
+struct RowRoots {
+    static GL_HD void apply(u64* v, int j) {
+        if (j == J - 1) {
+#pragma unroll
+            for (int k = 1; k < K; k++) v[k] = shl_v(v[k], root_shift<R, INV>((J - 1) * k));
+        } else {
+            RowRoots<R, INV, K, J - 1>::apply(v, j);
+        }
+    }
+};
+template <int R, bool INV, int K>
+struct RowRoots<R, INV, K, 1> {  // row 0: w^0 = 1
+    static GL_HD void apply(u64*, int) {}
+};
+
 template <int R>
 GL_HD void dft_fwd(u64* v);
 

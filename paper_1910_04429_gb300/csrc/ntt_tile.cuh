@@ -117,9 +117,9 @@ struct Strided {
             v[j1] = PACK ? digit_at(dig, p) : buf[p];
         }
         gl::dft<RB, false>(v);
+        gl::RowRoots<R, false, RB, RA>::apply(v, j0);
 #pragma unroll
-        for (int kr = 0; kr < RB; kr++)
-            sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
+        for (int kr = 0; kr < RB; kr++) sm[(kr * RA + j0) * C + c] = v[kr];
     }
 
     // fwd_a reading the tile from a [R][C] staging copy: words, or (PACK) 16-bit
@@ -141,9 +141,9 @@ struct Strided {
             }
         }
         gl::dft<RB, false>(v);
+        gl::RowRoots<R, false, RB, RA>::apply(v, j0);
 #pragma unroll
-        for (int kr = 0; kr < RB; kr++)
-            sm[(kr * RA + j0) * C + c] = gl::shl_v(v[kr], gl::root_shift<R, false>(j0 * kr));
+        for (int kr = 0; kr < RB; kr++) sm[(kr * RA + j0) * C + c] = v[kr];
     }
 
     // inter-pass twiddle w_M^(+-jl k) of column jl, digit k: the pass's table, or
@@ -218,8 +218,8 @@ struct Strided {
         int j0 = it / C, c = it % C;
         u64 v[RB];
 #pragma unroll
-        for (int kr = 0; kr < RB; kr++)
-            v[kr] = gl::shl_v(sm[(kr * RA + j0) * C + c], gl::root_shift<R, true>(j0 * kr));
+        for (int kr = 0; kr < RB; kr++) v[kr] = sm[(kr * RA + j0) * C + c];
+        gl::RowRoots<R, true, RB, RA>::apply(v, j0);
         gl::dft<RB, true>(v);
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {
@@ -252,9 +252,9 @@ GL_HD void c_fwd_col_a(int t, const u64* src, const Digits& dig, u64 base, u64* 
         v[j1] = PACK ? digit_at(dig, base + off) : src[off];
     }
     gl::dft<8, false>(v);
+    gl::RowRoots<64, false, 8, 8>::apply(v, ln.u);
 #pragma unroll
-    for (int kr = 0; kr < 8; kr++)
-        sm[sidx(kr * 8 + ln.u, ln.idx)] = gl::shl_v(v[kr], gl::root_shift<64, false>(ln.u * kr));
+    for (int kr = 0; kr < 8; kr++) sm[sidx(kr * 8 + ln.u, ln.idx)] = v[kr];
 }
 
 // F3: kr = u: length-8 DFT over j0, twiddle w_4096^(c k) with k = 8 ks + kr (regs only)
@@ -279,8 +279,7 @@ GL_HD void c_fwd_row_a_load(int t, const u64* sm, u64* v) {
 #pragma unroll
     for (int j1 = 0; j1 < 8; j1++) v[j1] = sm[sidx(ln.idx, ln.u + 8 * j1)];
     gl::dft<8, false>(v);
-#pragma unroll
-    for (int kr = 0; kr < 8; kr++) v[kr] = gl::shl_v(v[kr], gl::root_shift<64, false>(ln.u * kr));
+    gl::RowRoots<64, false, 8, 8>::apply(v, ln.u);
 }
 // F6
 GL_HD void c_fwd_row_a_store(int t, u64* sm, const u64* v) {
@@ -307,8 +306,8 @@ GL_HD void c_inv_row_b_store(int t, u64* sm, u64* v) {
 GL_HD void c_inv_row_a_load(int t, const u64* sm, u64* v) {
     Lane ln = lane_of(t);
 #pragma unroll
-    for (int kr = 0; kr < 8; kr++)
-        v[kr] = gl::shl_v(sm[sidx(ln.idx, kr * 8 + ln.u)], gl::root_shift<64, true>(ln.u * kr));
+    for (int kr = 0; kr < 8; kr++) v[kr] = sm[sidx(ln.idx, kr * 8 + ln.u)];
+    gl::RowRoots<64, true, 8, 8>::apply(v, ln.u);
     gl::dft<8, true>(v);
 }
 // I3
@@ -336,8 +335,8 @@ GL_HD void c_inv_col_a(int t, const u64* sm, u64* dst, u64 base, u64 keep) {
     Lane ln = lane_of(t);
     u64 v[8];
 #pragma unroll
-    for (int kr = 0; kr < 8; kr++)
-        v[kr] = gl::shl_v(sm[sidx(kr * 8 + ln.u, ln.idx)], gl::root_shift<64, true>(ln.u * kr));
+    for (int kr = 0; kr < 8; kr++) v[kr] = sm[sidx(kr * 8 + ln.u, ln.idx)];
+    gl::RowRoots<64, true, 8, 8>::apply(v, ln.u);
     gl::dft<8, true>(v);
 #pragma unroll
     for (int j1 = 0; j1 < 8; j1++) {
