@@ -78,10 +78,9 @@ int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
  * filled (it waits for `stream`). key and seed_a are copied into device
  * staging buffers from the library's pool on the library's copy stream, and
  * seed_b behind them, so b's copy overlaps the transforms; the hash waits on
- * each copy with an event. If `out` is pinned (page-locked and mapped, e.g.
- * cudaHostAlloc) the last kernel writes the result into it directly (over
- * NVLink-C2C on Grace systems); otherwise it is copied back on `stream`.
- * Pinned inputs make the copies asynchronous; pageable memory also works.
+ * each copy with an event; the result is copied back on `stream`. Pinned
+ * (page-locked) buffers make the copies asynchronous; pageable memory also
+ * works.
  *
  * pa_hash_host_async: the same, returning once everything is queued. The
  * copy stream runs at most two calls ahead of the hashes (staging memory is

@@ -458,7 +458,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     bool aligned = true;
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
-                  !nb.io[i].dx.sysmem && !nb.io[i].da.sysmem && !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
+                  !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, tw, p, narrow);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");

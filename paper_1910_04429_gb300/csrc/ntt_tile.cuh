@@ -61,7 +61,6 @@ struct Digits {
     const uint16_t* src;  // little-endian limbs viewed as 16-bit digits
     u64 L;                // live digits: ceil(n / 16), or n with one_bit
     uint16_t top_mask;    // mask of digit L-1 (bits >= n cleared); unused with one_bit
-    uint16_t sysmem;      // 1: src is host memory mapped into the device (read with plain loads)
     uint16_t one_bit;     // 1: every bit is a digit (GF(2) vectors as 0/1 coefficients)
 };
 

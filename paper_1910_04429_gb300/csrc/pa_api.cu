@@ -185,7 +185,7 @@ Geom toeplitz_base(uint64_t n, uint64_t m) { return choose_geom_len(n + m - 1); 
 
 // The key's (and seed's) bits as one-bit digits of the convolution.
 Digits bit_digits(const uint64_t* v, uint64_t bits) {
-    return Digits{reinterpret_cast<const uint16_t*>(v), bits, 0xFFFF, 0, 1};
+    return Digits{reinterpret_cast<const uint16_t*>(v), bits, 0xFFFF, 1};
 }
 
 // Tuning cache file (PA_TUNE_CACHE): lines "<gpu name>\t<N>\t<variant>".
@@ -248,9 +248,8 @@ uint16_t top_digit_mask(uint64_t n) {
 }
 
 // Queue steps 1-5 of Algorithm 1; on success *coef points at the digits (k < L).
-// sysmem: key and seed_a are host memory mapped into the device.
 int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, cudaStream_t st,
-                      Scratch& scr, int dev, u64** coef, bool sysmem = false) {
+                      Scratch& scr, int dev, u64** coef) {
     u64 L = (n + 15) / 16;
     NttJob j;
     j.geom = plan_for(dev, n);
@@ -264,8 +263,8 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
     j.buf_a = (u64*)ba;
     j.ahat = (u64*)ba;  // each tile is read completely before it is overwritten
     uint16_t top = top_digit_mask(n);
-    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top, (uint16_t)sysmem};
-    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top, (uint16_t)sysmem};
+    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top};
+    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top};
     cudaError_t e = launch_convolution(j, st);
     if (e != cudaSuccess) return cuda_fail(e, "NTT launch");
     *coef = j.buf_x;
@@ -301,14 +300,13 @@ int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint
 }
 
 int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
-                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool,
-                bool sysmem = false) {
+                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool) {
     Scratch scr(st, pool);
     u32* state = nullptr;
     int rc = carry_states(n, st, scr, &state);
     if (rc) return rc;
     u64* coef = nullptr;
-    if ((rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef, sysmem))) return rc;
+    if ((rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef))) return rc;
     return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr, state);
 }
 
@@ -408,18 +406,6 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     return PA_OK;
 }
 
-// Device address of pinned (page-locked, mapped) host memory, if p is such memory.
-bool host_mapped(const void* p, void** dptr) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
-        return false;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
-    *dptr = a.devicePointer;
-    return true;
-}
-
 int setup(int* dev, cudaMemPool_t* pool) {
     int rc = current_device(dev);
     if (rc) return rc;
@@ -430,8 +416,7 @@ int setup(int* dev, cudaMemPool_t* pool) {
 // Host buffers in, host buffer out, queued without waiting: x and a are copied
 // on the device's copy stream (two calls at most ahead of the hashes, so the
 // next call's copies overlap this call's transforms), b behind them, the hash
-// runs on st after each copy's event, and a pinned result buffer is written in
-// place by the carry kernel (else copied back on st).
+// runs on st after each copy's event, and the result is copied back on st.
 int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
                     uint64_t m, uint64_t* out, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -464,7 +449,6 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
             return cuda_fail(e, "host-buffer copies");
         }
         void* mo = nullptr;
-        bool out_mapped = host_mapped(out, &mo);
         u32* state = nullptr;
         if ((rc = carry_states(n, st, scr, &state)) || (e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
             cudaStreamWaitEvent(st, d.b_ready, 0);
@@ -474,9 +458,11 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
         rc = queue_convolution((const u64*)dx, (const u64*)da, n, st, scr, dev, &coef);
         if ((e = cudaStreamWaitEvent(st, d.b_ready, 0))) return cuda_fail(e, "cudaStreamWaitEvent");
         if (rc) return rc;
-        if (!out_mapped && (rc = scr.get(out_bytes, &mo))) return rc;
+        // the result goes to device memory and is copied back (writing it into a
+        // mapped pinned buffer from the carry kernel measured slower)
+        if ((rc = scr.get(out_bytes, &mo))) return rc;
         if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr, state))) return rc;
-        if (!out_mapped && (e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
+        if ((e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "cudaMemcpyAsync(D2H)");
     }
     if ((e = cudaEventRecord(done, st))) return cuda_fail(e, "cudaEventRecord");

@@ -37,7 +37,7 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;
     nb.io[0] = BlockIO{j.buf_a, j.buf_a, j.da, j.da, j.L};
-    bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.sysmem && !j.da.one_bit;
+    bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.one_bit;
     const Geom& G = j.geom;
     bool narrow = narrow_plan<1>(G);
     for (int p = 0; p < G.nstrided; p++) {

@@ -220,8 +220,8 @@ def test_hash_host_buffers():
 
 
 @pytest.mark.parametrize("n,m", [(3_000_017, 800_001), (1000, 333), (100_000_000, 25_000_000)])
-def test_hash_host_pinned_zero_copy(n, m):
-    """Pinned host buffers: the kernels read and write host memory directly."""
+def test_hash_host_pinned(n, m):
+    """Pinned host buffers through the synchronous host call, twice each."""
     import ctypes
 
     import torch
