@@ -239,8 +239,9 @@ int pa_prepare(uint64_t n);
  * asynchronous copies; for transforms of at most 64 tiles with one strided
  * pass, single-block tiles of a quarter of the columns, four times the CTAs).
  * Variants are 0 .. 15. pa_autotune times the applicable plans for the
- * transform length that keys of n bits use (reps hashes each, on synthetic
- * data, synchronous; it allocates with cudaMalloc) and keeps the fastest for
+ * transform length that keys of n bits use (the fastest of three runs of reps
+ * hashes each, on synthetic data, synchronous; it allocates with cudaMalloc)
+ * and keeps the fastest for
  * that length on the current device; later calls (single, batched, seeded,
  * served) use it. With the environment variable PA_TUNE_CACHE naming a file,
  * choices are saved there per GPU name and loaded on first use.

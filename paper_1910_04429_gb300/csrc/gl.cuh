@@ -262,6 +262,36 @@ struct RowRoots<R, INV, K, 1> {  // row 0: w^0 = 1
 template <int R>
 GL_HD void dft_fwd(u64* v);
 
+// Forward DFT of length R in {2, 4, 8} whose inputs v[R/2 ..] are zero (the
+// first decimation-in-frequency stage reduces to copies and roots).
+template <int R>
+GL_HD void dft_fwd_upper_zero(u64* v) {
+    if constexpr (R == 2) {
+        v[1] = v[0];
+    } else if constexpr (R == 4) {
+        u64 a = v[0], d = shl_v(v[1], root_shift<4, false>(1));
+        v[2] = sub(a, v[1]);
+        v[0] = add(a, v[1]);
+        v[1] = add(a, d);
+        v[3] = sub(a, d);
+    } else {
+        static_assert(R == 8, "upper-zero DFT of length 2, 4 or 8");
+        u64 s[4], t[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            s[i] = v[i];
+            t[i] = shl_v(v[i], root_shift<8, false>(i));
+        }
+        dft_fwd<4>(s);
+        dft_fwd<4>(t);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[2 * k] = s[k];
+            v[2 * k + 1] = t[k];
+        }
+    }
+}
+
 // In-register DFT of length R in {1, 2, 3, 4, 6, 8}, natural order in and out:
 // v[k] <- sum_j v[j] w^(jk), w = 2^(192/R) (or its inverse), no 1/R scaling.
 // The inverse is the forward DFT read backwards (sum_j v[j] w^(-jk) is the

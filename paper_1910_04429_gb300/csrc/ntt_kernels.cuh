@@ -37,8 +37,9 @@ __device__ __forceinline__ void stage_words(u64* stage, const u64* buf, const St
 // that the digit source is 16-byte aligned.
 template <int R, int C>
 __device__ __forceinline__ void stage_digits(uint16_t* stage, const Digits& dig, const StridedGeom& g,
-                                             const TilePos& tp) {
-    constexpr int CH = R * C / 8;
+                                             const TilePos& tp, bool upper_zero) {
+    // rows >= R/2 are all zero on the first pass of at most N/2 digits: not staged
+    const int CH = (upper_zero ? R / 2 : R) * C / 8;
     for (int ch = threadIdx.x; ch < CH; ch += NT) {
         int d = ch / (C / 8), c = (ch % (C / 8)) * 8;
         u64 pos = tp.base + c + g.S * (u64)d;
@@ -72,7 +73,10 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     if (STAGED) {
 #pragma unroll
         for (int op = 0; op < OPS; op++) {
-            if (PACK) stage_digits<S::R, C>((uint16_t*)st[op], op ? io.da : io.dx, g, tp);
+            if (PACK) {
+                const Digits& dg = op ? io.da : io.dx;
+                stage_digits<S::R, C>((uint16_t*)st[op], dg, g, tp, S::template upper_rows_zero<PACK>(g, dg));
+            }
             else stage_words<S::R, C>(st[op], op ? io.buf_a : io.buf_x, g, tp);
             cp_async_commit();
         }

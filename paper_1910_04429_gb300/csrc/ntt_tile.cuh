@@ -105,17 +105,29 @@ struct Strided {
     }
 
     // forward, step 1: length-RB DFT over j1 of digits j0 + RA*j1, twiddle w_R^(j0 kr)
+    // first pass on digits of at most N/2 live positions: rows j0 + RA j1 with
+    // j1 >= RB/2 lie at or above N/2, so they are zero
+    template <bool PACK>
+    static GL_HD bool upper_rows_zero(const StridedGeom& g, const Digits& dig) {
+        return PACK && (RB == 2 || RB == 4 || RB == 8) && 2 * dig.L <= g.N;
+    }
     template <bool PACK>
     static GL_HD void fwd_a(const StridedGeom& g, const TilePos& tp, int it, const u64* buf,
                             const Digits& dig, u64* sm) {
         int j0 = it / C, c = it % C;
         u64 v[RB];
+        const bool half = upper_rows_zero<PACK>(g, dig);
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {
             u64 p = tp.base + c + g.S * (u64)(j0 + RA * j1);
-            v[j1] = PACK ? digit_at(dig, p) : buf[p];
+            v[j1] = (half && 2 * j1 >= RB) ? 0 : PACK ? digit_at(dig, p) : buf[p];
         }
-        gl::dft<RB, false>(v);
+        if constexpr (PACK && (RB == 2 || RB == 4 || RB == 8)) {
+            if (half) gl::dft_fwd_upper_zero<RB>(v);
+            else gl::dft<RB, false>(v);
+        } else {
+            gl::dft<RB, false>(v);
+        }
         gl::RowRoots<R, false, RB, RA>::apply(v, j0);
 #pragma unroll
         for (int kr = 0; kr < RB; kr++) sm[(kr * RA + j0) * C + c] = v[kr];
@@ -128,10 +140,13 @@ struct Strided {
                                    const uint16_t* st16, const Digits& dig, u64* sm) {
         int j0 = it / C, c = it % C;
         u64 v[RB];
+        const bool half = upper_rows_zero<PACK>(g, dig);  // those rows were not staged
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {
             int d = j0 + RA * j1;
-            if (PACK) {
+            if (half && 2 * j1 >= RB) {
+                v[j1] = 0;
+            } else if (PACK) {
                 uint16_t x = st16[d * C + c];
                 if (tp.base + c + g.S * (u64)d == dig.L - 1) x &= dig.top_mask;
                 v[j1] = x;
@@ -139,7 +154,12 @@ struct Strided {
                 v[j1] = st64[d * C + c];
             }
         }
-        gl::dft<RB, false>(v);
+        if constexpr (PACK && (RB == 2 || RB == 4 || RB == 8)) {
+            if (half) gl::dft_fwd_upper_zero<RB>(v);
+            else gl::dft<RB, false>(v);
+        } else {
+            gl::dft<RB, false>(v);
+        }
         gl::RowRoots<R, false, RB, RA>::apply(v, j0);
 #pragma unroll
         for (int kr = 0; kr < RB; kr++) sm[(kr * RA + j0) * C + c] = v[kr];

@@ -1,0 +1,61 @@
+"""Seeded random sizes against the oracle, bit for bit: key lengths log-uniform
+from 1 bit to 3e6 bits with any output length, each under a random plan
+variant; random Toeplitz sizes; random mixed batches."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_04429_gb300 import binding, inputs
+from tests.gpu_util import dev, gpu_hash, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _sizes(seed, count, n_max):
+    u = inputs.uniforms(seed, 3 * count)
+    out = []
+    for i in range(count):
+        n = max(1, int(math.exp(float(u[3 * i]) * math.log(n_max))))
+        m = 1 + int(float(u[3 * i + 1]) * n) if n > 1 else 1
+        out.append((n, min(m, n), int(float(u[3 * i + 2]) * 16)))
+    return out
+
+
+@pytest.mark.parametrize("chunk", range(4))
+def test_random_sizes_and_plans(chunk):
+    for n, m, variant in _sizes(1000 + chunk, 12, 3_000_000):
+        blk = inputs.make_block(n, m, seed=n ^ (m << 1))
+        binding.plan_override(n, variant)  # masked to what applies at this length
+        try:
+            got = gpu_hash(binding, blk.x, blk.a, blk.b, n, m)
+        finally:
+            binding.plan_override(n, -1)
+        want = oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads())
+        np.testing.assert_array_equal(got, want, err_msg=f"n={n} m={m} variant={variant}")
+
+
+def test_random_toeplitz_sizes():
+    import torch
+
+    for n, m, _ in _sizes(77, 16, 400_000):
+        blk = inputs.make_toeplitz_block(n, m, seed=n + m)
+        got = binding.toeplitz(dev(blk.x), dev(blk.s), n, m)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(got), oracle.toeplitz(blk.x, blk.s, n, m, threads=8),
+                                      err_msg=f"n={n} m={m}")
+
+
+def test_random_batches():
+    import torch
+
+    sizes = [(n, m) for n, m, _ in _sizes(555, 40, 2_000_000)]
+    blks = [inputs.make_block(n, m, seed=7 + i) for i, (n, m) in enumerate(sizes)]
+    tensors = [(dev(b.x), dev(b.a), dev(b.b), b.n, b.m,
+                torch.zeros((b.m + 63) // 64, dtype=torch.int64, device="cuda")) for b in blks]
+    binding.hash_batched(tensors)
+    torch.cuda.synchronize()
+    for b, t in zip(blks, tensors):
+        want = oracle.pa_hash(b.x, b.a, b.b, b.n, b.m, threads=oracle.default_threads())
+        np.testing.assert_array_equal(host(t[5]), want, err_msg=f"n={b.n} m={b.m}")
