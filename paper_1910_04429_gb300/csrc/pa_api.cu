@@ -261,7 +261,6 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
     if ((rc = scr.get(j.geom.N * sizeof(u64), &ba))) return rc;
     j.buf_x = (u64*)bx;
     j.buf_a = (u64*)ba;
-    j.ahat = (u64*)ba;  // each tile is read completely before it is overwritten
     uint16_t top = top_digit_mask(n);
     j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top};
     j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top};
@@ -726,7 +725,7 @@ int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* ou
     u64* spec = nullptr;
     cudaError_t e = cudaMalloc(&spec, j.geom.N * sizeof(u64));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(seed spectrum)");
-    j.buf_x = j.buf_a = j.ahat = spec;
+    j.buf_x = j.buf_a = spec;
     j.da = j.dx = Digits{reinterpret_cast<const uint16_t*>(seed_a), j.L, top_digit_mask(n)};
     if ((e = launch_seed_spectrum(j, (cudaStream_t)stream)) != cudaSuccess) {
         cudaFree(spec);
@@ -758,7 +757,7 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
     void* bx;
     if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
     j.buf_x = (u64*)bx;
-    j.buf_a = j.ahat = seed->spec;
+    j.buf_a = seed->spec;
     j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top_digit_mask(seed->n)};
     j.da = j.dx;
     cudaError_t e = launch_convolution_seeded(j, st);
@@ -785,7 +784,7 @@ int pa_toeplitz(const uint64_t* key, const uint64_t* seed, uint64_t n, uint64_t 
     void *bx, *ba;
     if ((rc = scr.get(j.geom.N * sizeof(u64), &bx)) || (rc = scr.get(j.geom.N * sizeof(u64), &ba))) return rc;
     j.buf_x = (u64*)bx;
-    j.buf_a = j.ahat = (u64*)ba;
+    j.buf_a = (u64*)ba;
     j.dx = bit_digits(key, n);
     j.da = bit_digits(seed, n + m - 1);
     cudaError_t e = launch_convolution(j, st);
@@ -816,7 +815,7 @@ int pa_toeplitz_seed_create(const uint64_t* seed, uint64_t n, uint64_t m, void* 
     u64* spec = nullptr;
     cudaError_t e = cudaMalloc(&spec, j.geom.N * sizeof(u64));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(seed spectrum)");
-    j.buf_x = j.buf_a = j.ahat = spec;
+    j.buf_x = j.buf_a = spec;
     j.da = j.dx = bit_digits(seed, n + m - 1);
     if ((e = launch_seed_spectrum(j, (cudaStream_t)stream)) != cudaSuccess) {
         cudaFree(spec);
@@ -848,7 +847,7 @@ int pa_toeplitz_seeded(pa_seed seed, const uint64_t* key, uint64_t* out, void* s
     void* bx;
     if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
     j.buf_x = (u64*)bx;
-    j.buf_a = j.ahat = seed->spec;
+    j.buf_a = seed->spec;
     j.dx = j.da = bit_digits(key, n);
     cudaError_t e = launch_convolution_seeded(j, st);
     if (e != cudaSuccess) return cuda_fail(e, "seeded Toeplitz NTT launch");

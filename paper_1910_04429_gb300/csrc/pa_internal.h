@@ -14,14 +14,13 @@ struct NttJob {
     Geom geom;
     Twiddles tw;
     u64* buf_x;   // N words: transform of x, then the product digits
-    u64* buf_a;   // N words: transform of a (strided passes)
-    u64* ahat;    // N words: spectrum of a in tile register order, times N^-1
+    u64* buf_a;   // N words: transform of a (with a stored seed: its spectrum in tile
+                  // register order, times N^-1)
     Digits dx, da;
     u64 L;        // live product digits kept by the last inverse pass
 };
 
 // Launches: digits of x and a -> convolution digits c_k (k < L) in buf_x.
-// (ahat must equal buf_a: the seed's spectrum is written over its buffer.)
 cudaError_t launch_convolution(const NttJob& job, cudaStream_t st);
 
 // Seed reuse: a's spectrum alone into buf_a; then x's transform against it.
@@ -46,7 +45,8 @@ cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const Bl
                                      int count, cudaStream_t st);
 
 // Carry resolve, + b, mod 2^n and extraction of bits [n-m, n) (Algorithm 1
-// steps 6-7, Sec. 3.2.2-3.2.5), one decoupled look-back kernel.
+// steps 6-7, Sec. 3.2.2-3.2.5), one kernel over the output tiles (carry-in from
+// a halo, else bounded look-back).
 struct CarryJob {
     const u64* coef;  // convolution digits, coefficient k weighs 2^(16k)
     u64 L;            // digits present (coef[k] = 0 for k >= L)
