@@ -379,6 +379,7 @@ def run_toeplitz(dev, stream, sizes=((100_000_000, 25_000_000, 20), (1_000_000, 
 
     res = {}
     for n, m, steps in sizes:
+        variant = binding.toeplitz_autotune(n, m, reps=3 if n > 10_000_000 else 20)
         blks = [inputs.make_toeplitz_block(n, m, seed=1 + i) for i in range(2)]
         dv = [(torch.from_numpy(b.x.view(np.int64)).to(dev), torch.from_numpy(b.s.view(np.int64)).to(dev))
               for b in blks]
@@ -410,7 +411,7 @@ def run_toeplitz(dev, stream, sizes=((100_000_000, 25_000_000, 20), (1_000_000, 
         ms_seeded = e0.elapsed_time(e1) / steps
         seed.close()
         res[f"n{n:.0e}".replace("+0", "")] = {
-            "n": n, "m": m, "transform": binding.toeplitz_workspace_bytes(n, m) // 16,
+            "n": n, "m": m, "transform": binding.toeplitz_workspace_bytes(n, m) // 16, "plan_variant": variant,
             "value": round(n / ms / 1e3, 1), "ms_per_block": round(ms, 4),
             "seed_reuse_value": round(n / ms_seeded / 1e3, 1), "unit": UNIT}
         del dv, outs

@@ -293,6 +293,9 @@ int pa_toeplitz(const uint64_t* key, const uint64_t* seed, uint64_t n, uint64_t 
 uint64_t pa_toeplitz_workspace_bytes(uint64_t n, uint64_t m);
 int pa_toeplitz_seed_create(const uint64_t* seed, uint64_t n, uint64_t m, void* stream, pa_seed* out);
 int pa_toeplitz_seeded(pa_seed seed, const uint64_t* key, uint64_t* out, void* stream);
+/* pa_toeplitz_autotune: pa_autotune for the transform length pa_toeplitz(n, m) uses
+ * (timed through modular hashes of that length; the kernels are the same). */
+int pa_toeplitz_autotune(uint64_t n, uint64_t m, int reps, int* variant_out);
 
 /* Per-kernel device time, aggregated by kernel name (see pa_profile). */
 typedef struct {

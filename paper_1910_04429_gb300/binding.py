@@ -35,6 +35,8 @@ _SIGS = {
     "pa_toeplitz_seed_create": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "pa_toeplitz_seeded": ([ctypes.c_void_p] * 4, ctypes.c_int),
+    "pa_toeplitz_autotune": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                             ctypes.c_int),
     "pa_bits_to_limbs": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                           ctypes.c_void_p], ctypes.c_int),
     "pa_limbs_to_bits": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -223,6 +225,13 @@ def toeplitz(key, seed, n: int, m: int, out=None, stream=None):
     _check(load().pa_toeplitz(_dev_ptr(key, limbs(n), "key"), _dev_ptr(seed, limbs(n + m - 1), "seed"),
                               n, m, _dev_ptr(out, limbs(m), "out"), _stream_ptr(stream)), "pa_toeplitz")
     return out
+
+
+def toeplitz_autotune(n: int, m: int, reps: int = 5) -> int:
+    """Tune the plan of the transform length pa_toeplitz(n, m) uses; returns the variant."""
+    v = ctypes.c_int(0)
+    _check(load().pa_toeplitz_autotune(n, m, reps, ctypes.byref(v)), "pa_toeplitz_autotune")
+    return int(v.value)
 
 
 def toeplitz_workspace_bytes(n: int, m: int) -> int:

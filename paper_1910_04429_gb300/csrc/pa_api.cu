@@ -954,6 +954,16 @@ int pa_autotune(uint64_t n, int reps, int* variant_out) {
     return PA_OK;
 }
 
+// The plans of a transform length are the same kernels whatever feeds them, so
+// the Toeplitz transform's length is tuned through a modular hash of that length
+// (keys of 16 N / 2 bits: 2 L - 1 = N - 1 digits of product).
+int pa_toeplitz_autotune(uint64_t n, uint64_t m, int reps, int* variant_out) {
+    if (!check_toeplitz(n, m))
+        return fail(PA_EINVAL, "pa_toeplitz_autotune: need 1 <= m <= n, n + m - 1 <= PA_TOEPLITZ_MAX_BITS");
+    uint64_t N = toeplitz_base(n, m).N;
+    return pa_autotune(16 * (N / 2), reps, variant_out);
+}
+
 int pa_prepare(uint64_t n) {
     if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_prepare: need 1 <= n <= PA_MAX_BITS");
     std::lock_guard<std::mutex> lk(g_mu);

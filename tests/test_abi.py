@@ -118,6 +118,7 @@ def test_argument_checks_without_gpu():
     assert lib.pa_toeplitz(p, p, 10, 5, null, null) == binding.PA_EINVAL
     assert lib.pa_toeplitz_seed_create(null, 10, 5, null, ctypes.byref(h)) == binding.PA_EINVAL
     assert lib.pa_toeplitz_seeded(null, p, p, null) == binding.PA_EINVAL
+    assert lib.pa_toeplitz_autotune(10, 11, 1, None) == binding.PA_EINVAL
     # the fixed-scratch entry point refuses keys beyond its scratch size
     assert lib.pa_hash_noalloc(p, p, p, (1 << 20) + 1, 1, p, null) == binding.PA_EINVAL
     assert b"PA_NOALLOC_MAX_BITS" in lib.pa_last_error()

@@ -119,3 +119,14 @@ def test_seed_kinds_not_mixed():
         torch.cuda.synchronize()
         s.close()
         h.close()
+
+
+def test_toeplitz_autotune_keeps_exact():
+    torch = _need_gpu()
+    n, m = 300_000, 120_000
+    v = binding.toeplitz_autotune(n, m, reps=2)
+    assert 0 <= v < 16
+    blk = inputs.make_toeplitz_block(n, m, seed=21)
+    got = binding.toeplitz(dev(blk.x), dev(blk.s), n, m)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(got), oracle.toeplitz(blk.x, blk.s, n, m, threads=8))
