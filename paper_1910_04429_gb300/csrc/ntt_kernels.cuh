@@ -116,10 +116,12 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
 }
 
 // Inverse strided pass over one tile. STAGED: the tile is copied into shared
-// memory asynchronously while the inverse twiddles are computed; otherwise the
+// memory asynchronously while the inverse twiddles are read; otherwise the
 // first phase loads it directly (the autotuner picks per transform length).
+// Three CTAs per SM (40 registers): the extra warps hide the global-load latency
+// this one-operand pass is exposed to.
 template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
-__global__ void __launch_bounds__(NT, 2) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
+__global__ void __launch_bounds__(NT, 3) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     pdl_begin();
     using S = Strided<RA, RB, C>;
