@@ -195,7 +195,7 @@ def alu_ops(name: str, N: int):
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
 # launch at n = 10^8), valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 257.4e6, "src_sha": "8331e38bf4bad120",
+TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 258.0e6, "src_sha": "8cc4085f8a264686",
            "profile": "profiles/k_contig_both_n1e8.md"}
 
 
