@@ -226,9 +226,13 @@ int pa_batch_destroy(pa_batch batch);
 
 /*
  * pa_prepare: build the twiddle tables of the transform that serves keys of
- * n bits on the current device (synchronous). Optional: pa_hash does this
- * lazily. Call it for every key size before capturing a stream into a CUDA
- * graph.
+ * n bits on the current device, for the plan currently in effect for that
+ * length (synchronous; after pa_autotune picks another plan, call it again).
+ * Besides a few small tables per length, every strided pass of a plan keeps
+ * 2 M words of inter-pass twiddles (M its sub-problem size): about 205 MB at
+ * n = 10^8, 2.3 GB at n = 10^9, kept until pa_shutdown. Optional: pa_hash
+ * builds them lazily. Call it for every key size before capturing a stream
+ * into a CUDA graph.
  */
 int pa_prepare(uint64_t n);
 
