@@ -294,6 +294,22 @@ def run_ours(args, rank, world, local):
     ms_total = ev0.elapsed_time(ev1)
     clk = clocks.stop()
 
+    # latency of single plain launches timed alone (events around each hash,
+    # synchronized between hashes), p50 / p99 over 200 launches
+    lat = []
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(200):
+        torch.cuda.synchronize()
+        l0.record(stream)
+        step(i)
+        l1.record(stream)
+        l1.synchronize()
+        lat.append(l0.elapsed_time(l1) * 1e3)
+    lat.sort()
+    latency = {"p50_us": round(lat[len(lat) // 2], 1), "p99_us": round(lat[int(0.99 * len(lat))], 1),
+               "max_us": round(lat[-1], 1), "launches": len(lat),
+               "note": "one hash alone per measurement, CUDA events around it on its stream"}
+
     # per-kernel CUDA events over the same K steps (separate, identical pass)
     kstats = {}
     if not args.no_profile:
@@ -364,7 +380,7 @@ def run_ours(args, rank, world, local):
     small = None if args.no_small else run_small(dev, stream)
     toep = None if args.no_toeplitz else run_toeplitz(dev, stream)
     ms_total, e2e_ms, e2e_sync_ms = max_over_ranks([ms_total, e2e_ms, e2e_sync_ms], world, dev)
-    return dict(ms_total=ms_total, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats, clocks=clk,
+    return dict(ms_total=ms_total, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats, clocks=clk, latency=latency,
                 h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small,
                 toeplitz=toep)
 
@@ -753,6 +769,7 @@ def main():
                     "api": "pa_hash_host_async back to back on pinned buffers, host clock to the final sync",
                     "sync_value": round(aggregate_mbps(world, 1, n, res["e2e_sync_ms"]), 1)},
             "gpu_launches": launches,
+            "latency": res["latency"],
             "seed_reuse": None if res["seeded_ms"] is None else {
                 "value": round(aggregate_mbps(world, 1, n, res["seeded_ms"]), 1), "unit": UNIT,
                 "note": "same workload, multiplier's transform computed once (pa_hash_seeded)"},
