@@ -2,7 +2,7 @@
 // (Sec. 2.2: each reconciled block X is compressed to Y = g(X)), are admitted
 // while their device footprint fits a budget, and run as continuously formed
 // batches that overlap on several device streams. Host-side only; the hashing
-// itself is pa_hash_batched.
+// itself is pa_hash_batched (pa_hash for a batch of one).
 //
 // Worker thread:
 //   1. completed batches (signalled by a host callback queued after each
@@ -143,7 +143,11 @@ void worker_main() {
                 for (const Request& r : b->reqs) blocks.push_back(r.blk);
                 cudaStream_t st = g_srv.streams[slot];
                 lk.unlock();  // queueing takes the library lock; do not hold ours
-                int rc = pa_hash_batched(blocks.data(), (uint32_t)blocks.size(), st);
+                // a lone request takes the single-block path (no side-stream fork)
+                const pa_block& b0 = blocks[0];
+                int rc = blocks.size() == 1
+                             ? pa_hash(b0.key, b0.seed_a, b0.seed_b, b0.n, b0.m, b0.out, st)
+                             : pa_hash_batched(blocks.data(), (uint32_t)blocks.size(), st);
                 cudaError_t e = rc == PA_OK ? cudaLaunchHostFunc(st, batch_done, b) : cudaSuccess;
                 lk.lock();
                 if (rc != PA_OK || e != cudaSuccess) finish_batch(b, rc != PA_OK ? rc : PA_ECUDA);
