@@ -202,7 +202,8 @@ TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 258.0e6, "src_sha": "39aedf4868
 # The sources that define the hash's kernels and their launch sequence (the
 # profiled code); host-only files (API, serving, adapters) are not part of it.
 KERNEL_SOURCES = ["gl.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "cp_async.cuh", "pdl.cuh", "plan.h",
-                  "pa_internal.h", "pa_ntt.cu", "pa_ntt_batch.cu", "pa_carry.cu"]
+                  "pa_internal.h", "carry.cuh", "pa_ntt.cu", "pa_ntt_batch.cu", "pa_carry.cu",
+                  "pa_fallback.cu"]
 
 
 def kernel_src_sha() -> str:
@@ -233,19 +234,6 @@ def kernel_bytes(name: str, n: int, m: int, N: int) -> float:
         "ntt_inv_strided_last": N * w + L * w,                # only digits k < L written
         "carry_lookback": L * w + Ly * w + Mo * w,
     }.get(name, 0.0)
-
-
-def transform_length(n: int) -> int:
-    """The transform length the library picks: smallest 2^k or 3 * 2^k (first
-    radix <= 48) covering 2 ceil(n/16) - 1 words, at least 4096."""
-    need = 2 * ((n + 15) // 16) - 1
-    k = 12
-    while (1 << k) < need:
-        k += 1
-    for j in range(12, k):
-        if need <= (3 << j) < (1 << k) and (j - 12) % 6 <= 4:
-            return 3 << j
-    return 1 << k
 
 
 def run_ours(args, rank, world, local):
@@ -282,6 +270,7 @@ def run_ours(args, rank, world, local):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
+    binding.wrap_flags(clear=True)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -296,6 +285,7 @@ def run_ours(args, rank, world, local):
     barrier()
     ms_total = ev0.elapsed_time(ev1)
     clk = clocks.stop()
+    flags = binding.wrap_flags()  # failed certificates in the timed steps (each ran the full product)
 
     # latency of single plain launches timed alone (events around each hash,
     # synchronized between hashes), p50 / p99 over 200 launches
@@ -385,7 +375,7 @@ def run_ours(args, rank, world, local):
     ms_total, e2e_ms, e2e_sync_ms = max_over_ranks([ms_total, e2e_ms, e2e_sync_ms], world, dev)
     return dict(ms_total=ms_total, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats, clocks=clk, latency=latency,
                 h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small,
-                toeplitz=toep)
+                toeplitz=toep, flags=flags, plan=binding.plan_info(n, m))
 
 
 def run_toeplitz(dev, stream, sizes=((100_000_000, 25_000_000, 20), (1_000_000, 250_000, 200))):
@@ -723,7 +713,8 @@ def main():
     value = aggregate_mbps(world, K, n, res["ms_total"])
     e2e_value = aggregate_mbps(world, 1, n, res["e2e_ms"])
 
-    N = transform_length(n)
+    plan = res["plan"]
+    N = plan["first"]  # the transform the timed hashes run (wrapped where shorter)
     roofline = None
     launches = None
     if res["kstats"]:
@@ -763,6 +754,10 @@ def main():
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"G_cd hash, one key of n={n} bits, m={m} output bits per step",
                        "transform": f"Goldilocks NTT length {N}", "seeds": f"{ROTATE} rotating blocks",
+                       "product": ({"kind": "wrapped (cyclic) product, certified by the carry step",
+                                    "length": N, "full_length": plan["full"], "dropped_coefficients":
+                                    plan["dropped"], "full_product_runs_in_timed_steps": res["flags"]}
+                                   if plan["dropped"] else {"kind": "full-length product", "length": N}),
                        "plan_variant": res["variant"],
                        "l2": f"inputs rotate over {ROTATE} blocks ({ROTATE * 3 * ((n + 63) // 64) * 8 / 1e6:.0f}"
                              f" MB) plus {2 * N * 8 / 1e6:.0f} MB workspace per step, > 129 MB L2",

@@ -69,6 +69,18 @@ extern "C" {
  * seed_a need not be odd: the formula is evaluated for any value (the family
  * of Eq. 6 draws odd c; that is the caller's choice of seed).
  * Returns PA_OK once all kernels are queued (asynchronous).
+ *
+ * Only bits [n-m, n) of the product mod 2^n reach the output, so where it is
+ * shorter the product runs as a cyclic convolution of length N < 2L - 1
+ * (L = ceil(n/16) digits) whose wrapped-around part lands on the lowest
+ * coefficients; those are dropped. The carry step then checks the limb of the
+ * exact remaining sum just below bit n - m: unless all 64 of its bits are one,
+ * the dropped part cannot reach the output and the result is exact. If they
+ * are all one, an exact recomputation queued behind (one launch that returns
+ * at once otherwise) computes the full product at a power-of-two length and
+ * overwrites the output. With uniform seed_b this happens with probability
+ * 2^-64 per hash; results are identical either way (see pa_plan_info,
+ * pa_wrap_mode).
  */
 int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
             uint64_t m, uint64_t* out, void* stream);
@@ -228,11 +240,13 @@ int pa_batch_destroy(pa_batch batch);
  * pa_prepare: build the twiddle tables of the transform that serves keys of
  * n bits on the current device, for the plan currently in effect for that
  * length (synchronous; after pa_autotune picks another plan, call it again).
- * Besides a few small tables per length, every strided pass of a plan keeps
- * 2 M words of inter-pass twiddles (M its sub-problem size): about 205 MB at
- * n = 10^8, 2.3 GB at n = 10^9, kept until pa_shutdown. Optional: pa_hash
- * builds them lazily. Call it for every key size before capturing a stream
- * into a CUDA graph.
+ * It also builds those of every shorter length a wrapped product of n bits
+ * may run (which depends on m; see pa_plan_info). Besides a few small tables
+ * per length, every strided pass of a plan keeps 2 M words of inter-pass
+ * twiddles (M its sub-problem size): about 205 MB for the full length at
+ * n = 10^8 (and about 140 MB for its wrapped length), 2.3 GB at n = 10^9, kept until
+ * pa_shutdown. Optional: pa_hash builds them lazily. Call it for every key
+ * size before capturing a stream into a CUDA graph.
  */
 int pa_prepare(uint64_t n);
 
@@ -259,8 +273,31 @@ int pa_prepare(uint64_t n);
 int pa_autotune(uint64_t n, int reps, int* variant_out);
 int pa_plan_override(uint64_t n, int variant);
 
-/* pa_workspace_bytes: device workspace one pa_hash of n bits draws from the pool. */
+/* pa_workspace_bytes: device workspace one pa_hash of n bits draws from the pool
+ * (two buffers of the recomputation's power-of-two length, which also hold the
+ * wrapped and the full-length product, and the carry states). */
 uint64_t pa_workspace_bytes(uint64_t n);
+
+/*
+ * Wrapped products (see pa_hash).
+ * pa_plan_info: host only, needs no device. For keys of n bits and m output
+ *   bits: info[0] = the length of the transform the hash runs first, info[1] =
+ *   the full-length product's (N >= 2L - 1, used when not wrapped), info[2] =
+ *   how many low coefficients the wrapped product drops (0: not wrapped,
+ *   info[0] == info[1]).
+ *   PA_EINVAL for sizes pa_hash rejects.
+ * pa_wrap_mode: 1 (default) wrapped products where shorter; 0 always the
+ *   full-length product; 2 wrapped with the check forced to fail, so every hash
+ *   also runs the recomputation (tests of that path). Returns the
+ *   previous mode, or PA_EINVAL. Applies to later pa_hash / pa_hash_host calls
+ *   on every thread.
+ * pa_wrap_flags: waits for the device, then stores in *count how many checks
+ *   have failed (each ran the recomputation) since the counter was last
+ *   cleared; clear != 0 clears it.
+ */
+int pa_plan_info(uint64_t n, uint64_t m, uint64_t info[3]);
+int pa_wrap_mode(int mode);
+int pa_wrap_flags(uint64_t* count, int clear);
 
 /*
  * Toeplitz-hash privacy amplification on the same NTT engine: the hash family

@@ -57,6 +57,9 @@ _SIGS = {
     "pa_hash_batched": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p], ctypes.c_int),
     "pa_prepare": ([ctypes.c_uint64], ctypes.c_int),
     "pa_workspace_bytes": ([ctypes.c_uint64], ctypes.c_uint64),
+    "pa_plan_info": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "pa_wrap_mode": ([ctypes.c_int], ctypes.c_int),
+    "pa_wrap_flags": ([ctypes.POINTER(ctypes.c_uint64), ctypes.c_int], ctypes.c_int),
     "pa_shutdown": ([], ctypes.c_int),
     "pa_profile": ([ctypes.c_int], ctypes.c_int),
     "pa_init": ([ctypes.c_void_p], ctypes.c_int),
@@ -449,6 +452,31 @@ def prepare(n: int):
 
 def workspace_bytes(n: int) -> int:
     return int(load().pa_workspace_bytes(n))
+
+
+def plan_info(n: int, m: int) -> dict:
+    """Transform lengths of a hash of n bits with m output bits (host only):
+    {"first": length run first, "full": the full-length product's, "dropped":
+    low coefficients the wrapped product drops (0: not wrapped)}."""
+    info = (ctypes.c_uint64 * 3)()
+    _check(load().pa_plan_info(n, m, info), "pa_plan_info")
+    return {"first": int(info[0]), "full": int(info[1]), "dropped": int(info[2])}
+
+
+def wrap_mode(mode: int) -> int:
+    """1: wrapped products where shorter (default); 0: always full length;
+    2: wrapped with the check forced to fail (tests). Returns the previous mode."""
+    rc = load().pa_wrap_mode(mode)
+    if rc < 0:
+        _check(rc, "pa_wrap_mode")
+    return int(rc)
+
+
+def wrap_flags(clear: bool = False) -> int:
+    """Failed wrapped-product checks (each ran the full-length product) since the last clear."""
+    v = ctypes.c_uint64(0)
+    _check(load().pa_wrap_flags(ctypes.byref(v), 1 if clear else 0), "pa_wrap_flags")
+    return int(v.value)
 
 
 def profile(on: bool):

@@ -79,7 +79,8 @@ int get_pool(int dev, cudaMemPool_t* out) {
     return PA_OK;
 }
 
-int get_tables(int dev, const Geom& G, Twiddles* tw) {
+// The tables every plan of length G.N shares (no per-pass tables).
+int get_base_tables(int dev, const Geom& G, Twiddles* tw) {
     Device& d = g_dev[dev];
     auto it = d.tables.find(G.N);
     u64* p = nullptr;
@@ -108,6 +109,13 @@ int get_tables(int dev, const Geom& G, Twiddles* tw) {
     tw->whi = p + 16384;
     tw->whii = p + 16384 + nh;
     tw->w4096s = p + base_words;
+    return PA_OK;
+}
+
+int get_tables(int dev, const Geom& G, Twiddles* tw) {
+    int rc = get_base_tables(dev, G, tw);
+    if (rc) return rc;
+    Device& d = g_dev[dev];
     // per strided pass: full tables of its inter-pass twiddles (2 M words),
     // built once on the device and waited for
     for (int i = 0; i < G.nstrided && i < MAX_PASSES; i++) {
@@ -298,15 +306,116 @@ int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint
     return PA_OK;
 }
 
+// Wrapped products: 1 where one is shorter than the full-length product
+// (default), 0 never, 2 always with the flag forced (every hash then also runs
+// the exact recomputation: a test of that path).
+int g_wrap_mode = 1;
+
+WrapPlan wrap_for(uint64_t n, uint64_t m) { return g_wrap_mode ? wrap_plan(n, m) : WrapPlan{}; }
+
+// One hash's plans and scratch. Without wrapping: the full-length product.
+// With it: the wrapped product, then its carry step (which sets the flag when
+// the certificate fails), then the exact recomputation (one launch that does
+// nothing unless the flag is set); the buffers are sized for the
+// recomputation's power-of-two length, which the wrapped product's prefix of
+// them precedes.
+struct HashPlan {
+    WrapPlan wp;
+    NttJob prod;      // the product that runs first
+    FallbackJob fb;   // with wp.on: the recomputation
+    u32* state;       // carry states: one set, or two (wrapped, recomputation)
+};
+
+NttJob product_job(const Geom& G, u64* bx, u64* ba, const uint64_t* key, const uint64_t* seed_a, uint64_t n) {
+    NttJob j;
+    j.geom = G;
+    j.L = (n + 15) / 16;
+    j.buf_x = bx;
+    j.buf_a = ba;
+    uint16_t top = top_digit_mask(n);
+    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top};
+    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), j.L, top};
+    return j;
+}
+
+// The recomputation's power-of-two length (>= 2L - 1, at least one tile).
+Geom fallback_geom(uint64_t n) { return make_geom(logn_for_digits((n + 15) / 16)); }
+
+// Words of each transform buffer a hash of n bits may need, whatever m is.
+u64 buffer_words(uint64_t n) {
+    u64 full = geom_for_bits(n).N, fb = fallback_geom(n).N;
+    return full > fb ? full : fb;
+}
+
+// Plans, twiddle tables, buffers and the zeroed carry states (queued on st
+// now, before any transform).
+int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, cudaStream_t st,
+                 Scratch& scr, int dev, HashPlan* hp) {
+    hp->wp = wrap_for(n, m);
+    const Geom first = hp->wp.on ? plan_for_base(dev, hp->wp.geom) : plan_for(dev, n);
+    const Geom fg = fallback_geom(n);
+    const u64 words = hp->wp.on ? (fg.N > first.N ? fg.N : first.N) : first.N;
+    int rc;
+    void *bx, *ba, *sp;
+    if ((rc = scr.get(words * sizeof(u64), &bx)) || (rc = scr.get(words * sizeof(u64), &ba))) return rc;
+    hp->prod = product_job(first, (u64*)bx, (u64*)ba, key, seed_a, n);
+    if ((rc = get_tables(dev, first, &hp->prod.tw))) return rc;
+    const size_t state_words = (hp->wp.on ? 2 : 1) * carry_state_words(n);
+    if ((rc = scr.get(state_words * sizeof(u32), &sp))) return rc;
+    hp->state = (u32*)sp;
+    if (hp->wp.on) {
+        Twiddles t;
+        if ((rc = get_base_tables(dev, fg, &t))) return rc;
+        FallbackJob& f = hp->fb;
+        f.dx = hp->prod.dx;
+        f.da = hp->prod.da;
+        f.n = n;
+        f.m = m;
+        f.flag = hp->state + carry_flag_word(n);
+        f.X = (u64*)bx;
+        f.A = (u64*)ba;
+        f.logN = fg.logN;
+        f.wlo = t.wlo;
+        f.wloi = t.wloi;
+        f.whi = t.whi;
+        f.whii = t.whii;
+        f.ninv = n_inverse(fg.logN, 0);
+        f.state = hp->state + carry_state_words(n);
+    }
+    cudaError_t e = cudaMemsetAsync(sp, 0, state_words * sizeof(u32), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
+    return PA_OK;
+}
+
+// Steps 1-5 of Algorithm 1: the wrapped product, else the full-length one.
+int hash_product(HashPlan& hp, cudaStream_t st) {
+    cudaError_t e = launch_convolution(hp.prod, st);
+    return e == cudaSuccess ? PA_OK : cuda_fail(e, "NTT launch");
+}
+
+// Steps 6-7: the carry step; after a wrapped product, the recomputation.
+int hash_finish(HashPlan& hp, const uint64_t* seed_b, uint64_t n, uint64_t m, uint64_t* out, cudaStream_t st) {
+    const u64 L = (n + 15) / 16;
+    u32* flag = hp.wp.on ? hp.state + carry_flag_word(n) : nullptr;
+    CarryJob c{hp.prod.buf_x, L, seed_b, n, m, out, hp.state, true, hp.wp.lo, flag, g_wrap_mode == 2};
+    cudaError_t e = launch_carry(c, st);
+    if (e != cudaSuccess) return cuda_fail(e, "carry launch");
+    if (hp.wp.on) {
+        hp.fb.b = seed_b;
+        hp.fb.out = out;
+        if ((e = launch_fallback(&hp.fb, 1, st)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
+    }
+    return PA_OK;
+}
+
 int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
                 uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool) {
     Scratch scr(st, pool);
-    u32* state = nullptr;
-    int rc = carry_states(n, st, scr, &state);
-    if (rc) return rc;
-    u64* coef = nullptr;
-    if ((rc = queue_convolution(key, seed_a, n, st, scr, dev, &coef))) return rc;
-    return queue_carry(coef, (n + 15) / 16, seed_b, n, m, out, st, scr, state);
+    HashPlan hp;
+    int rc = hash_prepare(key, seed_a, n, m, st, scr, dev, &hp);
+    if (!rc) rc = hash_product(hp, st);
+    if (!rc) rc = hash_finish(hp, seed_b, n, m, out, st);
+    return rc;
 }
 
 int side_streams(int dev) {
@@ -448,19 +557,19 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
             return cuda_fail(e, "host-buffer copies");
         }
         void* mo = nullptr;
-        u32* state = nullptr;
-        if ((rc = carry_states(n, st, scr, &state)) || (e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
+        HashPlan hp;
+        rc = hash_prepare((const u64*)dx, (const u64*)da, n, m, st, scr, dev, &hp);
+        if (rc || (e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
             cudaStreamWaitEvent(st, d.b_ready, 0);
             return rc ? rc : cuda_fail(e, "cudaStreamWaitEvent");
         }
-        u64* coef = nullptr;
-        rc = queue_convolution((const u64*)dx, (const u64*)da, n, st, scr, dev, &coef);
+        rc = hash_product(hp, st);
         if ((e = cudaStreamWaitEvent(st, d.b_ready, 0))) return cuda_fail(e, "cudaStreamWaitEvent");
         if (rc) return rc;
         // the result goes to device memory and is copied back (writing it into a
         // mapped pinned buffer from the carry kernel measured slower)
         if ((rc = scr.get(out_bytes, &mo))) return rc;
-        if ((rc = queue_carry(coef, (n + 15) / 16, (const u64*)db, n, m, (u64*)mo, st, scr, state))) return rc;
+        if ((rc = hash_finish(hp, (const u64*)db, n, m, (u64*)mo, st))) return rc;
         if ((e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "cudaMemcpyAsync(D2H)");
     }
@@ -469,6 +578,49 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
     return PA_OK;
 }
 
+
+// Times every applicable plan variant of transform length base.N through
+// hashes of n bits (m output bits) on st and records the fastest in the tuned
+// table: the fastest of three timed runs of reps hashes each (short hashes
+// time noisily). *err receives a CUDA error, the return value a library one.
+int tune_length(int dev, cudaMemPool_t pool, const Geom& base, uint64_t n, uint64_t m, int reps,
+                cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, const u64* x, const u64* a, const u64* b,
+                u64* out, int* best_out, cudaError_t* err) {
+    Device& d = g_dev[dev];
+    const int mask = applicable_variants(base);
+    const bool had_force = d.forced.count(base.N) != 0;
+    const int old_force = had_force ? d.forced[base.N] : 0;
+    int best = 0, rc = PA_OK;
+    float best_ms = 0;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; e == cudaSuccess && rc == PA_OK && v < PLAN_VARIANTS; v++) {
+        if (v & ~mask) continue;
+        d.forced[base.N] = v;
+        for (int i = 0; i < 2 && rc == PA_OK; i++) rc = hash_device(x, a, b, n, m, out, st, dev, pool);
+        float ms = 0;
+        for (int trial = 0; trial < 3 && e == cudaSuccess && rc == PA_OK; trial++) {
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+            for (int i = 0; i < reps && rc == PA_OK; i++) rc = hash_device(x, a, b, n, m, out, st, dev, pool);
+            if (rc) break;
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess)
+                break;
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (trial == 0 || t < ms) ms = t;
+        }
+        if (rc || e != cudaSuccess) break;
+        if (v == 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    if (had_force) d.forced[base.N] = old_force;
+    else d.forced.erase(base.N);
+    if (rc == PA_OK && e == cudaSuccess) d.tuned[base.N] = best;
+    *best_out = best;
+    *err = e;
+    return rc;
+}
 
 }  // namespace
 
@@ -889,17 +1041,12 @@ int pa_autotune(uint64_t n, int reps, int* variant_out) {
     cudaMemPool_t pool;
     int rc = setup(&dev, &pool);
     if (rc) return rc;
-    Device& d = g_dev[dev];
-    Geom base = geom_for_bits(n);
-    int mask = applicable_variants(base);
     u64 m = n / 4 ? n / 4 : 1;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best = 0;
-    float best_ms = 0;
     void *x = nullptr, *a = nullptr, *b = nullptr, *out = nullptr;
     size_t in_bytes = ((n + 63) / 64) * 8, out_bytes = ((m + 63) / 64) * 8;
     if (e == cudaSuccess) e = cudaMalloc(&x, in_bytes);
@@ -909,35 +1056,20 @@ int pa_autotune(uint64_t n, int reps, int* variant_out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0x5A, in_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a, 0xC3, in_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b, 0x3C, in_bytes, st);
-    bool had_force = d.forced.count(base.N) != 0;
-    int old_force = had_force ? d.forced[base.N] : 0;
-    for (int v = 0; e == cudaSuccess && rc == PA_OK && v < PLAN_VARIANTS; v++) {
-        if (v & ~mask) continue;
-        d.forced[base.N] = v;
-        for (int i = 0; i < 2 && rc == PA_OK; i++)
-            rc = hash_device((const u64*)x, (const u64*)a, (const u64*)b, n, m, (u64*)out, st, dev, pool);
-        if (rc) break;
-        // the fastest of three timed runs of reps hashes (short hashes time noisily)
-        float ms = 0;
-        for (int trial = 0; trial < 3 && e == cudaSuccess && rc == PA_OK; trial++) {
-            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-            for (int i = 0; i < reps && rc == PA_OK; i++)
-                rc = hash_device((const u64*)x, (const u64*)a, (const u64*)b, n, m, (u64*)out, st, dev, pool);
-            if (rc) break;
-            if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess)
-                break;
-            float t = 0;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (trial == 0 || t < ms) ms = t;
-        }
-        if (rc || e != cudaSuccess) break;
-        if (v == 0 || ms < best_ms) {
-            best = v;
-            best_ms = ms;
-        }
+    // The lengths a hash of n bits (m = n / 4) runs: the full-length product's,
+    // timed with wrapping off, and the wrapped product's when there is one.
+    WrapPlan wp = wrap_plan(n, m);
+    const Geom lens[2] = {geom_for_bits(n), wp.geom};
+    const int saved_mode = g_wrap_mode;
+    int best_full = 0;
+    for (int li = 0; li < (wp.on ? 2 : 1) && e == cudaSuccess && rc == PA_OK; li++) {
+        g_wrap_mode = li;
+        int best = 0;
+        rc = tune_length(dev, pool, lens[li], n, m, reps, st, e0, e1, (const u64*)x, (const u64*)a,
+                         (const u64*)b, (u64*)out, &best, &e);
+        if (li == 0) best_full = best;
     }
-    if (had_force) d.forced[base.N] = old_force;
-    else d.forced.erase(base.N);
+    g_wrap_mode = saved_mode;
     if (st) cudaStreamSynchronize(st);
     cudaFree(x);
     cudaFree(a);
@@ -948,9 +1080,8 @@ int pa_autotune(uint64_t n, int reps, int* variant_out) {
     if (st) cudaStreamDestroy(st);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "pa_autotune");
-    d.tuned[base.N] = best;
     save_tune_cache(dev);
-    if (variant_out) *variant_out = best;
+    if (variant_out) *variant_out = best_full;
     return PA_OK;
 }
 
@@ -972,13 +1103,46 @@ int pa_prepare(uint64_t n) {
     int rc = setup(&dev, &pool);
     if (rc) return rc;
     Twiddles tw;
-    return get_tables(dev, plan_for(dev, n), &tw);
+    if ((rc = get_tables(dev, plan_for(dev, n), &tw))) return rc;
+    // the recomputation's length, and every shorter length a wrapped product of n bits may run
+    if ((rc = get_base_tables(dev, fallback_geom(n), &tw))) return rc;
+    const u64 L = (n + 15) / 16, full = geom_for_bits(n).N;
+    for (Geom g = choose_geom_len(L); g.N < full; g = choose_geom_len(g.N + 1))
+        if ((rc = get_tables(dev, plan_for_base(dev, g), &tw))) return rc;
+    return PA_OK;
 }
 
 uint64_t pa_workspace_bytes(uint64_t n) {
     if (n < 1 || n > PA_MAX_BITS) return 0;
-    uint64_t N = geom_for_bits(n).N;
-    return 2 * N * sizeof(u64) + carry_state_words(n) * sizeof(u32);
+    return 2 * buffer_words(n) * sizeof(u64) + 2 * carry_state_words(n) * sizeof(u32);
+}
+
+int pa_plan_info(uint64_t n, uint64_t m, uint64_t info[3]) {
+    if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_plan_info: need 1 <= m <= n <= PA_MAX_BITS");
+    if (!info) return fail(PA_EINVAL, "pa_plan_info: null pointer");
+    WrapPlan wp = wrap_plan(n, m);
+    info[1] = geom_for_bits(n).N;
+    info[0] = wp.on ? wp.geom.N : info[1];
+    info[2] = wp.on ? wp.lo : 0;
+    return PA_OK;
+}
+
+int pa_wrap_mode(int mode) {
+    if (mode < 0 || mode > 2) return fail(PA_EINVAL, "pa_wrap_mode: mode must be 0, 1 or 2");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int prev = g_wrap_mode;
+    g_wrap_mode = mode;
+    return prev;
+}
+
+int pa_wrap_flags(uint64_t* count, int clear) {
+    if (!count) return fail(PA_EINVAL, "pa_wrap_flags: null pointer");
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned long long c = 0;
+    if (e == cudaSuccess) e = read_flag_count(&c, clear != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pa_wrap_flags");
+    *count = c;
+    return PA_OK;
 }
 
 int pa_shutdown(void) {
@@ -1015,7 +1179,10 @@ int pa_device_status(int clear) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     u32 st = 0;
     if ((e = read_device_status(&st, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
+    u32 fst = 0;
+    if ((e = read_fallback_status(&fst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
     if (st & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (carry look-back)");
+    if (fst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (recomputation barrier)");
     return PA_OK;
 }
 

@@ -1,16 +1,8 @@
 // Carry resolve, addition of d, reduction mod 2^n and extraction of the top m
 // bits (Algorithm 1 steps 6-7 "combine" and "carry", the y = cx + d of
 // Sec. 3.2.2, Sec. 3.2.3 mod 2^n, Sec. 3.2.4-3.2.5 export of the r most
-// significant bits; Eq. 7).
-//
-// With c_k < 2^64 the convolution digits and b the addend, define per 64-bit
-// limb j
-//   V_j = sum_{i<4} c_{4j+i} 2^(16 i) + b_j            (< 2^115)
-//   E_j = lo64(V_j) + hi64(V_{j-1}) = e_j + f_j 2^64   (f_j in {0, 1})
-//   u_j = e_j + f_{j-1}                                (in [0, 2^64])
-// so that y = sum_j u_j 2^(64 j) exactly. What remains is a one-bit carry
-// chain: carry_{j+1} = [u_j + carry_j >= 2^64], whose generate / propagate
-// pairs (g_j = [u_j = 2^64], p_j = [u_j = 2^64 - 1]) compose associatively.
+// significant bits; Eq. 7). The per-limb sums u_j and their carry chain of
+// generate / propagate pairs are defined in carry.cuh.
 //
 // One kernel over the tiles of 1024 limbs that hold output limbs (from limb
 // (n - m) / 64 up; the limbs below matter only through the carry into the
@@ -28,145 +20,19 @@
 // and writes its output bits. Every wait on another tile is bounded: when the
 // limit runs out the kernel records PA_STATUS_TIMEOUT in the device status word
 // and carries on with a carry-in of 0, so it always terminates.
-#include "cp_async.cuh"
-#include "pa_internal.h"
+//
+// Wrapped products: the coefficients below job.lo read as zero, and the kernel
+// also resolves limb q - 1 (q = floor((n - m)/64), the limb just below the
+// output) and sets job.flag when it is all ones: only then can the dropped
+// coefficients change the output, and the exact recomputation queued behind
+// this launch (pa_fallback.cu) runs.
+#include "carry.cuh"
 #include "pdl.cuh"
 
 namespace pa {
 
 __device__ u32 g_status;  // sticky device status (PA_STATUS_* bits), read by pa_device_status
-
-// (G, P) packed in two bits: bit 0 generate, bit 1 propagate.
-__device__ __forceinline__ int compose(int earlier, int later) {
-    int G = (later & 1) | ((later >> 1) & earlier & 1);
-    int P = (later >> 1) & (earlier >> 1) & 1;
-    return G | (P << 1);
-}
-constexpr int GP_IDENTITY = 2;
-
-// tile state word: 0 = nothing yet, (1 << 2 | gp) = aggregate of the tile,
-// (2 << 2 | gp) = inclusive prefix from tile 0 through the tile
-constexpr u32 ST_AGG = 1u << 2, ST_INC = 2u << 2;
-
-constexpr int HALO_LO = 4, HALO_HI = 1;                       // extra limbs before / after a tile
-constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 1024
-constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 1029
-constexpr int SM_COEF = 4 * SM_LIMBS;                         // 4116
-constexpr int SM_LIMBS_PAD = SM_LIMBS + 1;                    // whole 16-byte chunks
-
-struct Limb {
-    u64 lo;   // u_j mod 2^64
-    int gp;   // (g_j, p_j)
-};
-
-// V of the limb at shared-memory position l (limb J0 + l)
-__device__ __forceinline__ void limb_v(const u64* cs, const u64* bs, int l, u64* vlo, u64* vhi) {
-    u64 lo = 0, hi = 0;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        u64 ck = cs[4 * l + i];
-        u64 plo = i ? (ck << (16 * i)) : ck;
-        u64 phi = i ? (ck >> (64 - 16 * i)) : 0;
-        lo += plo;
-        hi += phi + (lo < plo);
-    }
-    u64 bj = bs[l];
-    lo += bj;
-    hi += (lo < bj);
-    *vlo = lo;
-    *vhi = hi;
-}
-
-// u of CNT limbs starting at shared position l0 (needs V at l0-2 .. l0+CNT-1)
-template <int CNT>
-__device__ __forceinline__ void limbs_u(const u64* cs, const u64* bs, int l0, Limb* u) {
-    u64 vlo[CNT + 2], vhi[CNT + 2];
-#pragma unroll
-    for (int i = 0; i < CNT + 2; i++) limb_v(cs, bs, l0 - 2 + i, &vlo[i], &vhi[i]);
-    u64 e[CNT + 1];
-    int f[CNT + 1];
-#pragma unroll
-    for (int i = 0; i < CNT + 1; i++) {
-        e[i] = vlo[i + 1] + vhi[i];
-        f[i] = e[i] < vhi[i];
-    }
-#pragma unroll
-    for (int i = 0; i < CNT; i++) {
-        u64 lo = e[i + 1] + (u64)f[i];
-        bool wrap = f[i] && lo == 0;  // u_j = 2^64
-        u[i].lo = lo;
-        u[i].gp = wrap ? 1 : ((lo == ~0ull) ? 2 : 0);
-    }
-}
-
-// Block-wide exclusive scan of (G, P) in thread order; returns the prefix of
-// all earlier threads and writes the block total to *total.
-__device__ __forceinline__ int block_exclusive(int v, int* total) {
-    __shared__ int warp_tot[CARRY_THREADS / 32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int inc = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        int o = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc = compose(o, inc);
-    }
-    int exc = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) exc = GP_IDENTITY;
-    if (lane == 31) warp_tot[warp] = inc;
-    __syncthreads();
-    int wpre = GP_IDENTITY, tot = GP_IDENTITY;
-    for (int w = 0; w < CARRY_THREADS / 32; w++) {
-        if (w == warp) wpre = tot;
-        tot = compose(tot, warp_tot[w]);
-    }
-    *total = tot;
-    return compose(wpre, exc);
-}
-
-// tile states: release store / acquire load at GPU scope
-__device__ __forceinline__ void publish(u32* p, u32 v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ u32 observe(const u32* p) {
-    u32 v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Words [w0, w0 + 2 * chunks) of src (count words live) into dst with 16-byte
-// copies; words outside [0, count) read as zero. Needs src 16-byte aligned and
-// w0 even.
-__device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long w0, int chunks, u64 count) {
-    for (int ch = threadIdx.x; ch < chunks; ch += CARRY_THREADS) {
-        long long k = w0 + 2 * ch;
-        int live = (k < 0 || (u64)k >= count) ? 0 : ((u64)k + 1 < count ? 2 : 1);
-        cp_async16(dst + 2 * ch, live ? src + k : src, 8 * live);
-    }
-}
-
-// VEC: coef and b are 16-byte aligned (staged with cp.async), else plain loads.
-// Digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS) of tile tt
-// (J0 = 1024 tt - 4) into cs / bs; positions outside the operands read 0.
-template <bool VEC>
-__device__ __forceinline__ void stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs) {
-    const long long J0 = tt * TILE_LIMBS - HALO_LO;
-    if (VEC) {
-        stage_pairs(cs, c.coef, 4 * J0, SM_COEF / 2, c.L);
-        stage_pairs(bs, c.b, J0, SM_LIMBS_PAD / 2, Ly);
-        cp_async_commit();
-        cp_async_wait<0>();
-    } else {
-        for (int i = threadIdx.x; i < SM_COEF; i += CARRY_THREADS) {
-            long long k = 4 * J0 + i;
-            cs[i] = (k >= 0 && (u64)k < c.L) ? c.coef[k] : 0;
-        }
-        for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
-            long long j = J0 + i;
-            bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
-        }
-    }
-}
+__device__ unsigned long long g_flags;  // carry launches that set their wrapped-product flag
 
 // Only the tiles that hold output limbs (bits [n - m, n)) are processed: the
 // limbs below matter only through the carry into the first of them. Grid:
@@ -184,7 +50,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     pdl_begin();
     const CarryJob& c = cb.job[blockIdx.y];
     const u64 Ly = (c.n + 63) / 64, tiles = carry_tiles(c.n);
-    const u64 t0 = first_out_tile(c.n, c.m);
+    const u64 t0 = first_out_tile(c.n, c.m, c.flag != nullptr);
     u32* state = c.state;  // tiles words, then the ticket counter
     if (threadIdx.x == 0) tile_sh = atomicAdd(&state[tiles], 1u) + ticket_start;
     __syncthreads();
@@ -303,18 +169,16 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
         if (j >= Ly) y[i] = 0;
         else if (j == Ly - 1 && (c.n & 63)) y[i] &= (1ull << (c.n & 63)) - 1;  // mod 2^n
     }
-    u64 s = c.n - c.m, q = s >> 6;
-    unsigned r = (unsigned)(s & 63);
-    u64 Mo = (c.m + 63) >> 6;
+    const u64 q = (c.n - c.m) >> 6;
+    if (c.flag) {
 #pragma unroll
-    for (int i = 0; i < CARRY_LIMBS; i++) {
-        u64 j = j0 + i;
-        if (j < q || j >= q + Mo) continue;
-        u64 o = r ? ((y[i] >> r) | (y[i + 1] << (64 - r))) : y[i];
-        u64 oi = j - q;
-        if (oi == Mo - 1 && (c.m & 63)) o &= (1ull << (c.m & 63)) - 1;
-        c.out[oi] = o;
+        for (int i = 0; i < CARRY_LIMBS; i++)  // limb q - 1, if it is this thread's
+            if (j0 + i + 1 == q && (c.force_flag || y[i] == ~0ull)) {
+                *c.flag = 1u;
+                atomicAdd(&g_flags, 1ull);
+            }
     }
+    write_window(c, j0, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -329,7 +193,7 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     u64 tiles = 0;
     for (int i = 0; i < cb.count; i++) {
         u64 tt = carry_tiles(cb.job[i].n);
-        u64 out_tiles = tt - first_out_tile(cb.job[i].n, cb.job[i].m);
+        u64 out_tiles = tt - first_out_tile(cb.job[i].n, cb.job[i].m, cb.job[i].flag != nullptr);
         tiles = out_tiles > tiles ? out_tiles : tiles;
         if (cb.job[i].zeroed) continue;  // the caller cleared the states earlier on the stream
         cudaError_t e = cudaMemsetAsync(cb.job[i].state, 0, (tt + 1) * sizeof(u32), st);
@@ -340,7 +204,8 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     g_inject_ticket = 0;
     bool vec = true;
     for (int i = 0; i < cb.count; i++)
-        vec = vec && (uintptr_t)cb.job[i].coef % 16 == 0 && (uintptr_t)cb.job[i].b % 16 == 0;
+        vec = vec && (uintptr_t)cb.job[i].coef % 16 == 0 && (uintptr_t)cb.job[i].b % 16 == 0 &&
+              cb.job[i].lo % 2 == 0;
     dim3 grid((unsigned)tiles, (unsigned)cb.count);
     prof_begin(st, "carry_lookback");
     cudaError_t e = vec ? launch_pdl(k_carry<B, true>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)
@@ -365,6 +230,15 @@ cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t read_flag_count(unsigned long long* out, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_flags, sizeof(*out));
+    if (e == cudaSuccess && clear) {
+        unsigned long long zero = 0;
+        e = cudaMemcpyToSymbol(g_flags, &zero, sizeof(zero));
+    }
+    return e;
 }
 
 cudaError_t read_device_status(u32* out, bool clear) {

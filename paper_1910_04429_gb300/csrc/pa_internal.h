@@ -55,6 +55,10 @@ struct CarryJob {
     u64* out;         // ceil(m/64) limbs
     u32* state;       // scratch, carry_state_words(n) words, 4-byte aligned
     bool zeroed;      // state already cleared earlier on the stream; else the launch clears it
+    u64 lo;           // coefficients k < lo read as zero (a wrapped product's folded ones)
+    u32* flag;        // non-null: set to 1 when limb floor((n-m)/64) - 1 of the sum is all
+                      // ones (the dropped coefficients could carry into the output)
+    bool force_flag;  // set the flag whatever the limb holds (tests of the fallback)
 };
 template <int B>
 struct CarryBatch {
@@ -67,9 +71,15 @@ constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
 constexpr u32 CARRY_SPIN_LIMIT = 1u << 20;  // polls of a predecessor tile before giving up (~0.1-1 s)
 constexpr u32 PA_STATUS_TIMEOUT = 1u;       // device status bit: a bounded wait ran out
 GL_HD u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
-GL_HD u64 carry_state_words(u64 n) { return carry_tiles(n) + 1; }  // tile states + ticket
-// the first carry tile holding output limbs (limb (n - m) / 64 onwards)
-GL_HD u64 first_out_tile(u64 n, u64 m) { return ((n - m) / 64) / CARRY_TILE_LIMBS; }
+// tile states, the ticket counter, the wrapped product's flag
+GL_HD u64 carry_state_words(u64 n) { return carry_tiles(n) + 2; }
+GL_HD u64 carry_flag_word(u64 n) { return carry_tiles(n) + 1; }
+// the first carry tile holding output limbs (limb (n - m) / 64 onwards), or
+// with check the limb below them too
+GL_HD u64 first_out_tile(u64 n, u64 m, bool check = false) {
+    u64 q = (n - m) / 64;
+    return (check && q ? q - 1 : q) / CARRY_TILE_LIMBS;
+}
 cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
 // Carry steps of `count` independent blocks (any sizes), MAX_BATCH per launch.
 cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st);
@@ -79,6 +89,34 @@ cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st)
 void fault_inject_carry();
 // Sticky device status bits (PA_STATUS_*); synchronous.
 cudaError_t read_device_status(u32* out, bool clear);
+// How many carry launches have set their wrapped-product flag; synchronous.
+cudaError_t read_flag_count(unsigned long long* out, bool clear);
+
+// Exact recomputation of one hash behind a wrapped product, run only when the
+// wrapped product's carry step set its flag: the full product by a radix-2
+// transform of length N = 2^logN >= 2L - 1, then the carry step over every limb.
+struct FallbackJob {
+    Digits dx, da;      // the key's and the seed's digits (dx.L = L)
+    const u64* b;       // addend limbs
+    u64 n, m;
+    u64* out;           // overwritten when the flag is set
+    const u32* flag;    // the wrapped product's carry flag
+    u64* X;             // N words each
+    u64* A;
+    int logN;
+    const u64 *wlo, *wloi, *whi, *whii;  // w_N^t, w_N^-t (t < 4096), w_N^(4096 t), inverse
+    u64 ninv;           // N^-1
+    u32* state;         // carry_state_words(n) words, zeroed
+};
+template <int B>
+struct FallbackBatch {
+    int count;
+    u32* barrier;       // zeroed word: the grid barrier's counter
+    FallbackJob job[B];
+};
+// One cooperative launch per MAX_BATCH jobs; it returns at once unless a flag is set.
+cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st);
+cudaError_t read_fallback_status(u32* out, bool clear);
 
 // Inter-pass twiddle tables of a strided pass (M = sub-problem size, S =
 // stride): out[0 .. M) = w_M^(j k) at k S + j, out[M .. 2M) = w_M^-(j k).

@@ -84,6 +84,60 @@ inline Geom choose_geom_len(uint64_t need) {
 // ... that holds the linear convolution of two L-digit operands.
 inline Geom choose_geom(uint64_t L) { return choose_geom_len(2 * L - 1); }
 
+// Wrapped product for the modular hash (the output is bits [n-m, n) of
+// (a x + b) mod 2^n). A cyclic convolution of length N, L <= N < 2L - 1, gives
+// c_k = t_k + t_{k+N}, where t_k is the linear coefficient; t_{k+N} = 0 for
+// k >= W = 2L - 1 - N, so every c_k with k >= lo (lo >= W) is exact. The
+// coefficients below lo are dropped: what they would add,
+// T = sum_{k<lo} t_k 2^(16k), is below lo * 2^(16(lo+1)) <= 2^wbits. The exact
+// Q = sum_{k>=lo} c_k 2^(16k) + b then differs from a x + b by T alone, and T
+// changes the carry into bit n - m only if every bit of Q in [wbits, n - m)
+// is one. The carry step checks limb q - 1 of Q (q = floor((n - m)/64)), which
+// lies inside that range when wbits <= 64 (q - 1): if that limb is not all
+// ones the result from Q is exact, otherwise the full-length product decides.
+// (The rounding test of correctly rounded multiple-precision short products,
+// carried over to a truncated product's carry.)
+struct WrapPlan {
+    bool on = false;  // false: the full-length product (N >= 2L - 1)
+    Geom geom;        // the cyclic length
+    uint64_t lo = 0;  // coefficients k < lo are dropped (even: whole 16-byte pairs)
+};
+
+inline int bit_length(uint64_t v) {
+    int b = 0;
+    while (v) b++, v >>= 1;
+    return b;
+}
+
+// Whether a cyclic length N serves keys of n bits with m output bits (L digits).
+inline bool wrap_ok(uint64_t N, uint64_t L, uint64_t n, uint64_t m, uint64_t* lo_out) {
+    if (N < L || N >= 2 * L - 1) return false;
+    uint64_t W = 2 * L - 1 - N, lo = W + (W & 1);
+    uint64_t q = (n - m) / 64;
+    uint64_t wbits = 16 * (lo + 1) + (uint64_t)bit_length(lo);
+    if (q < 1 || wbits > 64 * (q - 1)) return false;
+    *lo_out = lo;
+    return true;
+}
+
+// The shortest transform length that is a valid wrapped length; off when none
+// is shorter than the full-length product's.
+inline WrapPlan wrap_plan(uint64_t n, uint64_t m) {
+    WrapPlan wp;
+    uint64_t L = (n + 15) / 16;
+    Geom full = choose_geom(L);
+    for (Geom g = choose_geom_len(L); g.N < full.N; g = choose_geom_len(g.N + 1)) {
+        uint64_t lo;
+        if (wrap_ok(g.N, L, n, m, &lo)) {
+            wp.on = true;
+            wp.geom = g;
+            wp.lo = lo;
+            return wp;
+        }
+    }
+    return wp;
+}
+
 // A primitive (3 * 2^32)-th root of unity R with R^(2^26) = 2: every
 // w_N = R^(3 * 2^32 / N) then satisfies w_N^(N/192) = 2 when 192 | N and
 // w_N^(N/64) = 8 when 64 | N, so all DFTs of length dividing 192 inside a

@@ -134,14 +134,16 @@ def test_argument_checks_without_gpu():
     assert b"unknown ticket" in lib.pa_last_error()
 
 
-@pytest.mark.parametrize("n,N", [(1, 4096), (32768, 4096), (32769, 8192), (96_000, 3 << 12),
-                                 (1_000_000, 1 << 17), (1_536_000, 3 << 16),
-                                 (100_000_000, 3 << 22), (1_000_000_000, 1 << 27)])
+@pytest.mark.parametrize("n,N", [(1, 4096), (32768, 4096), (32769, 8192), (96_000, 1 << 14),
+                                 (1_000_000, 1 << 17), (1_536_000, 1 << 18),
+                                 (100_000_000, 1 << 24), (1_000_000_000, 1 << 27)])
 def test_workspace_bytes(n, N):
-    """Transform length N = smallest 2^k or 3 * 2^k (first radix <= 48) that is
-    >= max(4096, 2 ceil(n/16) - 1)."""
+    """Two transform buffers of N words, N = the smallest power of two >=
+    max(4096, 2 ceil(n/16) - 1): the exact recomputation behind a wrapped
+    product runs at that length, which covers the full-length product (2^k or
+    3 * 2^k) too; and two carry-state sets (tile states, ticket, flag)."""
     tiles = -(-(-(-n // 64)) // 1024)
-    assert binding.workspace_bytes(n) == 2 * N * 8 + 4 * (tiles + 1)
+    assert binding.workspace_bytes(n) == 2 * N * 8 + 2 * 4 * (tiles + 2)
     assert binding.workspace_bytes(0) == 0
 
 

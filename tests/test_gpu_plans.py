@@ -20,15 +20,30 @@ SIZES = [1000, 100_003, 1_000_000, 1_536_000, 3_000_001, 4_800_000, 300_000_017]
 
 @pytest.mark.parametrize("n", SIZES)
 def test_every_plan_variant_is_exact(n):
-    blk = inputs.make_block(n, n // 3 or 1, seed=n)
+    """Each variant of the full-length product (wrapping off) and, where the
+    hash wraps, of the wrapped length (forced through the key size whose
+    full-length product has that length, 16 N / 2 bits)."""
+    m = n // 3 or 1
+    blk = inputs.make_block(n, m, seed=n)
     want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m, threads=oracle.default_threads())
+    first = binding.plan_info(n, m)["first"]
+    n_first = 16 * (first // 2)
+    prev = binding.wrap_mode(0)
     try:
         for v in range(16):
             binding.plan_override(n, v)
             np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
-                                          err_msg=f"variant {v}")
+                                          err_msg=f"full length, variant {v}")
+        binding.plan_override(n, -1)
+        binding.wrap_mode(1)
+        for v in range(16):
+            binding.plan_override(n_first, v)
+            np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
+                                          err_msg=f"first length {first}, variant {v}")
     finally:
         binding.plan_override(n, -1)
+        binding.plan_override(n_first, -1)
+        binding.wrap_mode(prev)
 
 
 def test_seed_keeps_its_plan():

@@ -1,0 +1,191 @@
+"""The wrapped product of the modular hash, on the CPU.
+
+The hash needs only bits [n-m, n) of a x + b mod 2^n. A cyclic convolution of
+the 16-bit digits of length N, L <= N < 2L - 1 (L = ceil(n/16)), folds the
+linear coefficients t_{k+N} onto c_k for k < W = 2L - 1 - N and leaves every
+c_k with k >= W exact. The library drops the coefficients below lo (W rounded
+up to even) and certifies the result: the dropped part is below 2^wbits,
+wbits = 16 (lo + 1) + bit_length(lo), so unless limb q - 1 (q = floor((n-m)/64))
+of the exact remaining sum Q is all ones -- which needs wbits <= 64 (q - 1) --
+the output taken from Q is exact; otherwise the full-length product runs.
+
+Here: pa_plan_info (host logic of the library, no device) against that rule,
+and an exact-integer model of the fold and of the certificate against the
+oracle on small sizes (cyclic lengths of any size, so that wrapping happens
+at a few hundred digits), including inputs built to fail the certificate.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_04429_gb300 import binding, inputs
+
+
+def _lengths(lo_len, hi_len):
+    """Transform lengths of the library (2^k, k >= 12, and 3 * 2^j, j >= 12 with
+    (j - 12) mod 6 <= 4), ascending, in [lo_len, hi_len]."""
+    out = set()
+    for k in range(12, 40):
+        if lo_len <= (1 << k) <= hi_len:
+            out.add(1 << k)
+        if (k - 12) % 6 <= 4 and lo_len <= (3 << k) <= hi_len:
+            out.add(3 << k)
+    return sorted(out)
+
+
+def _wbits(lo):
+    return 16 * (lo + 1) + lo.bit_length()
+
+
+def _certifiable(N, L, n, m):
+    """(ok, lo) of the rule above for cyclic length N."""
+    if N < L or N >= 2 * L - 1:
+        return False, 0
+    W = 2 * L - 1 - N
+    lo = W + (W & 1)
+    q = (n - m) // 64
+    return q >= 1 and _wbits(lo) <= 64 * (q - 1), lo
+
+
+SIZES = [(1, 1), (64, 1), (5000, 100), (65_536, 1), (65_537, 16_000), (100_000, 25_000), (100_000, 50_000),
+         (1_000_000, 100_000), (1_000_000, 250_000), (1_000_000, 500_000), (3_000_017, 300_001),
+         (10_000_000, 1_000_000), (10_000_000, 5_000_000), (100_000_000, 10_000_000),
+         (100_000_000, 25_000_000), (100_000_000, 50_000_000), (1_000_000_000, 250_000_000),
+         (2 ** 31, 2 ** 29), (2 ** 31, 1)]
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+def test_plan_info_follows_the_rule(n, m):
+    info = binding.plan_info(n, m)
+    L = -(-n // 16)
+    full = _lengths(max(4096, 2 * L - 1), 1 << 40)[0]
+    assert info["full"] == full
+    shorter = [N for N in _lengths(max(4096, L), full - 1)]
+    ok = [(N, lo) for N in shorter for c, lo in [_certifiable(N, L, n, m)] if c]
+    if ok:  # the shortest certifiable length, with its dropped-coefficient count
+        assert (info["first"], info["dropped"]) == ok[0]
+        assert L <= info["first"] < 2 * L - 1
+    else:
+        assert (info["first"], info["dropped"]) == (full, 0)
+
+
+def test_headline_sizes_wrap():
+    """The 10^8-bit block (m = n/4) runs 2^23 points instead of 3 * 2^22; the
+    10^9-bit block 3 * 2^25 instead of 2^27; the 10^6-bit block 3 * 2^15
+    instead of 2^17; at m = n/2 the 10^8-bit block has no shorter length."""
+    assert binding.plan_info(10 ** 8, 25 * 10 ** 6)["first"] == 1 << 23
+    assert binding.plan_info(10 ** 9, 25 * 10 ** 7)["first"] == 3 << 25
+    assert binding.plan_info(10 ** 6, 250_000)["first"] == 3 << 15
+    assert binding.plan_info(10 ** 8, 5 * 10 ** 7)["dropped"] == 0
+
+
+def test_plan_info_rejects_bad_sizes():
+    for n, m in [(0, 0), (10, 11), (10, 0), (2 ** 31 + 1, 1)]:
+        with pytest.raises(binding.PaError):
+            binding.plan_info(n, m)
+
+
+# ---------------------------------------------------------------------------
+# exact-integer model of the wrapped product and its certificate
+# ---------------------------------------------------------------------------
+def _digits(v, L):
+    return [(v >> (16 * i)) & 0xFFFF for i in range(L)]
+
+
+def _model(x, a, b, n, m, N):
+    """(output or None, lo): the output taken from the certified sum Q, or None
+    when the certificate fails (the library then runs the full product)."""
+    L = -(-n // 16)
+    ok, lo = _certifiable(N, L, n, m)
+    assert ok
+    dx, da = _digits(x, L), _digits(a, L)
+    c = [0] * N
+    t = [0] * (2 * L - 1)
+    for i in range(L):
+        if da[i]:
+            for j in range(L):
+                c[(i + j) % N] += da[i] * dx[j]
+                t[i + j] += da[i] * dx[j]
+    # the fold: every c_k with k >= lo is the linear coefficient
+    assert all(c[k] == t[k] for k in range(lo, min(N, 2 * L - 1)))
+    T = sum(t[k] << (16 * k) for k in range(lo))
+    assert T < 1 << _wbits(lo)  # the dropped part's bound
+    Q = sum(c[k] << (16 * k) for k in range(lo, L)) + b
+    assert (Q + T) % (1 << n) == (a * x + b) % (1 << n)
+    q = (n - m) // 64
+    if (Q >> (64 * (q - 1))) & ((1 << 64) - 1) == (1 << 64) - 1:
+        return None, lo
+    return (Q % (1 << n)) >> (n - m), lo
+
+
+def _small_case(n, m):
+    """The shortest cyclic length (any integer) that the rule certifies."""
+    L = -(-n // 16)
+    for N in range(L, 2 * L - 1):
+        if _certifiable(N, L, n, m)[0]:
+            return N
+    return None
+
+
+def _to_limbs(v, n):
+    return np.array([(v >> (64 * i)) & ((1 << 64) - 1) for i in range(-(-n // 64))], dtype=np.uint64)
+
+
+def _from_limbs(arr):
+    return sum(int(w) << (64 * i) for i, w in enumerate(arr))
+
+
+@pytest.mark.parametrize("n,m", [(1600, 160), (2000, 500), (3001, 750), (4096, 1024), (2500, 250)])
+def test_model_matches_oracle_on_random_inputs(n, m):
+    N = _small_case(n, m)
+    assert N is not None and N < 2 * (-(-n // 16)) - 1
+    rng = random.Random(n * 7 + m)
+    for _ in range(6):
+        x, a, b = (rng.getrandbits(n) for _ in range(3))
+        got, _ = _model(x, a, b, n, m, N)
+        want = _from_limbs(oracle.pa_hash(_to_limbs(x, n), _to_limbs(a, n), _to_limbs(b, n), n, m, threads=1))
+        assert got is not None  # a uniform b fails the certificate with probability 2^-64
+        assert got == want
+
+
+def test_model_certificate_fails_exactly_where_needed():
+    """Inputs built so that limb q - 1 of Q is all ones fail the certificate:
+    x = 0 with b = 2^n - 1; a = 1 with x = 2^n - 1; and b chosen so that the
+    low n - m bits of Q are 2^(n-m) - T, where T > 0 is the dropped part. In
+    that last case the dropped part carries into the output, so an output
+    taken from Q alone would be wrong: the fallback is needed there."""
+    n, m = 2000, 500
+    s = n - m
+    N = _small_case(n, m)
+    L = -(-n // 16)
+    lo = _certifiable(N, L, n, m)[1]
+    full = (1 << n) - 1
+    assert _model(0, 5, full, n, m, N)[0] is None
+    assert _model(full, 1, 0, n, m, N)[0] is None
+    rng = random.Random(3)
+    x, a = rng.getrandbits(n), rng.getrandbits(n) | 1
+    t = [0] * (2 * L - 1)
+    for i, ai in enumerate(_digits(a, L)):
+        for j, xj in enumerate(_digits(x, L)):
+            t[i + j] += ai * xj
+    T = sum(t[k] << (16 * k) for k in range(lo))
+    assert T > 0
+    q_target = (rng.getrandbits(m) << s) + ((1 << s) - T)
+    b = (q_target - a * x + T) % (1 << n)  # then a x + b = Q + T (mod 2^n) with Q = q_target
+    assert _model(x, a, b, n, m, N)[0] is None
+    want = ((a * x + b) % (1 << n)) >> s
+    assert want != (q_target % (1 << n)) >> s
+    assert want == _from_limbs(oracle.pa_hash(_to_limbs(x, n), _to_limbs(a, n), _to_limbs(b, n), n, m, threads=1))
+
+
+def test_inputs_module_blocks_pass_the_certificate():
+    """The seeded benchmark blocks (uniform b) pass the certificate in the model."""
+    n, m = 2000, 500
+    N = _small_case(n, m)
+    for seed in range(5):
+        blk = inputs.make_block(n, m, seed=seed)
+        x, a, b = (_from_limbs(v) for v in (blk.x, blk.a, blk.b))
+        got, _ = _model(x, a, b, n, m, N)
+        assert got == _from_limbs(oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=1))
