@@ -281,14 +281,18 @@ uint64_t pa_workspace_bytes(uint64_t n);
 /*
  * Wrapped products (see pa_hash).
  * pa_plan_info: host only, needs no device. For keys of n bits and m output
- *   bits: info[0] = the length of the transform the hash runs first, info[1] =
+ *   bits, under the current pa_wrap_mode: info[0] = the length of the
+ *   transform the hash runs first, info[1] =
  *   the full-length product's (N >= 2L - 1, used when not wrapped), info[2] =
  *   how many low coefficients the wrapped product drops (0: not wrapped,
  *   info[0] == info[1]).
  *   PA_EINVAL for sizes pa_hash rejects.
- * pa_wrap_mode: 1 (default) wrapped products where shorter; 0 always the
- *   full-length product; 2 wrapped with the check forced to fail, so every hash
- *   also runs the recomputation (tests of that path). Returns the
+ * pa_wrap_mode: 1 (default) wrapped products where shorter and the full
+ *   product has at least 2^19 points (below that the transforms fill a
+ *   fraction of the GPU and the recomputation's launch outweighs the saving);
+ *   0 always the full-length product; 2 wrapped wherever shorter; 3 as 2 with
+ *   the check forced to fail, so every hash also runs the recomputation (tests
+ *   of that path). Returns the
  *   previous mode, or PA_EINVAL. Applies to later pa_hash / pa_hash_host calls
  *   on every thread.
  * pa_wrap_flags: waits for the device, then stores in *count how many checks

@@ -306,12 +306,16 @@ int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint
     return PA_OK;
 }
 
-// Wrapped products: 1 where one is shorter than the full-length product
-// (default), 0 never, 2 always with the flag forced (every hash then also runs
-// the exact recomputation: a test of that path).
+// Wrapped products: 0 never; 1 (default) where one is shorter and the full
+// product has at least WRAP_MIN_FULL points; 2 wherever one is shorter; 3 as 2
+// with the flag forced (every hash then also runs the exact recomputation: a
+// test of that path).
 int g_wrap_mode = 1;
 
-WrapPlan wrap_for(uint64_t n, uint64_t m) { return g_wrap_mode ? wrap_plan(n, m) : WrapPlan{}; }
+WrapPlan wrap_for(uint64_t n, uint64_t m) {
+    if (g_wrap_mode == 0) return WrapPlan{};
+    return wrap_plan(n, m, g_wrap_mode == 1 ? WRAP_MIN_FULL : 0);
+}
 
 // One hash's plans and scratch. Without wrapping: the full-length product.
 // With it: the wrapped product, then its carry step (which sets the flag when
@@ -397,7 +401,7 @@ int hash_product(HashPlan& hp, cudaStream_t st) {
 int hash_finish(HashPlan& hp, const uint64_t* seed_b, uint64_t n, uint64_t m, uint64_t* out, cudaStream_t st) {
     const u64 L = (n + 15) / 16;
     u32* flag = hp.wp.on ? hp.state + carry_flag_word(n) : nullptr;
-    CarryJob c{hp.prod.buf_x, L, seed_b, n, m, out, hp.state, true, hp.wp.lo, flag, g_wrap_mode == 2};
+    CarryJob c{hp.prod.buf_x, L, seed_b, n, m, out, hp.state, true, hp.wp.lo, flag, g_wrap_mode == 3};
     cudaError_t e = launch_carry(c, st);
     if (e != cudaSuccess) return cuda_fail(e, "carry launch");
     if (hp.wp.on) {
@@ -437,13 +441,19 @@ int side_streams(int dev) {
     return PA_OK;
 }
 
-// Blocks grouped by transform geometry: each group runs its passes as batched
-// launches (blocks along gridDim.y), groups on side streams forked from and
-// joined back into `st`, then one batched carry launch for every block.
+// Blocks grouped by the geometry of the product they run first: each group
+// runs its passes as batched launches (blocks along gridDim.y), groups on side
+// streams forked from and joined back into `st`, then one batched carry launch
+// for every block and, when some block's product was wrapped, the exact
+// recomputation's launches (which return at once unless a flag is set). A
+// batch fills the GPU, so its blocks wrap wherever a shorter length exists
+// (mode 1 as well as 2); mode 0 never wraps, mode 3 forces the recomputation.
+WrapPlan batch_wrap(uint64_t n, uint64_t m) { return g_wrap_mode ? wrap_plan(n, m, 0) : WrapPlan{}; }
+
 u64 batch_workspace_bytes(const pa_block* blocks, uint32_t count) {
     u64 bytes = 0;
     for (uint32_t i = 0; i < count; i++)
-        bytes += 2 * geom_for_bits(blocks[i].n).N * sizeof(u64) + carry_state_words(blocks[i].n) * sizeof(u32);
+        bytes += 2 * buffer_words(blocks[i].n) * sizeof(u64) + 2 * carry_state_words(blocks[i].n) * sizeof(u32);
     return bytes;
 }
 
@@ -454,46 +464,86 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     int rc = side_streams(dev);
     if (rc) return rc;
     Device& d = g_dev[dev];
-    std::vector<std::pair<u64, std::vector<uint32_t>>> groups;  // N -> block indices
+    std::vector<WrapPlan> wps(count);
+    std::vector<std::pair<u64, std::vector<uint32_t>>> groups;  // first length N -> block indices
     for (uint32_t i = 0; i < count; i++) {
-        u64 N = geom_for_bits(blocks[i].n).N;
+        wps[i] = batch_wrap(blocks[i].n, blocks[i].m);
+        u64 N = wps[i].on ? wps[i].geom.N : geom_for_bits(blocks[i].n).N;
         size_t g = 0;
         while (g < groups.size() && groups[g].first != N) g++;
         if (g == groups.size()) groups.push_back({N, {}});
         groups[g].second.push_back(i);
     }
-    // workspace: all transform buffers, then the carry bytes, in one allocation
+    // workspace: every block's two transform buffers, then the carry states, in one allocation
     u64 words = 0, carry_bytes = 0;
-    for (auto& gr : groups) words += 2 * gr.first * gr.second.size();
-    for (uint32_t i = 0; i < count; i++) carry_bytes += carry_state_words(blocks[i].n) * sizeof(u32);
+    for (uint32_t i = 0; i < count; i++) {
+        words += 2 * buffer_words(blocks[i].n);
+        carry_bytes += 2 * carry_state_words(blocks[i].n) * sizeof(u32);
+    }
     Scratch scr(st, pool);
     void* ws = fixed_ws;
     if (!ws && (rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
-    u64* w = (u64*)ws;
-    u32* cb = (u32*)(w + words);
+    std::vector<u64*> wbuf(count);
+    std::vector<u32*> sbuf(count);
+    {
+        u64* w = (u64*)ws;
+        u32* cb = (u32*)((u64*)ws + words);
+        for (uint32_t i = 0; i < count; i++) {
+            wbuf[i] = w;
+            w += 2 * buffer_words(blocks[i].n);
+            sbuf[i] = cb;
+            cb += 2 * carry_state_words(blocks[i].n);
+        }
+    }
     std::vector<CarryJob> cj(count);
+    std::vector<FallbackJob> fj;
 
     // every block's carry states cleared at once, before the transforms
-    cudaError_t e = cudaMemsetAsync(cb, 0, carry_bytes, st);
+    cudaError_t e = cudaMemsetAsync((u64*)ws + words, 0, carry_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
     e = cudaEventRecord(d.fork, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(fork)");
     int used = 0;
     for (size_t g = 0; g < groups.size(); g++) {
         const auto& idx = groups[g].second;
-        Geom G = plan_for(dev, blocks[idx[0]].n);
+        const pa_block& b0 = blocks[idx[0]];
+        Geom G = wps[idx[0]].on ? plan_for_base(dev, wps[idx[0]].geom) : plan_for(dev, b0.n);
         Twiddles tw;
         if ((rc = get_tables(dev, G, &tw))) return rc;
         std::vector<BlockIO> io(idx.size());
         for (size_t k = 0; k < idx.size(); k++) {
-            const pa_block& b = blocks[idx[k]];
-            u64 L = (b.n + 15) / 16;
+            const uint32_t i = idx[k];
+            const pa_block& b = blocks[i];
+            const u64 L = (b.n + 15) / 16, bw = buffer_words(b.n);
             uint16_t top = top_digit_mask(b.n);
-            io[k] = BlockIO{w, w + G.N, Digits{(const uint16_t*)b.key, L, top},
-                            Digits{(const uint16_t*)b.seed_a, L, top}, L};
-            cj[idx[k]] = CarryJob{w, L, b.seed_b, b.n, b.m, b.out, cb, true};
-            cb += carry_state_words(b.n);
-            w += 2 * G.N;
+            Digits dx{(const uint16_t*)b.key, L, top}, da{(const uint16_t*)b.seed_a, L, top};
+            io[k] = BlockIO{wbuf[i], wbuf[i] + bw, dx, da, L};
+            const WrapPlan& wp = wps[i];
+            u32* flag = wp.on ? sbuf[i] + carry_flag_word(b.n) : nullptr;
+            cj[i] = CarryJob{wbuf[i], L, b.seed_b, b.n, b.m, b.out, sbuf[i], true, wp.lo, flag, g_wrap_mode == 3};
+            if (wp.on) {
+                const Geom fg = fallback_geom(b.n);
+                Twiddles ft;
+                if ((rc = get_base_tables(dev, fg, &ft))) return rc;
+                FallbackJob f;
+                f.dx = dx;
+                f.da = da;
+                f.b = b.seed_b;
+                f.n = b.n;
+                f.m = b.m;
+                f.out = b.out;
+                f.flag = flag;
+                f.X = wbuf[i];
+                f.A = wbuf[i] + bw;
+                f.logN = fg.logN;
+                f.wlo = ft.wlo;
+                f.wloi = ft.wloi;
+                f.whi = ft.whi;
+                f.whii = ft.whii;
+                f.ninv = n_inverse(fg.logN, 0);
+                f.state = sbuf[i] + carry_state_words(b.n);
+                fj.push_back(f);
+            }
         }
         cudaStream_t s = d.side[g % SIDE_STREAMS];
         if (g < SIDE_STREAMS) {
@@ -511,6 +561,8 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     }
     if ((e = launch_carry_batch(cj.data(), (int)count, st)) != cudaSuccess)
         return cuda_fail(e, "batched carry launch");
+    if (!fj.empty() && (e = launch_fallback(fj.data(), (int)fj.size(), st)) != cudaSuccess)
+        return cuda_fail(e, "recomputation launch");
     return PA_OK;
 }
 
@@ -1058,7 +1110,7 @@ int pa_autotune(uint64_t n, int reps, int* variant_out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b, 0x3C, in_bytes, st);
     // The lengths a hash of n bits (m = n / 4) runs: the full-length product's,
     // timed with wrapping off, and the wrapped product's when there is one.
-    WrapPlan wp = wrap_plan(n, m);
+    WrapPlan wp = wrap_plan(n, m);  // the default mode's choice
     const Geom lens[2] = {geom_for_bits(n), wp.geom};
     const int saved_mode = g_wrap_mode;
     int best_full = 0;
@@ -1120,7 +1172,11 @@ uint64_t pa_workspace_bytes(uint64_t n) {
 int pa_plan_info(uint64_t n, uint64_t m, uint64_t info[3]) {
     if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_plan_info: need 1 <= m <= n <= PA_MAX_BITS");
     if (!info) return fail(PA_EINVAL, "pa_plan_info: null pointer");
-    WrapPlan wp = wrap_plan(n, m);
+    WrapPlan wp;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        wp = wrap_for(n, m);
+    }
     info[1] = geom_for_bits(n).N;
     info[0] = wp.on ? wp.geom.N : info[1];
     info[2] = wp.on ? wp.lo : 0;
@@ -1128,7 +1184,7 @@ int pa_plan_info(uint64_t n, uint64_t m, uint64_t info[3]) {
 }
 
 int pa_wrap_mode(int mode) {
-    if (mode < 0 || mode > 2) return fail(PA_EINVAL, "pa_wrap_mode: mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(PA_EINVAL, "pa_wrap_mode: mode must be 0, 1, 2 or 3");
     std::lock_guard<std::mutex> lk(g_mu);
     int prev = g_wrap_mode;
     g_wrap_mode = mode;

@@ -29,6 +29,7 @@ namespace pa {
 __device__ u32 g_fb_status;  // sticky status bits of this kernel (PA_STATUS_*)
 
 constexpr u32 FB_SPIN_LIMIT = 1u << 24;  // polls of a grid barrier before giving up (seconds)
+constexpr int FB_BATCH = 64;             // jobs per launch (kernel parameter array, 11 KB)
 
 struct GridBarrier {
     u32* count;  // zeroed before the launch; every CTA adds one per barrier
@@ -213,7 +214,7 @@ static int fb_grid(int dev) {  // CTAs that can all be resident at once
     if (dev < 0 || dev >= 64) return 0;
     if (!cached[dev]) {
         int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback<MAX_BATCH>, CARRY_THREADS, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback<FB_BATCH>, CARRY_THREADS, 0) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;
@@ -228,9 +229,9 @@ cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int grid = fb_grid(dev);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    for (int i = 0; i < count; i += MAX_BATCH) {
-        FallbackBatch<MAX_BATCH> fb;
-        fb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
+    for (int i = 0; i < count; i += FB_BATCH) {
+        FallbackBatch<FB_BATCH> fb;
+        fb.count = count - i < FB_BATCH ? count - i : FB_BATCH;
         for (int k = 0; k < fb.count; k++) fb.job[k] = jobs[i + k];
         // the barrier counter: the (zeroed, otherwise unused) ticket word of the first job's states
         fb.barrier = fb.job[0].state + carry_tiles(fb.job[0].n);
@@ -245,7 +246,7 @@ cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         prof_begin(st, "fallback_check");
-        e = cudaLaunchKernelEx(&cfg, k_fallback<MAX_BATCH>, fb, limit);
+        e = cudaLaunchKernelEx(&cfg, k_fallback<FB_BATCH>, fb, limit);
         prof_end(st);
         if (e != cudaSuccess) return e;
     }

@@ -114,7 +114,7 @@ struct FallbackBatch {
     u32* barrier;       // zeroed word: the grid barrier's counter
     FallbackJob job[B];
 };
-// One cooperative launch per MAX_BATCH jobs; it returns at once unless a flag is set.
+// One cooperative launch per 64 jobs; it returns at once unless a flag is set.
 cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st);
 cudaError_t read_fallback_status(u32* out, bool clear);
 

@@ -120,12 +120,18 @@ inline bool wrap_ok(uint64_t N, uint64_t L, uint64_t n, uint64_t m, uint64_t* lo
     return true;
 }
 
+// Full-product lengths below this run as they are by default: their
+// transforms fill a fraction of the GPU, so a shorter one saves no time and the
+// recomputation's launch costs a few microseconds.
+constexpr uint64_t WRAP_MIN_FULL = 1ull << 19;
+
 // The shortest transform length that is a valid wrapped length; off when none
-// is shorter than the full-length product's.
-inline WrapPlan wrap_plan(uint64_t n, uint64_t m) {
+// is shorter than the full-length product's, or that one is below min_full.
+inline WrapPlan wrap_plan(uint64_t n, uint64_t m, uint64_t min_full = WRAP_MIN_FULL) {
     WrapPlan wp;
     uint64_t L = (n + 15) / 16;
     Geom full = choose_geom(L);
+    if (full.N < min_full) return wp;
     for (Geom g = choose_geom_len(L); g.N < full.N; g = choose_geom_len(g.N + 1)) {
         uint64_t lo;
         if (wrap_ok(g.N, L, n, m, &lo)) {

@@ -26,16 +26,17 @@ def test_every_plan_variant_is_exact(n):
     m = n // 3 or 1
     blk = inputs.make_block(n, m, seed=n)
     want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m, threads=oracle.default_threads())
+    prev = binding.wrap_mode(2)  # wrapped wherever a shorter length exists
     first = binding.plan_info(n, m)["first"]
     n_first = 16 * (first // 2)
-    prev = binding.wrap_mode(0)
+    binding.wrap_mode(0)
     try:
         for v in range(16):
             binding.plan_override(n, v)
             np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
                                           err_msg=f"full length, variant {v}")
         binding.plan_override(n, -1)
-        binding.wrap_mode(1)
+        binding.wrap_mode(2)
         for v in range(16):
             binding.plan_override(n_first, v)
             np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,

@@ -12,6 +12,15 @@ from tests.gpu_util import dev, gpu_hash, host
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(autouse=True)
+def wrap_wherever_shorter():
+    """Mode 2: wrapped products at every size with a shorter length (the
+    default, mode 1, leaves full products below 2^19 points unwrapped)."""
+    prev = binding.wrap_mode(2)
+    yield
+    binding.wrap_mode(prev)
+
 # sizes whose hash wraps (checked below): a few tiles, ragged n and m, 2^k and
 # 3 * 2^k wrapped lengths, one and two strided passes, and the 10^6-bit block
 WRAPPED = [(100_000, 25_000), (100_003, 12_345), (1_000_000, 250_000), (1_000_003, 100_001),
@@ -43,28 +52,22 @@ def test_wrapped_matches_oracle(n, m):
 
 @pytest.mark.parametrize("n,m", WRAPPED[:5])
 def test_forced_fallback_matches_oracle(n, m):
-    """Mode 2 fails every certificate: the recomputation runs after the
+    """Mode 3 fails every certificate: the recomputation runs after the
     wrapped product and its output replaces the wrapped one's."""
     blk = inputs.make_block(n, m, seed=5)
-    prev = binding.wrap_mode(2)
-    try:
-        binding.wrap_flags(clear=True)
-        got = gpu_hash(binding, blk.x, blk.a, blk.b, n, m)
-        assert binding.wrap_flags() == 1
-    finally:
-        binding.wrap_mode(prev)
+    binding.wrap_mode(3)
+    binding.wrap_flags(clear=True)
+    got = gpu_hash(binding, blk.x, blk.a, blk.b, n, m)
+    assert binding.wrap_flags() == 1
     np.testing.assert_array_equal(got, _want(blk))
 
 
 def test_wrapping_off_matches_oracle():
     n, m = 1_000_003, 100_001
     blk = inputs.make_block(n, m, seed=6)
-    prev = binding.wrap_mode(0)
-    try:
-        got = gpu_hash(binding, blk.x, blk.a, blk.b, n, m)
-    finally:
-        binding.wrap_mode(prev)
-    np.testing.assert_array_equal(got, _want(blk))
+    binding.wrap_mode(0)
+    assert binding.plan_info(n, m)["dropped"] == 0
+    np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, n, m), _want(blk))
 
 
 def _dropped_part(x, a, L, lo):
@@ -113,11 +116,8 @@ def test_host_buffers_wrapped_and_forced():
     blk = inputs.make_block(n, m, seed=9)
     want = _want(blk)
     np.testing.assert_array_equal(binding.hash_host(blk.x, blk.a, blk.b, n, m), want)
-    prev = binding.wrap_mode(2)
-    try:
-        np.testing.assert_array_equal(binding.hash_host(blk.x, blk.a, blk.b, n, m), want)
-    finally:
-        binding.wrap_mode(prev)
+    binding.wrap_mode(3)
+    np.testing.assert_array_equal(binding.hash_host(blk.x, blk.a, blk.b, n, m), want)
 
 
 def test_full_size_wrapped_sampled():
@@ -134,15 +134,12 @@ def test_full_size_wrapped_sampled():
     got = host(binding.hash(tx, ta, tb, n, m))
     torch.cuda.synchronize()
     assert binding.wrap_flags() == 0
-    prev = binding.wrap_mode(0)
-    try:
-        ref = host(binding.hash(tx, ta, tb, n, m))
-        torch.cuda.synchronize()
-        binding.wrap_mode(2)  # the recomputation at length 2^24 as well
-        forced = host(binding.hash(tx, ta, tb, n, m))
-        torch.cuda.synchronize()
-    finally:
-        binding.wrap_mode(prev)
+    binding.wrap_mode(0)
+    ref = host(binding.hash(tx, ta, tb, n, m))
+    torch.cuda.synchronize()
+    binding.wrap_mode(3)  # the recomputation at length 2^24 as well
+    forced = host(binding.hash(tx, ta, tb, n, m))
+    torch.cuda.synchronize()
     np.testing.assert_array_equal(got, ref)
     np.testing.assert_array_equal(forced, ref)
     assert binding.device_status() == 0  # no bounded wait ran out

@@ -56,14 +56,33 @@ SIZES = [(1, 1), (64, 1), (5000, 100), (65_536, 1), (65_537, 16_000), (100_000, 
          (2 ** 31, 2 ** 29), (2 ** 31, 1)]
 
 
+@pytest.fixture
+def wrap_mode():
+    """Sets pa_wrap_mode for one test (a host-side setting, no device)."""
+    prev = []
+
+    def set_mode(mode):
+        prev.append(binding.wrap_mode(mode))
+
+    yield set_mode
+    if prev:
+        binding.wrap_mode(prev[0])
+
+
+@pytest.mark.parametrize("mode", [1, 2, 0])
 @pytest.mark.parametrize("n,m", SIZES)
-def test_plan_info_follows_the_rule(n, m):
+def test_plan_info_follows_the_rule(n, m, mode, wrap_mode):
+    """Mode 1 (default): the rule where the full product has >= 2^19 points;
+    mode 2: wherever a shorter length is certifiable; mode 0: never."""
+    wrap_mode(mode)
     info = binding.plan_info(n, m)
     L = -(-n // 16)
     full = _lengths(max(4096, 2 * L - 1), 1 << 40)[0]
     assert info["full"] == full
     shorter = [N for N in _lengths(max(4096, L), full - 1)]
     ok = [(N, lo) for N in shorter for c, lo in [_certifiable(N, L, n, m)] if c]
+    if mode == 0 or (mode == 1 and full < 1 << 19):
+        ok = []
     if ok:  # the shortest certifiable length, with its dropped-coefficient count
         assert (info["first"], info["dropped"]) == ok[0]
         assert L <= info["first"] < 2 * L - 1
@@ -71,14 +90,17 @@ def test_plan_info_follows_the_rule(n, m):
         assert (info["first"], info["dropped"]) == (full, 0)
 
 
-def test_headline_sizes_wrap():
+def test_headline_sizes_wrap(wrap_mode):
     """The 10^8-bit block (m = n/4) runs 2^23 points instead of 3 * 2^22; the
-    10^9-bit block 3 * 2^25 instead of 2^27; the 10^6-bit block 3 * 2^15
-    instead of 2^17; at m = n/2 the 10^8-bit block has no shorter length."""
+    10^9-bit block 3 * 2^25 instead of 2^27; at m = n/2 the 10^8-bit block has
+    no shorter length. The 10^6-bit block (2^17 points) stays unwrapped by
+    default and wraps to 3 * 2^15 in mode 2."""
     assert binding.plan_info(10 ** 8, 25 * 10 ** 6)["first"] == 1 << 23
     assert binding.plan_info(10 ** 9, 25 * 10 ** 7)["first"] == 3 << 25
-    assert binding.plan_info(10 ** 6, 250_000)["first"] == 3 << 15
     assert binding.plan_info(10 ** 8, 5 * 10 ** 7)["dropped"] == 0
+    assert binding.plan_info(10 ** 6, 250_000)["dropped"] == 0
+    wrap_mode(2)
+    assert binding.plan_info(10 ** 6, 250_000)["first"] == 3 << 15
 
 
 def test_plan_info_rejects_bad_sizes():
