@@ -351,6 +351,33 @@ u64 buffer_words(uint64_t n) {
     return full > fb ? full : fb;
 }
 
+// The recomputation of one wrapped hash: digits dx, da; buffers X, A of the
+// power-of-two length's words; its own (zeroed) carry states; the wrapped
+// product's flag. b and out are filled in when the carry step is queued.
+int fallback_job(int dev, uint64_t n, uint64_t m, const Digits& dx, const Digits& da, u64* X, u64* A,
+                 u32* state, const u32* flag, FallbackJob* f) {
+    const Geom fg = fallback_geom(n);
+    Twiddles t;
+    int rc = get_base_tables(dev, fg, &t);
+    if (rc) return rc;
+    *f = FallbackJob{};
+    f->dx = dx;
+    f->da = da;
+    f->n = n;
+    f->m = m;
+    f->flag = flag;
+    f->X = X;
+    f->A = A;
+    f->logN = fg.logN;
+    f->wlo = t.wlo;
+    f->wloi = t.wloi;
+    f->whi = t.whi;
+    f->whii = t.whii;
+    f->ninv = n_inverse(fg.logN, 0);
+    f->state = state;
+    return PA_OK;
+}
+
 // Plans, twiddle tables, buffers and the zeroed carry states (queued on st
 // now, before any transform).
 int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, cudaStream_t st,
@@ -367,25 +394,10 @@ int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64
     const size_t state_words = (hp->wp.on ? 2 : 1) * carry_state_words(n);
     if ((rc = scr.get(state_words * sizeof(u32), &sp))) return rc;
     hp->state = (u32*)sp;
-    if (hp->wp.on) {
-        Twiddles t;
-        if ((rc = get_base_tables(dev, fg, &t))) return rc;
-        FallbackJob& f = hp->fb;
-        f.dx = hp->prod.dx;
-        f.da = hp->prod.da;
-        f.n = n;
-        f.m = m;
-        f.flag = hp->state + carry_flag_word(n);
-        f.X = (u64*)bx;
-        f.A = (u64*)ba;
-        f.logN = fg.logN;
-        f.wlo = t.wlo;
-        f.wloi = t.wloi;
-        f.whi = t.whi;
-        f.whii = t.whii;
-        f.ninv = n_inverse(fg.logN, 0);
-        f.state = hp->state + carry_state_words(n);
-    }
+    if (hp->wp.on && (rc = fallback_job(dev, n, m, hp->prod.dx, hp->prod.da, (u64*)bx, (u64*)ba,
+                                        hp->state + carry_state_words(n), hp->state + carry_flag_word(n),
+                                        &hp->fb)))
+        return rc;
     cudaError_t e = cudaMemsetAsync(sp, 0, state_words * sizeof(u32), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
     return PA_OK;
@@ -522,26 +534,12 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
             u32* flag = wp.on ? sbuf[i] + carry_flag_word(b.n) : nullptr;
             cj[i] = CarryJob{wbuf[i], L, b.seed_b, b.n, b.m, b.out, sbuf[i], true, wp.lo, flag, g_wrap_mode == 3};
             if (wp.on) {
-                const Geom fg = fallback_geom(b.n);
-                Twiddles ft;
-                if ((rc = get_base_tables(dev, fg, &ft))) return rc;
                 FallbackJob f;
-                f.dx = dx;
-                f.da = da;
+                if ((rc = fallback_job(dev, b.n, b.m, dx, da, wbuf[i], wbuf[i] + bw,
+                                       sbuf[i] + carry_state_words(b.n), flag, &f)))
+                    return rc;
                 f.b = b.seed_b;
-                f.n = b.n;
-                f.m = b.m;
                 f.out = b.out;
-                f.flag = flag;
-                f.X = wbuf[i];
-                f.A = wbuf[i] + bw;
-                f.logN = fg.logN;
-                f.wlo = ft.wlo;
-                f.wloi = ft.wloi;
-                f.whi = ft.whi;
-                f.whii = ft.whii;
-                f.ninv = n_inverse(fg.logN, 0);
-                f.state = sbuf[i] + carry_state_words(b.n);
                 fj.push_back(f);
             }
         }
@@ -903,6 +901,14 @@ int pa_batch_destroy(pa_batch batch) {
 
 }  // extern "C"
 
+// A spectrum of the seed at a wrapped length, built on first use on the
+// caller's stream; later uses on any stream wait for `ready`.
+struct SeedSpectrum {
+    Geom G;
+    u64* spec;
+    cudaEvent_t ready;
+};
+
 struct pa_seed_s {
     int dev;
     uint64_t n;
@@ -910,6 +916,9 @@ struct pa_seed_s {
     u64* spec;  // the seed's spectrum, N words (tile register order, times N^-1)
     uint64_t m = 0;         // Toeplitz handles: output bits
     bool toeplitz = false;  // a Toeplitz seed (one-bit digits, n + m - 1 bits)
+    u64* limbs = nullptr;   // modular-hash handles: a copy of the seed's limbs (the digits of
+                            // the wrapped spectra and of the recomputation)
+    std::vector<SeedSpectrum> wrapped;
 };
 
 extern "C" {
@@ -935,9 +944,61 @@ int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* ou
         cudaFree(spec);
         return cuda_fail(e, "seed transform launch");
     }
-    *out = new pa_seed_s{dev, n, j.geom, spec};
+    u64* limbs = nullptr;
+    const size_t limb_bytes = ((n + 63) / 64) * sizeof(u64);
+    if ((e = cudaMalloc(&limbs, limb_bytes)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(limbs, seed_a, limb_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)) !=
+            cudaSuccess) {
+        cudaFree(limbs);
+        cudaFree(spec);
+        return cuda_fail(e, "seed limbs copy");
+    }
+    pa_seed_s* h = new pa_seed_s{dev, n, j.geom, spec};
+    h->limbs = limbs;
+    *out = h;
     return PA_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// The handle's spectrum at wrapped length G0 (plan for it taken on first use).
+int seed_spectrum(pa_seed seed, const Geom& G0, cudaStream_t st, int dev, SeedSpectrum** out) {
+    for (SeedSpectrum& s : seed->wrapped)
+        if (s.G.N == G0.N) {
+            cudaError_t e = cudaStreamWaitEvent(st, s.ready, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent(seed spectrum)");
+            *out = &s;
+            return PA_OK;
+        }
+    SeedSpectrum s{plan_for_base(dev, G0), nullptr, nullptr};
+    NttJob j;
+    j.geom = s.G;
+    j.L = (seed->n + 15) / 16;
+    int rc = get_tables(dev, s.G, &j.tw);
+    if (rc) return rc;
+    cudaError_t e = cudaMalloc(&s.spec, s.G.N * sizeof(u64));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        j.buf_x = j.buf_a = s.spec;
+        j.da = j.dx = Digits{reinterpret_cast<const uint16_t*>(seed->limbs), j.L, top_digit_mask(seed->n)};
+        e = launch_seed_spectrum(j, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s.ready, st);
+    if (e != cudaSuccess) {
+        if (s.ready) cudaEventDestroy(s.ready);
+        cudaFree(s.spec);
+        return cuda_fail(e, "wrapped seed spectrum");
+    }
+    seed->wrapped.push_back(s);
+    *out = &seed->wrapped.back();
+    return PA_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, uint64_t m,
                    uint64_t* out, void* stream) {
@@ -952,6 +1013,44 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
     if (dev != seed->dev) return fail(PA_EINVAL, "pa_hash_seeded: seed made on another device");
     cudaStream_t st = (cudaStream_t)stream;
     Scratch scr(st, pool);
+    const uint64_t n = seed->n;
+    WrapPlan wp = wrap_for(n, m);
+    if (wp.on) {
+        // x's transform at the wrapped length against the seed's spectrum there,
+        // the certified carry step, the recomputation (a's digits from the copy)
+        SeedSpectrum* ss = nullptr;
+        if ((rc = seed_spectrum(seed, wp.geom, st, dev, &ss))) return rc;
+        const Geom fg = fallback_geom(n);
+        const u64 words = fg.N > ss->G.N ? fg.N : ss->G.N;
+        void *bx, *ba, *sp;
+        const size_t state_words = 2 * carry_state_words(n);
+        if ((rc = scr.get(words * sizeof(u64), &bx)) || (rc = scr.get(fg.N * sizeof(u64), &ba)) ||
+            (rc = scr.get(state_words * sizeof(u32), &sp)))
+            return rc;
+        u32* state = (u32*)sp;
+        cudaError_t e = cudaMemsetAsync(sp, 0, state_words * sizeof(u32), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
+        NttJob j;
+        j.geom = ss->G;
+        j.L = (n + 15) / 16;
+        if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
+        j.buf_x = (u64*)bx;
+        j.buf_a = ss->spec;
+        j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top_digit_mask(n)};
+        j.da = Digits{reinterpret_cast<const uint16_t*>(seed->limbs), j.L, top_digit_mask(n)};
+        if ((e = launch_convolution_seeded(j, st)) != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
+        u32* flag = state + carry_flag_word(n);
+        CarryJob c{j.buf_x, j.L, seed_b, n, m, out, state, true, wp.lo, flag, g_wrap_mode == 3};
+        if ((e = launch_carry(c, st)) != cudaSuccess) return cuda_fail(e, "carry launch");
+        FallbackJob f;
+        if ((rc = fallback_job(dev, n, m, j.dx, j.da, (u64*)bx, (u64*)ba, state + carry_state_words(n), flag,
+                               &f)))
+            return rc;
+        f.b = seed_b;
+        f.out = out;
+        if ((e = launch_fallback(&f, 1, st)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
+        return PA_OK;
+    }
     NttJob j;
     j.geom = seed->G;
     j.L = (seed->n + 15) / 16;
@@ -1066,6 +1165,11 @@ int pa_seed_destroy(pa_seed seed) {
     cudaGetDevice(&prev);
     cudaSetDevice(seed->dev);
     cudaError_t e = cudaFree(seed->spec);
+    if (seed->limbs) cudaFree(seed->limbs);
+    for (SeedSpectrum& s : seed->wrapped) {
+        cudaFree(s.spec);
+        cudaEventDestroy(s.ready);
+    }
     if (prev >= 0) cudaSetDevice(prev);
     delete seed;
     return e == cudaSuccess ? PA_OK : cuda_fail(e, "cudaFree(seed spectrum)");

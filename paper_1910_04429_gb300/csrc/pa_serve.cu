@@ -98,6 +98,9 @@ void finish_batch(Batch* b, int status) {  // with g_srv.mu held
     g_srv.inflight_bytes -= b->footprint;
     if (b->slot >= 0) g_srv.slot_busy[b->slot] = nullptr;
     delete b;
+    // wake pa_poll callers: the device callback's notification came before the
+    // results were marked done, so a poller woken by it went back to waiting
+    g_srv.cv.notify_all();
 }
 
 void worker_main() {

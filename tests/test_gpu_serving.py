@@ -136,3 +136,32 @@ def test_served_admission_budget():
         binding.submit(x, x, x, big.n, big.m, o)
     assert e.value.code == binding.PA_EINVAL
     binding.serve_stop()
+
+
+def test_poll_returns_when_the_result_is_ready():
+    """pa_poll wakes when the serving loop marks the result done, not at its
+    deadline: each of several lone requests (nothing else in flight to wake the
+    poller again) is polled with a 10 s timeout and must come back in well
+    under a second."""
+    import time
+
+    import torch
+
+    binding.serve_stop()
+    binding.serve_init(max_batch=4, streams=2)
+    b = inputs.make_block(200_000, 50_000, seed=12)
+    x, a, bb = dev(b.x), dev(b.a), dev(b.b)
+    o = torch.empty((b.m + 63) // 64, dtype=torch.int64, device="cuda")
+    want = _alone([b])[0]
+    try:
+        for _ in range(5):
+            tk = binding.submit(x, a, bb, b.n, b.m, o)
+            t0 = time.perf_counter()
+            rc, st = binding.poll(tk, 10_000_000)
+            waited = time.perf_counter() - t0
+            assert (rc, st) == (binding.PA_OK, binding.PA_OK)
+            assert waited < 0.5, waited
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(host(o), want)
+    finally:
+        binding.serve_stop()
