@@ -215,19 +215,28 @@ GL_HD u64 shl_hi(u64 x, int s) { return sub(mul_eps((u32)x << (s - 64)), x >> (9
 // x * 2^s mod p for s in [160, 192): 2^s = -2^(s-96), the negation of shl_hi.
 GL_HD u64 shl_top(u64 x, int s) { return sub(x >> (192 - s), mul_eps((u32)x << (s - 160))); }
 
-// x * 2^s mod p for a run-time s in [0, 192), by range: s < 32 folds one top
-// word; s < 64 and s < 96 split x at bit 96 - s (2^96 = -1); s >= 96 negates a
-// smaller shift, and s >= 160 splits like s < 96. Inside fully unrolled loops s
-// is a constant and the branches fold away; where s varies it is uniform across
-// a warp in every caller.
+// x * 2^s mod p for a run-time s in [0, 192), by range. The integer ALU pipe
+// bounds the transforms while the multiplier (FMA) pipe has room, so where a
+// chain of the multiplier-based routes (shl_hi: 1 ALU + 3 FMA instructions,
+// shl_top: 2 + 3) costs fewer ALU instructions than a direct route it is used
+// instead, with 2^192 = 1 (2 has order 192 mod p):
+//   s < 32           shl_small                      5 + 5
+//   32 <= s < 64     2^64 * 2^(s+128): hi, top       3 + 6  (shl_mid: 8 + 3)
+//   64 <= s < 96     shl_hi                          1 + 3
+//   s = 96           negation
+//   96 < s < 128     2^64 * 2^64 * 2^(s+64)          4 + 9  (negated shl_small: 7 + 5)
+//   128 <= s < 160   2^64 * 2^(s-64): hi, hi         2 + 6  (negated shl_mid: 10 + 3)
+//   160 <= s < 192   shl_top                         2 + 3
+// Inside fully unrolled loops s is a constant and the branches fold away; where
+// s varies it is uniform across a warp in every caller.
 GL_HD u64 shl_v(u64 x, int s) {
     if (s == 0) return x;
     if (s < 32) return shl_small(x, s);
-    if (s < 64) return shl_mid(x, s);
+    if (s < 64) return shl_top(shl_hi(x, 64), s + 128);
     if (s < 96) return shl_hi(x, s);
     if (s == 96) return neg(x);
-    if (s < 128) return neg(shl_small(x, s - 96));
-    if (s < 160) return neg(shl_mid(x, s - 96));
+    if (s < 128) return shl_top(shl_hi(shl_hi(x, 64), 64), s + 64);
+    if (s < 160) return shl_hi(shl_hi(x, 64), s - 64);
     return shl_top(x, s);
 }
 
