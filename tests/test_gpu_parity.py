@@ -303,15 +303,24 @@ def test_parity_config2_full_size():
     _check_block(inputs.make_block(100_000_000, 25_000_000, seed=1))
 
 
-def test_parity_config5_digest():
-    """n = 10^9, m = 2.5 * 10^8, seed 1, against the stored oracle digest."""
+@pytest.mark.parametrize("wrap_mode", [1, 0, 3])
+def test_parity_config5_digest(wrap_mode):
+    """n = 10^9, m = 2.5 * 10^8, seed 1, against the stored oracle digest: as
+    the library runs it (the wrapped product, length 3 * 2^25), as the
+    full-length product (2^27), and with the certificate forced to fail (the
+    recomputation at 2^27 points)."""
     path = os.path.join(GOLDEN, "oracle_digest_n1000000000_m250000000_seed1.json")
     if not os.path.exists(path):
         pytest.skip("oracle digest for n = 10^9 not generated")
     with open(path) as f:
         rec = json.load(f)
     blk = inputs.make_block(rec["n"], rec["m"], rec["seed"])
-    got = gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m)
+    prev = binding.wrap_mode(wrap_mode)
+    try:
+        got = gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m)
+    finally:
+        binding.wrap_mode(prev)
     assert got.size == rec["out_limbs"]
     assert [f"{int(v):016x}" for v in got[:4]] == rec["first_limbs"]
     assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == rec["sha256"]
+    assert binding.device_status() == 0
