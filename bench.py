@@ -287,6 +287,25 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     flags = binding.wrap_flags()  # failed certificates in the timed steps (each ran the full product)
 
+    # the same workload as the full-length product (wrapping off), for comparison
+    full_ms = None
+    if binding.plan_info(n, m)["dropped"] and not args.no_profile:
+        prev_mode = binding.wrap_mode(0)
+        try:
+            kf = min(args.steps, 200)
+            for i in range(3):
+                step(i)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for i in range(kf):
+                step(i)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            full_ms = f0.elapsed_time(f1) / kf
+        finally:
+            binding.wrap_mode(prev_mode)
+
     # latency of single plain launches timed alone (events around each hash,
     # synchronized between hashes), p50 / p99 over 200 launches
     lat = []
@@ -375,7 +394,7 @@ def run_ours(args, rank, world, local):
     ms_total, e2e_ms, e2e_sync_ms = max_over_ranks([ms_total, e2e_ms, e2e_sync_ms], world, dev)
     return dict(ms_total=ms_total, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats, clocks=clk, latency=latency,
                 h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small,
-                toeplitz=toep, flags=flags, plan=binding.plan_info(n, m))
+                toeplitz=toep, flags=flags, plan=binding.plan_info(n, m), full_ms=full_ms)
 
 
 def run_toeplitz(dev, stream, sizes=((100_000_000, 25_000_000, 20), (1_000_000, 250_000, 200))):
@@ -768,6 +787,10 @@ def main():
                     "sync_value": round(aggregate_mbps(world, 1, n, res["e2e_sync_ms"]), 1)},
             "gpu_launches": launches,
             "latency": res["latency"],
+            "full_length_product": None if res["full_ms"] is None else {
+                "value": round(aggregate_mbps(world, 1, n, res["full_ms"]), 1), "unit": UNIT,
+                "length": plan["full"],
+                "note": "same workload with wrapped products off (pa_wrap_mode 0): the full product"},
             "seed_reuse": None if res["seeded_ms"] is None else {
                 "value": round(aggregate_mbps(world, 1, n, res["seeded_ms"]), 1), "unit": UNIT,
                 "note": "same workload, multiplier's transform computed once (pa_hash_seeded)"},
