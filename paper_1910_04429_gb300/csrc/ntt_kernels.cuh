@@ -186,7 +186,7 @@ template <bool PACK, int B>
 __global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttBatch<B> nb, u64 ninv,
                                                     Twiddles tw) {
     pdl_begin();
-    __shared__ u64 sm[TILE];
+    __shared__ u64 sm[TILE_SM];
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
     u64 v[8];
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttB
 template <bool PACK, int B>
 __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ NttBatch<B> nb, Twiddles tw) {
     pdl_begin();
-    __shared__ u64 sm[TILE];
+    __shared__ u64 sm[TILE_SM];
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
     int t = threadIdx.x;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ N
     pdl_begin();
     extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
-    u64* ah = dsm + TILE;
+    u64* ah = dsm + TILE_SM;
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
     int t = threadIdx.x;
@@ -290,8 +290,8 @@ static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_c
     pdl_begin();
     extern __shared__ __align__(16) u64 dsm[];
     const int h = threadIdx.x / NT, t = threadIdx.x % NT;  // half 0: a, half 1: x
-    u64* sm = dsm + h * TILE;
-    u64* ah = dsm + 2 * TILE;
+    u64* sm = dsm + h * TILE_SM;
+    u64* ah = dsm + 2 * TILE_SM;
     const BlockIO& io = nb.io[0];
     u64 base = (u64)blockIdx.x * TILE;
     const bool scaled = tw.w4096s != nullptr;
@@ -478,7 +478,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     if constexpr (B == 1) {
         if (ops == 2 && narrow && !pack) {
             // few tiles: the two operands' forward tile passes side by side
-            constexpr size_t smem = 3 * TILE * sizeof(u64);
+            constexpr size_t smem = (2 * TILE_SM + TILE) * sizeof(u64);
             prof_begin(st, "ntt_contig_both");
             allow_smem(k_contig_pair, smem);
             launch_pdl(k_contig_pair, tiles, dim3(2 * NT), smem, st, nb, ninv, tw);
@@ -488,7 +488,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     }
     if (!paired && ops == 2) {
         // both operands' tile passes in one kernel (a's spectrum stays on chip)
-        constexpr size_t smem = 2 * TILE * sizeof(u64);
+        constexpr size_t smem = (TILE_SM + TILE) * sizeof(u64);
         prof_begin(st, "ntt_contig_both");
         if (pack) {
             allow_smem(k_contig_both<true, B>, smem);

@@ -252,7 +252,14 @@ struct Strided {
 // ---------------------------------------------------------------------------
 // contiguous 4096-element pass: 64 x 64 tile, element (r, c) at offset 64 r + c
 // ---------------------------------------------------------------------------
-GL_HD int sidx(int r, int c) { return r * 64 + (c ^ (r & 15)); }  // bank-conflict-free swizzle
+// The contiguous pass's 64 x 64 tile in shared memory, rows padded to 65 words:
+// a column access (one row across a warp's lanes) and a row access (one column
+// across lanes, rows 65 words apart, 65 = 1 mod 16) both touch 16 distinct
+// 8-byte bank slots per half-warp, and every address is affine in the loop
+// index, so the per-access offsets fold into the load and store instructions.
+constexpr int TILE_PITCH = 65;
+constexpr int TILE_SM = 64 * TILE_PITCH;  // words
+GL_HD int sidx(int r, int c) { return r * TILE_PITCH + c; }
 
 struct Lane {
     int u;    // warp & 7: j0 or kr of the current step (uniform in a warp)
