@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ Ntt
     __syncthreads();
     c_inv_col_b_store(t, sm, v);
     __syncthreads();
-    c_inv_col_a(t, sm, io.buf_x + base, base, PACK ? io.L : ~0ull);
+    c_inv_col_a<PACK>(t, sm, io.buf_x + base, base, io.L);
 }
 
 // Both operands of one tile in one CTA: a's forward contiguous pass (times N^-1)
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ N
     __syncthreads();
     c_inv_col_b_store(t, sm, v);
     __syncthreads();
-    c_inv_col_a(t, sm, io.buf_x + base, base, PACK ? io.L : ~0ull);
+    c_inv_col_a<PACK>(t, sm, io.buf_x + base, base, io.L);
 }
 
 __device__ __forceinline__ void bar_sync_half() {  // named barrier 1 over NT threads
@@ -318,7 +318,7 @@ static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_c
     bar_sync_half();
     c_inv_col_b_store(t, sm, v);
     bar_sync_half();
-    c_inv_col_a(t, sm, io.buf_x + base, base, ~0ull);
+    c_inv_col_a<false>(t, sm, io.buf_x + base, base, io.L);
 }
 
 // ---------------------------------------------------------------------------

@@ -356,7 +356,10 @@ GL_HD void c_inv_col_b_store(int t, u64* sm, const u64* v) {
 #pragma unroll
     for (int j0 = 0; j0 < 8; j0++) sm[sidx(ln.u * 8 + j0, ln.idx)] = v[j0];
 }
-// I6: inverse of F1 (j0 = u): rows u + 8 j1 of column c go back to global
+// I6: inverse of F1 (j0 = u): rows u + 8 j1 of column c go back to global.
+// LAST (the transform's last pass): only positions below keep, as exact
+// digits; otherwise field values for the next inverse pass (p may stand for 0).
+template <bool LAST>
 GL_HD void c_inv_col_a(int t, const u64* sm, u64* dst, u64 base, u64 keep) {
     Lane ln = lane_of(t);
     u64 v[8];
@@ -367,7 +370,8 @@ GL_HD void c_inv_col_a(int t, const u64* sm, u64* dst, u64 base, u64 keep) {
 #pragma unroll
     for (int j1 = 0; j1 < 8; j1++) {
         int off = (ln.u + 8 * j1) * 64 + ln.idx;
-        if (base + off < keep) dst[off] = gl::canon(v[j1]);
+        if (!LAST) dst[off] = v[j1];
+        else if (base + off < keep) dst[off] = gl::canon(v[j1]);
     }
 }
 

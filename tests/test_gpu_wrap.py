@@ -24,7 +24,11 @@ def wrap_wherever_shorter():
 # sizes whose hash wraps (checked below): a few tiles, ragged n and m, 2^k and
 # 3 * 2^k wrapped lengths, one and two strided passes, and the 10^6-bit block
 WRAPPED = [(100_000, 25_000), (100_003, 12_345), (1_000_000, 250_000), (1_000_003, 100_001),
-           (3_000_017, 300_001), (4_800_000, 1_200_000), (10_000_000, 1_000_000)]
+           (3_000_017, 300_001), (4_800_000, 1_200_000), (10_000_000, 1_000_000),
+           # floor((n - m)/64) = 10 * 1024: the certificate's limb lies in the carry
+           # tile below the first output tile (the carry kernel starts one tile lower),
+           # with n - m a multiple of 64 and not
+           (819_200, 163_840), (819_200, 163_823)]
 
 
 def _want(blk):
@@ -109,6 +113,20 @@ def test_crafted_inputs_take_the_fallback():
         assert binding.wrap_flags() == i + 1, i
     # the last case needed the fallback: the sum without the dropped part is one off
     assert _int(oracle.pa_hash(x, a, b_carry, n, m, threads=4)) == ((q_target >> s) + 1) % (1 << m)
+
+
+@pytest.mark.parametrize("n,m", [(819_200, 163_840), (819_200, 163_823), (1_000_000, 250_000)])
+def test_all_ones_addend_is_flagged(n, m):
+    """x = 0, b = 2^n - 1: the sum's limb below the output is all ones, so the
+    certificate must fail (also where that limb lies in the tile below the
+    first output tile) and the output is b's top m bits."""
+    assert binding.plan_info(n, m)["dropped"] > 0
+    ones = _limbs((1 << n) - 1, n)
+    a = inputs.make_block(n, m, seed=3).a
+    binding.wrap_flags(clear=True)
+    got = gpu_hash(binding, np.zeros_like(ones), a, ones, n, m)
+    assert binding.wrap_flags() == 1
+    np.testing.assert_array_equal(got, oracle.pa_hash(np.zeros_like(ones), a, ones, n, m, threads=4))
 
 
 def test_host_buffers_wrapped_and_forced():
