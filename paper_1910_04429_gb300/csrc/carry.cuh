@@ -31,9 +31,9 @@ constexpr int GP_IDENTITY = 2;
 constexpr u32 ST_AGG = 1u << 2, ST_INC = 2u << 2;
 
 constexpr int HALO_LO = 4, HALO_HI = 1;                       // extra limbs before / after a tile
-constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 1024
-constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 1029
-constexpr int SM_COEF = 4 * SM_LIMBS;                         // 4116
+constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 512
+constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 517
+constexpr int SM_COEF = 4 * SM_LIMBS;                         // 2068
 constexpr int SM_LIMBS_PAD = SM_LIMBS + 1;                    // whole 16-byte chunks
 
 struct Limb {
@@ -130,7 +130,7 @@ __device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long 
 
 // VEC: coef and b are 16-byte aligned (staged with cp.async), else plain loads.
 // Digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS) of tile tt
-// (J0 = 1024 tt - 4) into cs / bs; positions outside the operands read 0.
+// (J0 = TILE_LIMBS tt - 4) into cs / bs; positions outside the operands read 0.
 template <bool VEC>
 __device__ __forceinline__ void stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs) {
     const long long J0 = tt * TILE_LIMBS - HALO_LO;

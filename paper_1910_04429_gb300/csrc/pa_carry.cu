@@ -4,7 +4,7 @@
 // significant bits; Eq. 7). The per-limb sums u_j and their carry chain of
 // generate / propagate pairs are defined in carry.cuh.
 //
-// One kernel over the tiles of 1024 limbs that hold output limbs (from limb
+// One kernel over the tiles of 512 limbs that hold output limbs (from limb
 // (n - m) / 64 up; the limbs below matter only through the carry into the
 // first of them). Each CTA takes the next such tile from an atomic ticket (so
 // every earlier tile has started), stages its digits and addend limbs in
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
         publish(&state[t], (t == 0 ? ST_INC : ST_AGG) | (u32)total);
         int decided = 0, cin = 0;
         if (ticket_start == 0) {
-            Limb h[2];  // limbs 1024 t - 2 and 1024 t - 1 (zero below limb 0)
+            Limb h[2];  // limbs TILE_LIMBS t - 2 and TILE_LIMBS t - 1 (zero below limb 0)
             limbs_u<2>(cs, bs, HALO_LO - 2, h);
             if (!(h[1].gp & 2)) decided = 1, cin = h[1].gp & 1;  // generate or kill
             else if (!(h[0].gp & 2)) decided = 1, cin = h[0].gp & 1;

@@ -66,7 +66,7 @@ struct CarryBatch {
     CarryJob job[B];
 };
 constexpr int CARRY_THREADS = 256;
-constexpr int CARRY_LIMBS = 4;  // limbs per thread
+constexpr int CARRY_LIMBS = 2;  // limbs per thread (4 measured slower: longer per-thread chains)
 constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
 constexpr u32 CARRY_SPIN_LIMIT = 1u << 20;  // polls of a predecessor tile before giving up (~0.1-1 s)
 constexpr u32 PA_STATUS_TIMEOUT = 1u;       // device status bit: a bounded wait ran out
