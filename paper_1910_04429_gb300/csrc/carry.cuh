@@ -31,9 +31,9 @@ constexpr int GP_IDENTITY = 2;
 constexpr u32 ST_AGG = 1u << 2, ST_INC = 2u << 2;
 
 constexpr int HALO_LO = 4, HALO_HI = 1;                       // extra limbs before / after a tile
-constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 512
-constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 517
-constexpr int SM_COEF = 4 * SM_LIMBS;                         // 2068
+constexpr int TILE_LIMBS = CARRY_THREADS * CARRY_LIMBS;       // 256
+constexpr int SM_LIMBS = TILE_LIMBS + HALO_LO + HALO_HI;      // 261
+constexpr int SM_COEF = 4 * SM_LIMBS;                         // 1044
 constexpr int SM_LIMBS_PAD = SM_LIMBS + 1;                    // whole 16-byte chunks
 
 struct Limb {

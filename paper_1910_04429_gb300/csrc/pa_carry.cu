@@ -4,7 +4,7 @@
 // significant bits; Eq. 7). The per-limb sums u_j and their carry chain of
 // generate / propagate pairs are defined in carry.cuh.
 //
-// One kernel over the tiles of 512 limbs that hold output limbs (from limb
+// One kernel over the tiles of 256 limbs that hold output limbs (from limb
 // (n - m) / 64 up; the limbs below matter only through the carry into the
 // first of them). Each CTA takes the next such tile from an atomic ticket (so
 // every earlier tile has started), stages its digits and addend limbs in

@@ -218,7 +218,7 @@ static int fb_grid(int dev) {  // CTAs that can all be resident at once
                 cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;
-        cached[dev] = (per_sm < 2 ? per_sm : 2) * sms;
+        cached[dev] = (per_sm < 4 ? per_sm : 4) * sms;
     }
     return cached[dev];
 }

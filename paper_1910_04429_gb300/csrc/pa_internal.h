@@ -65,8 +65,9 @@ struct CarryBatch {
     int count;
     CarryJob job[B];
 };
-constexpr int CARRY_THREADS = 256;
+constexpr int CARRY_THREADS = 128;
 constexpr int CARRY_LIMBS = 2;  // limbs per thread (4 measured slower: longer per-thread chains)
+// (tiles of 256 limbs: 128 x 2 measured ahead of 256 x 2 and 256 x 1)
 constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
 constexpr u32 CARRY_SPIN_LIMIT = 1u << 20;  // polls of a predecessor tile before giving up (~0.1-1 s)
 constexpr u32 PA_STATUS_TIMEOUT = 1u;       // device status bit: a bounded wait ran out

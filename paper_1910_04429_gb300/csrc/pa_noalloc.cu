@@ -34,7 +34,9 @@ constexpr u64 NA_MAX_N = 1ull << NA_MAX_LOGN;
 constexpr int NA_LOGN0 = LOG_TILE;                       // smallest transform, 2^12
 constexpr int NA_SIZES = NA_MAX_LOGN - NA_LOGN0 + 1;
 constexpr u64 NA_TABLE_WORDS = 4 * 4096 + 2 * (NA_MAX_N >> 12);
-constexpr u64 NA_CARRY_BYTES = 256;                      // carry tile states (17 words used)
+constexpr u64 NA_CARRY_BYTES = 1024;                     // carry tile states, ticket, flag
+static_assert(((PA_NOALLOC_MAX_BITS + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS * 4 + 8 <= NA_CARRY_BYTES,
+              "carry-state scratch too small for the cap");
 
 static_assert(PA_NOALLOC_MAX_BITS <= 16 * (NA_MAX_N / 2), "transform too short for the cap");
 

@@ -142,7 +142,7 @@ def test_workspace_bytes(n, N):
     max(4096, 2 ceil(n/16) - 1): the exact recomputation behind a wrapped
     product runs at that length, which covers the full-length product (2^k or
     3 * 2^k) too; and two carry-state sets (tile states, ticket, flag)."""
-    tiles = -(-(-(-n // 64)) // 512)
+    tiles = -(-(-(-n // 64)) // 256)
     assert binding.workspace_bytes(n) == 2 * N * 8 + 2 * 4 * (tiles + 2)
     assert binding.workspace_bytes(0) == 0
 

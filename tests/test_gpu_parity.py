@@ -133,7 +133,7 @@ def _carry_ref(coef, b_int, n, m):
 
 @pytest.mark.parametrize("pattern", ["random64", "all_ffff", "propagate", "max"])
 def test_carry_extract(pattern):
-    """Carry chains inside and across carry tiles (512 limbs per tile)."""
+    """Carry chains inside and across carry tiles (256 limbs per tile)."""
     import torch
 
     n = 64 * 1024 * 5 + 48
@@ -161,7 +161,7 @@ def test_carry_extract(pattern):
 
 @pytest.mark.parametrize("pattern", ["gen_prop", "gen_prop_prop", "kill_prop_prop"])
 def test_carry_decided_at_tile_boundaries(pattern):
-    """Carries into the carry tiles (512 limbs each) at limbs T = 512 t: limb
+    """Carries into the carry tiles (256 limbs each) at limbs T = 256 t: limb
     T-2 generates and T-1 propagates (the tile's own halo decides), or T-3
     generates / kills and T-2, T-1 propagate (the tile must look back at its
     predecessor)."""
@@ -173,7 +173,7 @@ def test_carry_decided_at_tile_boundaries(pattern):
     coef = np.zeros(L, dtype=np.uint64)
     b = np.zeros(Ly, dtype=np.uint64)
     ones = np.uint64(0xFFFFFFFFFFFFFFFF)
-    for T in (512, 1024, 1536, 2048, 4096):
+    for T in (256, 768, 1024, 1536, 2048, 4096):
         if pattern == "gen_prop":
             g = T - 2  # u_g = 2^64: f_(g-1) = 1 (hi(V_(g-2)) = 1, lo(V_(g-1)) = 2^64 - 1), e_g = 2^64 - 1
             coef[4 * (g - 2) + 3] = 65536
@@ -193,8 +193,8 @@ def test_carry_decided_at_tile_boundaries(pattern):
 def test_carry_walk_back_below_output(case):
     """Only the carry tiles holding output limbs run; the first of them composes
     the tiles below it when its halo propagates. b all ones (every limb
-    propagates) with a generate at limb 5: the carry ripples through 14 tiles
-    of 512 limbs into the output; a kill at limb 3000 stops it; no generate at
+    propagates) with a generate at limb 5: the carry ripples through 28 tiles
+    of 256 limbs into the output; a kill at limb 3000 stops it; no generate at
     all walks back to limb 0; and an output range starting mid-tile."""
     import torch
 
