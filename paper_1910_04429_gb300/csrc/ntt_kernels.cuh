@@ -17,6 +17,15 @@
 
 namespace pa {
 
+// The first kernel of a product clears the carry states in CTA (0, 0), after
+// the dependent-launch wait, in place of a memset before it: the carry step
+// runs after every transform kernel has completed.
+template <int B>
+__device__ __forceinline__ void clear_states(const NttBatch<B>& nb, int nthreads) {
+    if (nb.zero_words && blockIdx.x == 0 && blockIdx.y == 0)
+        for (u32 i = threadIdx.x; i < nb.zero_words; i += nthreads) nb.zero[i] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // asynchronous staging of tile inputs (cp.async, 16-byte chunks)
 // ---------------------------------------------------------------------------
@@ -63,6 +72,7 @@ template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     pdl_begin();
+    clear_states(nb, NT);
     using S = Strided<RA, RB, C>;
     using SZ = StageSize<S::R, C, PACK>;
     extern __shared__ __align__(16) u64 dsm[];
@@ -211,6 +221,7 @@ __global__ void __launch_bounds__(NT) k_contig_seed(const __grid_constant__ NttB
 template <bool PACK, int B>
 __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ NttBatch<B> nb, Twiddles tw) {
     pdl_begin();
+    clear_states(nb, NT);
     __shared__ u64 sm[TILE_SM];
     const BlockIO& io = nb.io[blockIdx.y];
     u64 base = (u64)blockIdx.x * TILE;
@@ -247,6 +258,7 @@ template <bool PACK, int B>
 __global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ NttBatch<B> nb, u64 ninv,
                                                     Twiddles tw) {
     pdl_begin();
+    clear_states(nb, NT);
     extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
     u64* ah = dsm + TILE_SM;
@@ -288,6 +300,7 @@ __device__ __forceinline__ void bar_sync_half() {  // named barrier 1 over NT th
 static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_constant__ NttBatch<1> nb, u64 ninv,
                                                           Twiddles tw) {
     pdl_begin();
+    clear_states(nb, 2 * NT);
     extern __shared__ __align__(16) u64 dsm[];
     const int h = threadIdx.x / NT, t = threadIdx.x % NT;  // half 0: a, half 1: x
     u64* sm = dsm + h * TILE_SM;
@@ -465,11 +478,17 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
                   !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
+    // only the first launch clears the carry states
+    NttBatch<B> later = nb;
+    later.zero = nullptr;
+    later.zero_words = 0;
+    const NttBatch<B>* cur = &nb;
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, tw, p, narrow);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow}.dispatch_fwd(G.pass[p].R, p == 0);
+        Launcher<B>{&g, cur, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow}.dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
+        cur = &later;
     }
     dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
     bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
@@ -481,7 +500,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
             constexpr size_t smem = (2 * TILE_SM + TILE) * sizeof(u64);
             prof_begin(st, "ntt_contig_both");
             allow_smem(k_contig_pair, smem);
-            launch_pdl(k_contig_pair, tiles, dim3(2 * NT), smem, st, nb, ninv, tw);
+            launch_pdl(k_contig_pair, tiles, dim3(2 * NT), smem, st, *cur, ninv, tw);
             prof_end(st);
             paired = true;
         }
@@ -492,24 +511,24 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
         prof_begin(st, "ntt_contig_both");
         if (pack) {
             allow_smem(k_contig_both<true, B>, smem);
-            launch_pdl(k_contig_both<true, B>, tiles, dim3(NT), smem, st, nb, ninv, tw);
+            launch_pdl(k_contig_both<true, B>, tiles, dim3(NT), smem, st, *cur, ninv, tw);
         } else {
             allow_smem(k_contig_both<false, B>, smem);
-            launch_pdl(k_contig_both<false, B>, tiles, dim3(NT), smem, st, nb, ninv, tw);
+            launch_pdl(k_contig_both<false, B>, tiles, dim3(NT), smem, st, *cur, ninv, tw);
         }
         prof_end(st);
     } else if (!paired) {
         prof_begin(st, "ntt_contig_fused");
         if (pack)
-            launch_pdl(k_contig_fused<true, B>, tiles, dim3(NT), 0, st, nb, tw);
+            launch_pdl(k_contig_fused<true, B>, tiles, dim3(NT), 0, st, *cur, tw);
         else
-            launch_pdl(k_contig_fused<false, B>, tiles, dim3(NT), 0, st, nb, tw);
+            launch_pdl(k_contig_fused<false, B>, tiles, dim3(NT), 0, st, *cur, tw);
         prof_end(st);
     }
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, tw, p, narrow);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        Launcher<B>{&g, &nb, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow}.dispatch_inv(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &later, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow}.dispatch_inv(G.pass[p].R, p == 0);
         prof_end(st);
     }
     return cudaGetLastError();

@@ -378,8 +378,8 @@ int fallback_job(int dev, uint64_t n, uint64_t m, const Digits& dx, const Digits
     return PA_OK;
 }
 
-// Plans, twiddle tables, buffers and the zeroed carry states (queued on st
-// now, before any transform).
+// Plans, twiddle tables, buffers and the carry states (cleared by the first
+// transform kernel).
 int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, cudaStream_t st,
                  Scratch& scr, int dev, HashPlan* hp) {
     hp->wp = wrap_for(n, m);
@@ -398,8 +398,11 @@ int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64
                                         hp->state + carry_state_words(n), hp->state + carry_flag_word(n),
                                         &hp->fb)))
         return rc;
-    cudaError_t e = cudaMemsetAsync(sp, 0, state_words * sizeof(u32), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
+    // no memset between this hash and the previous one on the stream: the
+    // first transform kernel clears the states
+    hp->prod.zero = hp->state;
+    hp->prod.zero_words = (u32)state_words;
+    (void)st;
     return PA_OK;
 }
 
@@ -1028,9 +1031,10 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
             (rc = scr.get(state_words * sizeof(u32), &sp)))
             return rc;
         u32* state = (u32*)sp;
-        cudaError_t e = cudaMemsetAsync(sp, 0, state_words * sizeof(u32), st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(carry states)");
+        cudaError_t e;
         NttJob j;
+        j.zero = state;  // cleared by the first transform kernel
+        j.zero_words = (u32)state_words;
         j.geom = ss->G;
         j.L = (n + 15) / 16;
         if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;

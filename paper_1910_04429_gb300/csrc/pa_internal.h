@@ -18,6 +18,8 @@ struct NttJob {
                   // register order, times N^-1)
     Digits dx, da;
     u64 L;        // live product digits kept by the last inverse pass
+    u32* zero = nullptr;  // words the first kernel clears (the carry states), or null
+    u32 zero_words = 0;
 };
 
 // Launches: digits of x and a -> convolution digits c_k (k < L) in buf_x.
@@ -38,6 +40,8 @@ constexpr int MAX_BATCH = 32;  // blocks per launch (kernel parameter array)
 template <int B>
 struct NttBatch {
     int count;
+    u32* zero;        // words the launch's CTA (0, 0) clears first (the carry states that
+    u32 zero_words;   // the carry step reads after the transforms), or 0 words
     BlockIO io[B];
 };
 // Launches the transforms of `count` blocks of geometry G, MAX_BATCH blocks per launch.

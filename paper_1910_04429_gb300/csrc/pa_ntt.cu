@@ -26,6 +26,8 @@ cudaError_t launch_pass_twiddles(const Twiddles& tw, u64 N, u64 M, u64 S, u64* o
 cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;
+    nb.zero = j.zero;
+    nb.zero_words = j.zero_words;
     nb.io[0] = BlockIO{j.buf_x, j.buf_a, j.dx, j.da, j.L};
     return launch_batch<1>(j.geom, j.tw, nb, st);
 }
@@ -36,6 +38,8 @@ cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
 cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;
+    nb.zero = nullptr;
+    nb.zero_words = 0;
     nb.io[0] = BlockIO{j.buf_a, j.buf_a, j.da, j.da, j.L};
     bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.one_bit;
     const Geom& G = j.geom;
@@ -61,6 +65,8 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
 cudaError_t launch_convolution_seeded(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;
+    nb.zero = j.zero;
+    nb.zero_words = j.zero_words;
     nb.io[0] = BlockIO{j.buf_x, j.buf_a, j.dx, j.da, j.L};
     return launch_batch<1>(j.geom, j.tw, nb, st, 1);
 }

@@ -9,6 +9,8 @@ cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const Bl
     for (int i = 0; i < count; i += MAX_BATCH) {
         NttBatch<MAX_BATCH> nb;
         nb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
+        nb.zero = nullptr;  // a batch clears its carry states with one memset
+        nb.zero_words = 0;
         for (int k = 0; k < nb.count; k++) nb.io[k] = io[i + k];
         cudaError_t e = launch_batch<MAX_BATCH>(G, tw, nb, st);
         if (e != cudaSuccess) return e;

@@ -59,3 +59,32 @@ def test_random_batches():
     for b, t in zip(blks, tensors):
         want = oracle.pa_hash(b.x, b.a, b.b, b.n, b.m, threads=oracle.default_threads())
         np.testing.assert_array_equal(host(t[5]), want, err_msg=f"n={b.n} m={b.m}")
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_random_sizes_wrapped(mode):
+    """Wrapped products at random sizes from 1e5 to 5e6 bits (log-uniform) with
+    random m up to 0.6 n (mode 2:
+    wherever a shorter length is certifiable; mode 3: the certificate forced to
+    fail, so every hash also runs the recomputation), against the oracle; in
+    mode 2 no certificate fails on these uniform inputs."""
+    prev = binding.wrap_mode(mode)
+    try:
+        binding.wrap_flags(clear=True)
+        wrapped = 0
+        u = inputs.uniforms(4242 + mode, 48)
+        sizes = [(int(math.exp(math.log(1e5) + float(u[2 * i]) * math.log(50.0))), float(u[2 * i + 1]))
+                 for i in range(24)]
+        for n, r in sizes:
+            m = max(1, int(r * 0.6 * n))
+            if binding.plan_info(n, m)["dropped"] == 0:
+                continue
+            wrapped += 1
+            blk = inputs.make_block(n, m, seed=n + 3 * m)
+            got = gpu_hash(binding, blk.x, blk.a, blk.b, n, m)
+            want = oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads())
+            np.testing.assert_array_equal(got, want, err_msg=f"n={n} m={m} mode={mode}")
+        assert wrapped >= 16
+        assert binding.wrap_flags() == (wrapped if mode == 3 else 0)
+    finally:
+        binding.wrap_mode(prev)
