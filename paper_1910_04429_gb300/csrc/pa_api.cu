@@ -387,14 +387,16 @@ int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64
     const Geom fg = fallback_geom(n);
     const u64 words = hp->wp.on ? (fg.N > first.N ? fg.N : first.N) : first.N;
     int rc;
-    void *bx, *ba, *sp;
-    if ((rc = scr.get(words * sizeof(u64), &bx)) || (rc = scr.get(words * sizeof(u64), &ba))) return rc;
-    hp->prod = product_job(first, (u64*)bx, (u64*)ba, key, seed_a, n);
-    if ((rc = get_tables(dev, first, &hp->prod.tw))) return rc;
+    // one pool allocation per hash: both transform buffers, then the carry states
     const size_t state_words = (hp->wp.on ? 2 : 1) * carry_state_words(n);
-    if ((rc = scr.get(state_words * sizeof(u32), &sp))) return rc;
-    hp->state = (u32*)sp;
-    if (hp->wp.on && (rc = fallback_job(dev, n, m, hp->prod.dx, hp->prod.da, (u64*)bx, (u64*)ba,
+    void* ws;
+    if ((rc = scr.get(2 * words * sizeof(u64) + state_words * sizeof(u32), &ws))) return rc;
+    u64* bx = (u64*)ws;
+    u64* ba = bx + words;
+    hp->prod = product_job(first, bx, ba, key, seed_a, n);
+    if ((rc = get_tables(dev, first, &hp->prod.tw))) return rc;
+    hp->state = (u32*)(ba + words);
+    if (hp->wp.on && (rc = fallback_job(dev, n, m, hp->prod.dx, hp->prod.da, bx, ba,
                                         hp->state + carry_state_words(n), hp->state + carry_flag_word(n),
                                         &hp->fb)))
         return rc;
