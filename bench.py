@@ -195,7 +195,7 @@ def alu_ops(name: str, N: int):
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
 # launch at n = 10^8), valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 157.9e6, "src_sha": "8c98ec3deb0c832b",
+TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 158.0e6, "src_sha": "2409fecd4e4a973e",
            "profile": "profiles/k_contig_both_n1e8.md"}
 
 
