@@ -380,8 +380,8 @@ int fallback_job(int dev, uint64_t n, uint64_t m, const Digits& dx, const Digits
 
 // Plans, twiddle tables, buffers and the carry states (cleared by the first
 // transform kernel).
-int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, cudaStream_t st,
-                 Scratch& scr, int dev, HashPlan* hp) {
+int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, Scratch& scr, int dev,
+                 HashPlan* hp) {
     hp->wp = wrap_for(n, m);
     const Geom first = hp->wp.on ? plan_for_base(dev, hp->wp.geom) : plan_for(dev, n);
     const Geom fg = fallback_geom(n);
@@ -404,7 +404,6 @@ int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64
     // first transform kernel clears the states
     hp->prod.zero = hp->state;
     hp->prod.zero_words = (u32)state_words;
-    (void)st;
     return PA_OK;
 }
 
@@ -433,7 +432,7 @@ int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* see
                 uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool) {
     Scratch scr(st, pool);
     HashPlan hp;
-    int rc = hash_prepare(key, seed_a, n, m, st, scr, dev, &hp);
+    int rc = hash_prepare(key, seed_a, n, m, scr, dev, &hp);
     if (!rc) rc = hash_product(hp, st);
     if (!rc) rc = hash_finish(hp, seed_b, n, m, out, st);
     return rc;
@@ -613,7 +612,7 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
         }
         void* mo = nullptr;
         HashPlan hp;
-        rc = hash_prepare((const u64*)dx, (const u64*)da, n, m, st, scr, dev, &hp);
+        rc = hash_prepare((const u64*)dx, (const u64*)da, n, m, scr, dev, &hp);
         if (rc || (e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
             cudaStreamWaitEvent(st, d.b_ready, 0);
             return rc ? rc : cuda_fail(e, "cudaStreamWaitEvent");
