@@ -301,7 +301,75 @@ GL_HD void dft_fwd_upper_zero(u64* v) {
     }
 }
 
-// In-register DFT of length R in {1, 2, 3, 4, 6, 8}, natural order in and out:
+// Roots for the lengths 5 * 2^k. w40_pow(e) = w_40^e for the 40th root w_40 that
+// every transform of length 5 * 2^k uses (w_N^(N/40); the transform roots come
+// from a fixed (15 * 2^32)-th root W with W^(5 * 2^26) = 2, and w_40 =
+// W^(3 * 2^29)); w_40^(5 i) = 2^(24 i), consistent with the power-of-two roots
+// of the other steps. Values checked on the host against that construction.
+GL_HD constexpr u64 w40_pow(int e) {
+    constexpr u64 t[40] = {
+        0x0000000000000001ull, 0xd850dddf7d0e7367ull, 0x8ee62dc0237ef6b1ull, 0x0cadbf02e30803a7ull,
+        0xecf1f86a7562be2bull, 0x0000000001000000ull, 0xe0555f506627af23ull, 0xc0b26523b07119d3ull,
+        0x02efb5c2a6f35241ull, 0x6b6254b62a130e08ull, 0x0001000000000000ull, 0x51467d0e221faaa1ull,
+        0x2471237ed23f4d9bull, 0xc2a9e30740fd104bull, 0xb695756207949dacull, 0x000000ffffffff00ull,
+        0x0e736627a0aeb983ull, 0x7ef6b0709adb8eddull, 0x0803a6f34a3d561dull, 0x62be2a12ab496a8bull,
+        0xffffffff00000000ull, 0x27af221f82f18c9aull, 0x7119d23edc810950ull, 0xf35240fc1cf7fc5aull,
+        0x130e07948a9d41d6ull, 0xfffffffeff000001ull, 0x1faaa0ae99d850deull, 0x3f4d9adb4f8ee62eull,
+        0xfd104a3c590cadc0ull, 0x949dab48d5ecf1f9ull, 0xfffeffff00000001ull, 0xaeb982f0dde05560ull,
+        0xdb8edc802dc0b266ull, 0x3d561cf7bf02efb6ull, 0x496a8a9cf86b6255ull, 0xfffffeff00000101ull,
+        0xf18c99d75f51467eull, 0x81094f8e65247124ull, 0xf7fc590bb5c2a9e4ull, 0x9d41d5ec54b69576ull,
+};
+    return t[e];
+}
+// Constants of the 5-point DFT with w = w_5 = w40_pow(8): with alpha = (w + w^4)/2,
+// beta = (w^2 + w^3)/2, gamma = (w - w^4)/2, delta = (w^2 - w^3)/2 (alpha + beta
+// = -1/2): K1 = (alpha - beta)/2, and gamma, gamma + delta, delta - gamma.
+constexpr u64 DFT5_K1 = 0xaf3f49212a5a0254ull;
+constexpr u64 DFT5_GA = 0x13b06ca0bc994feeull;
+constexpr u64 DFT5_GPD = 0x91631be9c7a20bc5ull;
+constexpr u64 DFT5_DMG = 0x6a0242a84e6f6be9ull;
+
+// x * w_40^e: a shift where w_40^e is a power of two (e a multiple of 5), else
+// a product by the constant.
+template <int E>
+GL_HD u64 mul_w40(u64 x) {
+    constexpr int e = ((E % 40) + 40) % 40;
+    if constexpr (e % 5 == 0) return shl_v(x, 24 * (e / 5));
+    else return mul(x, w40_pow(e));
+}
+
+// RowRoots for R in {10, 20, 40} (R not a divisor of 192): v[k] <- v[k] * w_R^(j k),
+// w_R = w_40^(40/R), for a run-time row j < J uniform across a warp.
+template <int R, bool INV, int K, int J>
+struct RowRoots40 {
+    template <int k>
+    static GL_HD void one(u64* v) {
+        constexpr int e = (40 / R) * (J - 1) * k;
+        v[k] = mul_w40<INV ? -e : e>(v[k]);
+        if constexpr (k + 1 < K) one<k + 1>(v);
+    }
+    static GL_HD void apply(u64* v, int j) {
+        if (j == J - 1) {
+            if constexpr (K > 1) one<1>(v);
+        } else {
+            RowRoots40<R, INV, K, J - 1>::apply(v, j);
+        }
+    }
+};
+template <int R, bool INV, int K>
+struct RowRoots40<R, INV, K, 1> {  // row 0: w^0 = 1
+    static GL_HD void apply(u64*, int) {}
+};
+
+// The middle roots of a radix-R step: power-of-two shifts when R divides 192,
+// else products by the w_40 constants.
+template <int R, bool INV, int K, int J>
+GL_HD void row_roots(u64* v, int j) {
+    if constexpr (192 % R == 0) RowRoots<R, INV, K, J>::apply(v, j);
+    else RowRoots40<R, INV, K, J>::apply(v, j);
+}
+
+// In-register DFT of length R in {1, 2, 3, 4, 5, 6, 8}, natural order in and out:
 // v[k] <- sum_j v[j] w^(jk), w = 2^(192/R) (or its inverse), no 1/R scaling.
 // The inverse is the forward DFT read backwards (sum_j v[j] w^(-jk) is the
 // forward output R - k), which keeps every root a cheap forward shift.
@@ -358,6 +426,25 @@ GL_HD void dft_fwd(u64* v) {
             v[2 * k] = s[k];
             v[2 * k + 1] = t[k];
         }
+    } else if constexpr (R == 5) {
+        // Winograd's form: with a1 = v1 + v4, b1 = v1 - v4, a2 = v2 + v3,
+        // b2 = v2 - v3, s = a1 + a2: X0 = v0 + s, and from base = v0 - s/4,
+        // m1 = K1 (a1 - a2), P = gamma b1 + delta b2, Q = delta b1 - gamma b2
+        // (three products): X1 = base + m1 + P, X4 = base + m1 - P,
+        // X2 = base - m1 + Q, X3 = base - m1 - Q
+        u64 a1 = add(v[1], v[4]), b1 = sub(v[1], v[4]), a2 = add(v[2], v[3]), b2 = sub(v[2], v[3]);
+        u64 s = add(a1, a2), x0 = v[0];
+        u64 m1 = mul(sub(a1, a2), DFT5_K1);
+        u64 base = sub(x0, shl_v(s, 190));  // s * 2^-2
+        u64 ma = mul(sub(b1, b2), DFT5_GA);
+        u64 pp = add(ma, mul(b2, DFT5_GPD));
+        u64 qq = add(mul(b1, DFT5_DMG), ma);
+        u64 bp = add(base, m1), bm = sub(base, m1);
+        v[0] = add(x0, s);
+        v[1] = add(bp, pp);
+        v[4] = sub(bp, pp);
+        v[2] = add(bm, qq);
+        v[3] = sub(bm, qq);
     } else if constexpr (R == 8) {
         // one radix-2 decimation-in-frequency step, then two length-4 DFTs:
         // X[2k] = DFT4(v_i + v_{i+4}), X[2k+1] = DFT4((v_i - v_{i+4}) w^i)

@@ -342,7 +342,7 @@ static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_c
 #define PA_RADIX_TABLE(X)                                                                  \
     X(2, 1, 2, 2048) X(4, 2, 2, 1024) X(8, 2, 4, 512) X(16, 4, 4, 256) X(32, 4, 8, 128)     \
     X(64, 8, 8, 64) X(3, 3, 1, 1024) X(6, 3, 2, 512) X(12, 3, 4, 256) X(24, 3, 8, 128)      \
-    X(48, 6, 8, 64)
+    X(48, 6, 8, 64) X(5, 5, 1, 512) X(10, 5, 2, 256) X(20, 5, 4, 128) X(40, 5, 8, 64)
 
 inline int strided_columns(int R) {
 #define PA_COLS(r, a, b, c) if (R == r) return c;
@@ -492,7 +492,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     }
     dim3 tiles((unsigned)(G.N / TILE), (unsigned)nb.count);
     bool pack = G.nstrided == 0;  // a single 4096-word tile reads the digits itself
-    u64 ninv = n_inverse(G.logN, G.three);
+    u64 ninv = n_inverse(G.logN, G.odd);
     bool paired = false;
     if constexpr (B == 1) {
         if (ops == 2 && narrow && !pack) {

@@ -128,7 +128,7 @@ struct Strided {
         } else {
             gl::dft<RB, false>(v);
         }
-        gl::RowRoots<R, false, RB, RA>::apply(v, j0);
+        gl::row_roots<R, false, RB, RA>(v, j0);
 #pragma unroll
         for (int kr = 0; kr < RB; kr++) sm[(kr * RA + j0) * C + c] = v[kr];
     }
@@ -160,7 +160,7 @@ struct Strided {
         } else {
             gl::dft<RB, false>(v);
         }
-        gl::RowRoots<R, false, RB, RA>::apply(v, j0);
+        gl::row_roots<R, false, RB, RA>(v, j0);
 #pragma unroll
         for (int kr = 0; kr < RB; kr++) sm[(kr * RA + j0) * C + c] = v[kr];
     }
@@ -238,7 +238,7 @@ struct Strided {
         u64 v[RB];
 #pragma unroll
         for (int kr = 0; kr < RB; kr++) v[kr] = sm[(kr * RA + j0) * C + c];
-        gl::RowRoots<R, true, RB, RA>::apply(v, j0);
+        gl::row_roots<R, true, RB, RA>(v, j0);
         gl::dft<RB, true>(v);
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {

@@ -87,9 +87,9 @@ int get_base_tables(int dev, const Geom& G, Twiddles* tw) {
     size_t base_words = table_words_n(G.N);
     if (it == d.tables.end()) {
         std::vector<u64> host;
-        make_tables(G.logN, host, G.three);
+        make_tables(G.logN, host, G.odd);
         // then w_4096^t * N^-1: the seed's tile pass scales by N^-1 through its twiddles
-        u64 ninv = n_inverse(G.logN, G.three);
+        u64 ninv = n_inverse(G.logN, G.odd);
         host.resize(base_words + 4096);
         for (size_t i = 0; i < 4096; i++) host[base_words + i] = gl::mul(host[i], ninv);
         cudaError_t e = cudaMalloc(&p, host.size() * sizeof(u64));
@@ -163,7 +163,7 @@ Geom geom_for_bits(uint64_t n) { return choose_geom((n + 15) / 16); }
 // Plan variants that change anything for this transform length.
 int applicable_variants(const Geom& g) {
     if (g.nstrided == 0) return 0;
-    int R0 = (g.three ? 3 : 1) << ((g.logN - LOG_TILE) % 6);
+    int R0 = g.odd << ((g.logN - LOG_TILE) % 6);
     return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV |
            (g.nstrided == 1 && g.N / TILE <= 64 ? PLAN_NARROW : 0);
 }
@@ -179,7 +179,7 @@ Geom plan_for_base(int dev, const Geom& base) {
         auto t = d.tuned.find(base.N);
         if (t != d.tuned.end()) v = t->second;
     }
-    return make_geom(base.logN, base.three, v & applicable_variants(base));
+    return make_geom(base.logN, base.odd, v & applicable_variants(base));
 }
 
 // ... for keys of n bits (the modular hash)
@@ -373,7 +373,7 @@ int fallback_job(int dev, uint64_t n, uint64_t m, const Digits& dx, const Digits
     f->wloi = t.wloi;
     f->whi = t.whi;
     f->whii = t.whii;
-    f->ninv = n_inverse(fg.logN, 0);
+    f->ninv = n_inverse(fg.logN, fg.odd);
     f->state = state;
     return PA_OK;
 }

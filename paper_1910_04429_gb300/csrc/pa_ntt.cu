@@ -54,9 +54,9 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     dim3 tiles((unsigned)(G.N / TILE), 1);
     prof_begin(st, "ntt_contig_seed");
     if (G.nstrided == 0)
-        launch_pdl(k_contig_seed<true, 1>, tiles, dim3(NT), 0, st, nb, n_inverse(G.logN, G.three), j.tw);
+        launch_pdl(k_contig_seed<true, 1>, tiles, dim3(NT), 0, st, nb, n_inverse(G.logN, G.odd), j.tw);
     else
-        launch_pdl(k_contig_seed<false, 1>, tiles, dim3(NT), 0, st, nb, n_inverse(G.logN, G.three), j.tw);
+        launch_pdl(k_contig_seed<false, 1>, tiles, dim3(NT), 0, st, nb, n_inverse(G.logN, G.odd), j.tw);
     prof_end(st);
     return cudaGetLastError();
 }

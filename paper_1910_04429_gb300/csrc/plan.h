@@ -19,7 +19,7 @@ struct PassDesc {
 
 struct Geom {
     int logN = 0;    // log2 of the power-of-two part of N
-    int three = 0;   // 1: N = 3 * 2^logN, 0: N = 2^logN
+    int odd = 1;     // N = odd * 2^logN, odd in {1, 3, 5}
     uint64_t N = 0;
     int nstrided = 0;
     PassDesc pass[8];
@@ -35,18 +35,18 @@ constexpr int PLAN_DIRECT_INV = 4;  // inverse strided passes load their tiles d
 constexpr int PLAN_NARROW = 8;      // single-pass plans, single blocks: tiles of a quarter of the columns
 constexpr int PLAN_VARIANTS = 16;
 
-// N = R_0 * 64^q * 4096 with N = 2^logN (R_0 = 2^((logN-12) mod 6), omitted when
-// 1) or N = 3 * 2^logN (R_0 = 3 * 2^((logN-12) mod 6), which must be <= 48):
-// one strided pass of radix R_0, then q strided passes of radix 64, then the
-// contiguous 4096-element pass.
-inline Geom make_geom(int logN, int three = 0, int variant = 0) {
+// N = R_0 * 64^q * 4096 with N = odd * 2^logN and R_0 = odd * 2^((logN-12) mod 6)
+// (omitted when 1; at most 48 for odd = 3, 40 for odd = 5): one strided pass of
+// radix R_0, then q strided passes of radix 64, then the contiguous
+// 4096-element pass.
+inline Geom make_geom(int logN, int odd = 1, int variant = 0) {
     Geom g;
     g.logN = logN;
-    g.three = three;
+    g.odd = odd;
     g.variant = variant;
-    g.N = (three ? 3ull : 1ull) << logN;
+    g.N = (uint64_t)odd << logN;
     int rem = (logN - LOG_TILE) % 6, q = (logN - LOG_TILE) / 6;
-    int R0 = (three ? 3 : 1) << rem;
+    int R0 = odd << rem;
     int radix[8], nr = 0;
     if (R0 > 1 && !(variant & PLAN_R0_LAST)) radix[nr++] = R0;
     for (int i = 0; i < q; i++) radix[nr++] = 64;
@@ -69,16 +69,27 @@ inline int logn_for_digits(uint64_t L) {
     return k;
 }
 
-// The shortest transform, 2^k or 3 * 2^k (with a first radix of at most 48),
-// of at least `need` points (and at least one 4096-point tile).
+// Whether odd * 2^j (j >= 12) is a transform length here: its first radix
+// odd * 2^((j-12) mod 6) is at most 48 (odd = 3) or 40 (odd = 5).
+inline bool length_ok(int odd, int j) {
+    if (j < LOG_TILE) return false;
+    int rem = (j - LOG_TILE) % 6;
+    return odd == 1 || (odd == 3 && rem <= 4) || (odd == 5 && rem <= 3);
+}
+
+// The shortest transform, 2^k, 3 * 2^k or 5 * 2^k (with the first radix
+// bounds above), of at least `need` points (and at least one 4096-point tile).
 inline Geom choose_geom_len(uint64_t need) {
     int k = LOG_TILE;
     while ((1ull << k) < need) k++;
-    for (int j = LOG_TILE; j < k; j++) {
-        bool fits = (3ull << j) >= need && (3ull << j) < (1ull << k);
-        if (fits && (j - LOG_TILE) % 6 <= 4) return make_geom(j, 1);
-    }
-    return make_geom(k, 0);
+    Geom best = make_geom(k, 1);
+    for (int odd : {3, 5})
+        for (int j = LOG_TILE; j < k; j++)
+            if (length_ok(odd, j) && ((uint64_t)odd << j) >= need && ((uint64_t)odd << j) < best.N) {
+                best = make_geom(j, odd);
+                break;
+            }
+    return best;
 }
 
 // ... that holds the linear convolution of two L-digit operands.
@@ -144,14 +155,18 @@ inline WrapPlan wrap_plan(uint64_t n, uint64_t m, uint64_t min_full = WRAP_MIN_F
     return wp;
 }
 
-// A primitive (3 * 2^32)-th root of unity R with R^(2^26) = 2: every
-// w_N = R^(3 * 2^32 / N) then satisfies w_N^(N/192) = 2 when 192 | N and
-// w_N^(N/64) = 8 when 64 | N, so all DFTs of length dividing 192 inside a
-// transform have power-of-two roots. 7 generates GF(p)^*, and 2 has order 192.
-inline uint64_t root_3_2_32() {
+// A primitive (15 * 2^32)-th root W with W^(5 * 2^26) = 2, from which every
+// transform length N (dividing 15 * 2^32) takes its root w_N = W^(15 * 2^32 / N).
+// Then w_N^(N/192) = 2 when 192 | N and w_N^(N/64) = 8 when 64 | N, so all DFTs
+// of length dividing 192 inside a transform have power-of-two roots (2 has
+// order 192), and w_N^(N/40) = W^(3 * 2^29) is the 40th root the radix-5 steps
+// use (the constants gl::w40_pow and the DFT-5 constants are derived from it).
+// One root for all lengths also makes a strided pass's twiddle table depend on
+// its (M, S) alone. 7 generates GF(p)^*.
+inline uint64_t root_15_2_32() {
     const uint64_t p1 = gl::P - 1;
-    uint64_t r0 = gl::pow(7, p1 / (3ull << 32));  // order 3 * 2^32
-    uint64_t c = gl::pow(r0, 1ull << 26);         // order 192: c = 2^u, gcd(u, 192) = 1
+    uint64_t r0 = gl::pow(7, p1 / (15ull << 32));  // order 15 * 2^32
+    uint64_t c = gl::pow(r0, 5ull << 26);          // order 192: c = 2^u, gcd(u, 192) = 1
     int u = -1;
     uint64_t e = 1;
     for (int i = 0; i < 192; i++) {
@@ -161,21 +176,22 @@ inline uint64_t root_3_2_32() {
     if (u < 0) return 0;
     int v = 1;
     while ((u * v) % 192 != 1) v++;               // v = u^-1 mod 192
+    while (v % 5 == 0) v += 192;                  // keep the order 15 * 2^32
     return gl::pow(r0, (uint64_t)v);
 }
 
-// primitive N-th root for N = 2^logN (three = 0) or 3 * 2^logN (three = 1)
-inline uint64_t omega(int logN, int three = 0) {
-    return gl::pow(root_3_2_32(), (three ? 1ull : 3ull) << (32 - logN));
+// primitive N-th root for N = odd * 2^logN, odd in {1, 3, 5}
+inline uint64_t omega(int logN, int odd = 1) {
+    return gl::pow(root_15_2_32(), (uint64_t)(15 / odd) << (32 - logN));
 }
 
 // Table layout: w4096 | w4096^-1 | wlo | wlo^-1 | whi | whi^-1
 inline size_t table_words_n(uint64_t N) { return 4 * 4096 + 2 * (N >> 12); }
 inline size_t table_words(int logN) { return table_words_n(1ull << logN); }
 
-inline void make_tables(int logN, std::vector<uint64_t>& t, int three = 0) {
-    uint64_t N = (three ? 3ull : 1ull) << logN;
-    uint64_t w = omega(logN, three), wi = gl::pow(w, gl::P - 2);
+inline void make_tables(int logN, std::vector<uint64_t>& t, int odd = 1) {
+    uint64_t N = (uint64_t)odd << logN;
+    uint64_t w = omega(logN, odd), wi = gl::pow(w, gl::P - 2);
     uint64_t w4 = gl::pow(w, N >> 12), w4i = gl::pow(wi, N >> 12);
     uint64_t nh = N >> 12;
     t.assign(table_words_n(N), 0);
@@ -200,8 +216,8 @@ inline void make_tables(int logN, std::vector<uint64_t>& t, int three = 0) {
     }
 }
 
-inline uint64_t n_inverse(int logN, int three = 0) {
-    return gl::pow((three ? 3ull : 1ull) << logN, gl::P - 2);
+inline uint64_t n_inverse(int logN, int odd = 1) {
+    return gl::pow((uint64_t)odd << logN, gl::P - 2);
 }
 
 }  // namespace pa

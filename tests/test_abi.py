@@ -148,9 +148,10 @@ def test_workspace_bytes(n, N):
 
 
 @pytest.mark.parametrize("n,m,N", [(1, 1, 4096), (2048, 2049 - 2048, 4096), (3000, 1097, 4096),
-                                   (3000, 1098, 8192), (1_000_000, 250_000, 3 << 19),
-                                   (100_000_000, 25_000_000, 1 << 27)])
+                                   (3000, 1098, 8192), (1_000_000, 250_000, 5 << 18),
+                                   (1_000_000, 320_000, 3 << 19), (100_000_000, 25_000_000, 1 << 27)])
 def test_toeplitz_workspace_bytes(n, m, N):
-    """Toeplitz transform length: smallest 2^k or 3 * 2^k (first radix <= 48)
-    that is >= max(4096, n + m - 1); two N-word buffers."""
+    """Toeplitz transform length: smallest 2^k, 3 * 2^k (first radix <= 48) or
+    5 * 2^k (first radix <= 40) that is >= max(4096, n + m - 1); two N-word
+    buffers."""
     assert binding.toeplitz_workspace_bytes(n, m) == 2 * N * 8

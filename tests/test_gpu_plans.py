@@ -11,11 +11,14 @@ from tests.gpu_util import dev, gpu_hash, host
 
 pytestmark = pytest.mark.gpu
 
-# transform lengths 2^12 (no strided pass), 2^14 ([4]), 2^17 ([32]), 3*2^16
+# full-product lengths 2^12 (no strided pass), 2^14 ([4]), 2^17 ([32]), 3*2^16
 # ([48]), 2^19 ([2, 64]), 3*2^18 ([3, 64]) and 3*2^24 ([3, 64, 64]; with the
 # odd radix last, [64, 64, 3], the middle pass has 64 sub-problems of 192 tiles
-# each); the single-pass lengths also run with narrow tiles (variants 8 .. 15)
-SIZES = [1000, 100_003, 1_000_000, 1_536_000, 3_000_001, 4_800_000, 300_000_017]
+# each), and the radix-5 family 5*2^12 ([5]), 5*2^13 ([10]), 5*2^14 ([20]),
+# 5*2^15 ([40]) and 5*2^18 ([5, 64]); the single-pass lengths also run with
+# narrow tiles (variants 8 .. 15). Each size also runs its wrapped length.
+SIZES = [1000, 100_003, 1_000_000, 1_536_000, 3_000_001, 4_800_000, 300_000_017,
+         163_840, 327_680, 655_360, 1_310_720, 10_485_760]
 
 
 @pytest.mark.parametrize("n", SIZES)

@@ -24,14 +24,17 @@ from paper_1910_04429_gb300 import binding, inputs
 
 
 def _lengths(lo_len, hi_len):
-    """Transform lengths of the library (2^k, k >= 12, and 3 * 2^j, j >= 12 with
-    (j - 12) mod 6 <= 4), ascending, in [lo_len, hi_len]."""
+    """Transform lengths of the library (2^k, k >= 12; 3 * 2^j, j >= 12 with
+    (j - 12) mod 6 <= 4; 5 * 2^j, j >= 12 with (j - 12) mod 6 <= 3: first radix
+    at most 48 or 40), ascending, in [lo_len, hi_len]."""
     out = set()
     for k in range(12, 40):
         if lo_len <= (1 << k) <= hi_len:
             out.add(1 << k)
         if (k - 12) % 6 <= 4 and lo_len <= (3 << k) <= hi_len:
             out.add(3 << k)
+        if (k - 12) % 6 <= 3 and lo_len <= (5 << k) <= hi_len:
+            out.add(5 << k)
     return sorted(out)
 
 
@@ -91,16 +94,18 @@ def test_plan_info_follows_the_rule(n, m, mode, wrap_mode):
 
 
 def test_headline_sizes_wrap(wrap_mode):
-    """The 10^8-bit block (m = n/4) runs 2^23 points instead of 3 * 2^22; the
-    10^9-bit block 3 * 2^25 instead of 2^27; at m = n/2 the 10^8-bit block has
-    no shorter length. The 10^6-bit block (2^17 points) stays unwrapped by
-    default and wraps to 3 * 2^15 in mode 2."""
+    """The 10^8-bit block (m = n/4) runs 2^23 points instead of 3 * 2^22, and
+    5 * 2^21 at m = n/2; the 10^9-bit block 5 * 2^24 instead of 2^27; the
+    10^7-bit block's full product is 5 * 2^18 (2L - 1 = 1249999). The 10^6-bit
+    block (2^17 points) stays unwrapped by default and wraps to 5 * 2^14 in
+    mode 2."""
     assert binding.plan_info(10 ** 8, 25 * 10 ** 6)["first"] == 1 << 23
-    assert binding.plan_info(10 ** 9, 25 * 10 ** 7)["first"] == 3 << 25
-    assert binding.plan_info(10 ** 8, 5 * 10 ** 7)["dropped"] == 0
+    assert binding.plan_info(10 ** 8, 5 * 10 ** 7)["first"] == 5 << 21
+    assert binding.plan_info(10 ** 9, 25 * 10 ** 7)["first"] == 5 << 24
+    assert binding.plan_info(10 ** 7, 10 ** 6)["full"] == 5 << 18
     assert binding.plan_info(10 ** 6, 250_000)["dropped"] == 0
     wrap_mode(2)
-    assert binding.plan_info(10 ** 6, 250_000)["first"] == 3 << 15
+    assert binding.plan_info(10 ** 6, 250_000)["first"] == 5 << 14
 
 
 def test_plan_info_rejects_bad_sizes():
