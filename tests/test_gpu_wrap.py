@@ -21,8 +21,9 @@ def wrap_wherever_shorter():
     yield
     binding.wrap_mode(prev)
 
-# sizes whose hash wraps (checked below): a few tiles, ragged n and m, 2^k and
-# 3 * 2^k wrapped lengths, one and two strided passes, and the 10^6-bit block
+# sizes whose hash wraps (checked below): a few tiles, ragged n and m, 2^k,
+# 3 * 2^k and 5 * 2^k wrapped lengths, one and two strided passes, and the
+# 10^6-bit block
 WRAPPED = [(100_000, 25_000), (100_003, 12_345), (1_000_000, 250_000), (1_000_003, 100_001),
            (3_000_017, 300_001), (4_800_000, 1_200_000), (10_000_000, 1_000_000),
            # floor((n - m)/64) = 10 * 1024: the certificate's limb lies in the carry
