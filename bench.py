@@ -68,8 +68,9 @@ def parse():
     p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--n", type=int, default=N_BITS)
-    p.add_argument("--m", type=int, default=M_BITS)
+    p.add_argument("--n", "--n-bits", dest="n", type=int, default=N_BITS,
+                   help="key length in bits (--n-bits passes through torchrun)")
+    p.add_argument("--m", "--m-bits", dest="m", type=int, default=M_BITS, help="output bits")
     p.add_argument("--workload", choices=["single", "batched", "served"], default="single",
                    help="single: one 10^8-bit block per step (default); batched: 256 blocks of "
                         "10^6..10^7 bits per pa_hash_batched call; served: Poisson arrivals "
