@@ -99,7 +99,10 @@ def test_headline_sizes_wrap(wrap_mode):
     10^7-bit block's full product is 5 * 2^18 (2L - 1 = 1249999). The 10^6-bit
     block (2^17 points) stays unwrapped by default and wraps to 5 * 2^14 in
     mode 2."""
-    assert binding.plan_info(10 ** 8, 25 * 10 ** 6)["first"] == 1 << 23
+    info = binding.plan_info(10 ** 8, 25 * 10 ** 6)
+    assert info["first"] == 1 << 23
+    # W = 2L - 1 - N = 12,499,999 - 8,388,608 = 4,111,391, rounded up to even
+    assert info["dropped"] == 4_111_392 and _wbits(4_111_392) == 65_782_310
     assert binding.plan_info(10 ** 8, 5 * 10 ** 7)["first"] == 5 << 21
     assert binding.plan_info(10 ** 9, 25 * 10 ** 7)["first"] == 5 << 24
     assert binding.plan_info(10 ** 7, 10 ** 6)["full"] == 5 << 18
