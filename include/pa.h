@@ -97,7 +97,9 @@ int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
  * pa_hash_host_async: the same, returning once everything is queued. The
  * copy stream runs at most two calls ahead of the hashes (staging memory is
  * bounded to three calls' inputs), so back-to-back calls overlap one call's
- * input copies with the previous call's transforms. The caller must keep key,
+ * input copies with the previous call's transforms; each queued hash starts
+ * once all three of its inputs are in (pa_hash_host starts the product once
+ * key and seed_a are in and copies seed_b meanwhile). The caller must keep key,
  * seed_a, seed_b and out valid, leave the inputs unmodified and not read out
  * until `stream` has passed the call (e.g. cudaStreamSynchronize). With
  * pageable buffers the copies block the host and nothing overlaps.

@@ -580,7 +580,7 @@ int setup(int* dev, cudaMemPool_t* pool) {
 // next call's copies overlap this call's transforms), b behind them, the hash
 // runs on st after each copy's event, and the result is copied back on st.
 int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
-                    uint64_t m, uint64_t* out, cudaStream_t st) {
+                    uint64_t m, uint64_t* out, cudaStream_t st, bool queued) {
     std::lock_guard<std::mutex> lk(g_mu);
     int dev, rc;
     cudaMemPool_t pool;
@@ -613,12 +613,18 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
         void* mo = nullptr;
         HashPlan hp;
         rc = hash_prepare((const u64*)dx, (const u64*)da, n, m, scr, dev, &hp);
-        if (rc || (e = cudaStreamWaitEvent(st, d.xa_ready, 0))) {
+        // A queued call waits for all three inputs before its first kernel (their
+        // copies ran during the hashes before it), so that nothing sits between
+        // the product's last kernel and the carry kernel on st and the
+        // programmatic launch joins them; a call that waits for its result starts
+        // the product once x and a are in and copies b meanwhile.
+        cudaEvent_t in_ready = queued ? d.b_ready : d.xa_ready;
+        if (rc || (e = cudaStreamWaitEvent(st, in_ready, 0))) {
             cudaStreamWaitEvent(st, d.b_ready, 0);
             return rc ? rc : cuda_fail(e, "cudaStreamWaitEvent");
         }
         rc = hash_product(hp, st);
-        if ((e = cudaStreamWaitEvent(st, d.b_ready, 0))) return cuda_fail(e, "cudaStreamWaitEvent");
+        if (!queued && (e = cudaStreamWaitEvent(st, d.b_ready, 0))) return cuda_fail(e, "cudaStreamWaitEvent");
         if (rc) return rc;
         // the result goes to device memory and is copied back (writing it into a
         // mapped pinned buffer from the carry kernel measured slower)
@@ -764,7 +770,7 @@ int pa_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* se
     if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_hash_host: need 1 <= m <= n <= PA_MAX_BITS");
     if (!key || !seed_a || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_host: null pointer");
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = queue_hash_host(key, seed_a, seed_b, n, m, out, st);
+    int rc = queue_hash_host(key, seed_a, seed_b, n, m, out, st, false);
     if (rc) return rc;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -775,7 +781,7 @@ int pa_hash_host_async(const uint64_t* key, const uint64_t* seed_a, const uint64
                        uint64_t n, uint64_t m, uint64_t* out, void* stream) {
     if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_hash_host_async: need 1 <= m <= n <= PA_MAX_BITS");
     if (!key || !seed_a || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_host_async: null pointer");
-    return queue_hash_host(key, seed_a, seed_b, n, m, out, (cudaStream_t)stream);
+    return queue_hash_host(key, seed_a, seed_b, n, m, out, (cudaStream_t)stream, true);
 }
 
 int pa_convolve16(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t* coef,
