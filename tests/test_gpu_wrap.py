@@ -162,3 +162,29 @@ def test_full_size_wrapped_sampled():
     np.testing.assert_array_equal(got, ref)
     np.testing.assert_array_equal(forced, ref)
     assert binding.device_status() == 0  # no bounded wait ran out
+
+
+def test_batched_forced_fallback_over_several_launches():
+    """70 wrapped blocks (two transform lengths) and 3 unwrapped ones in one
+    batched call, every certificate failed (mode 3): the recomputation runs in
+    two launches of at most 64 jobs, each with its own grid-barrier counter;
+    every block comes out exact and only the wrapped ones were flagged."""
+    import torch
+
+    wrapped = [inputs.make_block(100_000 + 1009 * i, 25_000 + 7 * i, seed=700 + i) for i in range(70)]
+    plain = [inputs.make_block(5_000 + 17 * i, 100 + i, seed=800 + i) for i in range(3)]
+    for b in wrapped:  # the batch rule is mode 2's: wrap wherever a shorter length certifies
+        assert binding.plan_info(b.n, b.m)["dropped"] > 0
+    for b in plain:
+        assert binding.plan_info(b.n, b.m)["dropped"] == 0
+    blks = wrapped[:40] + plain + wrapped[40:]
+    binding.wrap_mode(3)
+    binding.wrap_flags(clear=True)
+    t = [(dev(b.x), dev(b.a), dev(b.b)) for b in blks]
+    outs = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in blks]
+    binding.hash_batched([(x, a, bb, b.n, b.m, o) for b, (x, a, bb), o in zip(blks, t, outs)])
+    torch.cuda.synchronize()
+    assert binding.wrap_flags() == len(wrapped)
+    for i, (b, o) in enumerate(zip(blks, outs)):
+        np.testing.assert_array_equal(host(o), _want(b), err_msg=f"block {i}")
+    assert binding.device_status() == 0
