@@ -307,7 +307,7 @@ def test_parity_config2_full_size():
 @pytest.mark.parametrize("wrap_mode", [1, 0, 3])
 def test_parity_config5_digest(wrap_mode):
     """n = 10^9, m = 2.5 * 10^8, seed 1, against the stored oracle digest: as
-    the library runs it (the wrapped product, length 3 * 2^25), as the
+    the library runs it (the wrapped product, length 5 * 2^24), as the
     full-length product (2^27), and with the certificate forced to fail (the
     recomputation at 2^27 points)."""
     path = os.path.join(GOLDEN, "oracle_digest_n1000000000_m250000000_seed1.json")
