@@ -98,6 +98,12 @@ def test_argument_checks_without_gpu():
     blocks[1] = binding.PaBlock(z.ctypes.data, z.ctypes.data, z.ctypes.data, 100, 101, z.ctypes.data)
     assert lib.pa_hash_batched(blocks, 2, null) == binding.PA_EINVAL
     assert b"block 1" in lib.pa_last_error()
+    # an empty batch is a no-op (no device touched); a null array with blocks is refused
+    assert lib.pa_hash_batched(None, 0, null) == binding.PA_OK
+    assert lib.pa_hash_batched(None, 3, null) == binding.PA_EINVAL
+    hb = ctypes.c_void_p(0)
+    assert lib.pa_batch_create(blocks, 0, ctypes.byref(hb)) == binding.PA_EINVAL
+    assert lib.pa_batch_create(blocks, 2, None) == binding.PA_EINVAL
     assert lib.pa_prepare(0) == binding.PA_EINVAL
     assert lib.pa_fault_inject(99) == binding.PA_EINVAL
     assert lib.pa_plan_override(0, 0) == binding.PA_EINVAL
