@@ -3,10 +3,16 @@
 Workload (default): one privacy-amplification block of n = 10^8 key bits,
 m = 2.5 * 10^7 output bits, uniform key and seeds from SplitMix64 (the
 10^8-bit row of the paper's Table 2, hashed as Eq. 7 defines). A step is one
-full hash: digit split, three length-2^24 NTTs, pointwise product, carry
-resolve, + b, mod 2^n and extraction. Inputs rotate over several seeded
-blocks whose total size exceeds the 129 MB L2, so no step reads another
-step's inputs from L2.
+full hash: digit split, the forward NTTs of key and seed, pointwise product,
+inverse NTT, carry resolve, + b, mod 2^n and extraction. Inputs rotate over
+several seeded blocks whose total size exceeds the 129 MB L2, so no step reads
+another step's inputs from L2. Five windows of K steps are timed; the median
+is reported.
+
+The same line also carries the 10^6-bit block (n1e6), the batched workload (256
+blocks of 10^6..10^7 bits), the served workload (Poisson arrivals at 200/s for
+60 s, 10^6..10^8 bits) with a sweep of arrival rates against plain launches,
+the Toeplitz-hash comparison workload, and the CPU baselines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,6 +42,7 @@ UNIT = "Mbps"
 N_BITS = 100_000_000
 M_BITS = 25_000_000
 ROTATE = 4                      # distinct input blocks: 4 x 37.5 MB > L2
+WINDOWS = 5                     # timed windows of K steps; the median is reported
 PAPER_I9_N1E8_MBPS = 140.96     # Table 2, i9-9900k, 100M-bit block (other hardware)
 
 
@@ -71,7 +78,7 @@ def parse():
     p.add_argument("--n", "--n-bits", dest="n", type=int, default=N_BITS,
                    help="key length in bits (--n-bits passes through torchrun)")
     p.add_argument("--m", "--m-bits", dest="m", type=int, default=M_BITS, help="output bits")
-    p.add_argument("--workload", choices=["single", "batched", "served"], default="single",
+    p.add_argument("--workload", choices=["single", "batched", "served", "served-sweep"], default="single",
                    help="single: one 10^8-bit block per step (default); batched: 256 blocks of "
                         "10^6..10^7 bits per pa_hash_batched call; served: Poisson arrivals "
                         "through pa_submit/pa_poll")
@@ -83,6 +90,11 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-small", action="store_true", help="skip the 10^6-bit block measurement")
     p.add_argument("--no-toeplitz", action="store_true", help="skip the Toeplitz-hash measurement")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the batched and served records of the default line")
+    p.add_argument("--sweep-rates", default="1000,4000,7000,10000",
+                   help="arrival rates (blocks/s) of the served-against-plain sweep")
+    p.add_argument("--sweep-duration", type=float, default=2.0)
     return p.parse_args()
 
 
@@ -162,9 +174,16 @@ def load_peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-# Integer ALU-pipe peak: 152 SMs x 64 lanes (the ALU pipe accepts one warp
-# instruction every second cycle per scheduler) x the maximum SM clock.
-SMS, ALU_LANES_PER_SM = 152, 64
+# Integer ALU-pipe peak: the device's SM count (152 on a GB300) x 64 lanes (the
+# ALU pipe accepts one warp instruction every second cycle per scheduler) x the
+# maximum SM clock.
+ALU_LANES_PER_SM = 64
+
+
+def sm_count(device=None) -> int:
+    import torch
+
+    return int(torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count)
 
 # Roofline work model. The algorithmic work of a length-N transform is
 # (N/2) log2 N radix-2 butterflies, each one Goldilocks modmul plus one modular
@@ -192,6 +211,22 @@ def alu_ops(name: str, N: int):
     if name == "ntt_contig_seed":
         return 12 * stage + N * COST["mul"]
     return None
+
+
+def step_alu_ops(N: int) -> float:
+    """Butterfly-model ALU operations of one whole hash of transform length N:
+    three transforms (x, a forward; the product inverse) of (N/2) log2 N
+    butterflies, the pointwise product and the N^-1 scaling (the carry step's
+    few instructions per limb are not counted)."""
+    import math
+
+    return 3 * (N / 2) * math.log2(N) * BUTTERFLY + 2 * N * COST["mul"]
+
+
+def hash_bytes(n: int, m: int) -> int:
+    """The bytes the hash must move (its algorithmic HBM traffic): x, a and b
+    read once, ceil(n/64) limbs each, and the ceil(m/64) output limbs written."""
+    return 8 * (3 * ((n + 63) // 64) + (m + 63) // 64)
 
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
@@ -273,19 +308,25 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     binding.wrap_flags(clear=True)
 
+    # WINDOWS timed windows of exactly K steps each, every one bracketed by a
+    # barrier and a device synchronize; the median window is reported
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for i in range(args.steps):
-        step(i)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_total = ev0.elapsed_time(ev1)
+    windows = []
+    for w in range(WINDOWS):
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(w * args.steps + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        windows.append(ev0.elapsed_time(ev1))
     clk = clocks.stop()
+    windows = max_over_ranks(windows, world, dev)
+    ms_total = statistics.median(windows)
     flags = binding.wrap_flags()  # failed certificates in the timed steps (each ran the full product)
 
     # the same workload as the full-length product (wrapping off), for comparison
@@ -400,10 +441,17 @@ def run_ours(args, rank, world, local):
 
     small = None if args.no_small else run_small(dev, stream)
     toep = None if args.no_toeplitz else run_toeplitz(dev, stream)
-    ms_total, e2e_ms, e2e_sync_ms = max_over_ranks([ms_total, e2e_ms, e2e_sync_ms], world, dev)
-    return dict(ms_total=ms_total, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats, clocks=clk, latency=latency,
-                h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant, small=small,
-                toeplitz=toep, flags=flags, plan=binding.plan_info(n, m), full_ms=full_ms)
+    # the batched and served forms (one GPU: their records describe that GPU)
+    batched = served = sweep = None
+    if world == 1 and not args.no_forms:
+        batched = run_batched(args)
+        served = run_served(args)
+        sweep = run_served_sweep(args)
+    e2e_ms, e2e_sync_ms = max_over_ranks([e2e_ms, e2e_sync_ms], world, dev)
+    return dict(ms_total=ms_total, windows=windows, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats,
+                clocks=clk, latency=latency, h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant,
+                small=small, toeplitz=toep, flags=flags, plan=binding.plan_info(n, m), full_ms=full_ms,
+                batched=batched, served=served, served_sweep=sweep, sms=sm_count(dev))
 
 
 def run_toeplitz(dev, stream, sizes=((100_000_000, 25_000_000, 20), (1_000_000, 250_000, 200))):
@@ -468,11 +516,30 @@ def cpu_toeplitz_oracle_rate():
             "sample": f"one n=1e6, m=2.5e5 Toeplitz block, column-by-column GF(2) product, {dt:.2f} s"}
 
 
+def kernel_roofline(kstats: dict, N: int):
+    """ALU roofline of the dominant tile kernel of a profiled run: its
+    butterfly-model operations per launch over its mean CUDA-event launch time."""
+    if not kstats:
+        return None
+    name, (cnt, tot_ms) = max(kstats.items(), key=lambda kv: kv[1][1])
+    ops = alu_ops(name, N)
+    _, mhz, src = load_peaks()
+    peak = sm_count() * ALU_LANES_PER_SM * mhz * 1e6 / 1e12
+    total = sum(v[1] for v in kstats.values())
+    out = {"kernel": name, "share": round(tot_ms / total, 3), "launch_ms": round(tot_ms / cnt, 5)}
+    if ops is not None:
+        achieved = ops / (tot_ms / cnt / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "Tops/s",
+                    "frac": round(achieved / peak, 4)})
+    return out
+
+
 def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
     """The 10^6-bit block (m = 2.5e5): plain launches back to back, the time of
     each plain launch alone (events around it, median and p99 of `launches`),
-    and one-block captured graphs replayed back to back. Everything here is
-    resident in the L2 cache (inputs 0.4 MB a block, workspace 2 MB)."""
+    one-block captured graphs replayed back to back, and the ALU roofline of its
+    dominant kernel (per-kernel CUDA events over a separate pass). Everything here
+    is resident in the L2 cache (inputs 0.4 MB a block, workspace 2 MB)."""
     import torch
 
     from paper_1910_04429_gb300 import binding
@@ -509,6 +576,13 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
     torch.cuda.synchronize()
     alone = sorted(a0.elapsed_time(a1) * 1e3 for a0, a1 in evs)
 
+    binding.profile(True)
+    for i in range(launches):
+        step(i)
+    torch.cuda.synchronize()
+    binding.profile(False)
+    kstats = binding.profile_collect()
+
     graphs = [binding.Batch([(x, a, b, n, m, outs[j])]) for j, (x, a, b) in enumerate(dv)]
     for i in range(10):
         graphs[i % rotate].run(stream)
@@ -521,19 +595,23 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
     graph_ms = e0.elapsed_time(e1) / launches
     for g in graphs:
         g.close()
+    N = binding.plan_info(n, m)["first"]
     return {"workload": f"G_cd hash, one key of n={n} bits, m={m}, {rotate} rotating blocks, "
-                        f"L2-resident", "plan_variant": tuned,
+                        f"L2-resident", "plan_variant": tuned, "transform": N,
             "value": round(n / b2b_ms / 1e3, 1), "unit": UNIT,
             "note": f"plain launches back to back, {launches} steps",
             "plain_single_launch_median_us": round(alone[len(alone) // 2], 2),
             "plain_single_launch_p99_us": round(alone[min(len(alone) - 1, int(0.99 * len(alone)))], 2),
-            "captured_graph_value": round(n / graph_ms / 1e3, 1)}
+            "captured_graph_value": round(n / graph_ms / 1e3, 1),
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kstats.items()},
+            "roofline": kernel_roofline(kstats, N)}
 
 
 def run_batched(args):
     """256 independent blocks, n = floor(exp(U(ln 1e6, ln 1e7))), m = floor(n r),
-    r ~ U(0.1, 0.5): one pa_hash_batched per step, against the same blocks as
-    plain single-block pa_hash calls on one stream."""
+    r ~ U(0.1, 0.5), seeds 1..256: one pa_hash_batched per step, the same batch
+    as a captured graph (pa_batch_run), and the same blocks as plain single-block
+    pa_hash calls on one stream."""
     import torch
 
     from paper_1910_04429_gb300 import binding
@@ -546,9 +624,10 @@ def run_batched(args):
         binding.prepare(b.n)
     spec = [(x, a, bb, b.n, b.m, o) for (x, a, bb), b, o in zip(d, blks, outs)]
     bits = sum(b.n for b in blks)
+    # 256 blocks: inputs 3 x 122 MB and 2 x 2.1 GB of workspace per batch, > 129 MB L2
 
     def timed(fn, steps):
-        for _ in range(args.warmup):
+        for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -575,9 +654,11 @@ def run_batched(args):
     ms_g = timed(graph.run, steps)
     same = same and all(torch.equal(r, o) for r, o in zip(ref, outs))
     graph.close()
+    lens = sorted({binding.plan_info(b.n, b.m)["first"] for b in blks})
     return {"metric": "PA input throughput (Mbps of key bits), batched blocks", "unit": UNIT,
             "workload": f"{len(blks)} blocks, n log-uniform in [1e6, 1e7] (sum {bits} bits), "
                         f"m = floor(n r), r ~ U(0.1, 0.5), seeds 1..{len(blks)}",
+            "transform_lengths": len(lens),
             "batched": {"value": round(bits / ms_b / 1e3, 1), "ms_per_batch": round(ms_b, 3)},
             "plain_single_launches": {"value": round(bits / ms_p / 1e3, 1),
                                       "ms_per_batch": round(ms_p, 3)},
@@ -585,36 +666,44 @@ def run_batched(args):
             "results_identical": same, "steps": steps}
 
 
-def run_served(args):
-    """Poisson arrivals through pa_submit; keys are prefixes of one resident
-    10^8-bit pool (the bits do not affect the work), outputs rotate over a ring."""
-    import threading as th
+class _ServedPool:
+    """Keys of the served workloads: prefixes of one resident 10^8-bit block (the
+    bits do not affect the work), outputs rotating over a ring."""
 
-    import torch
+    RING = 512
+
+    def __init__(self):
+        import torch
+
+        pool = inputs.make_block(100_000_000, 1, seed=1)
+        self.x, self.a, self.b = (torch.from_numpy(v.view(np.int64)).cuda() for v in (pool.x, pool.a, pool.b))
+        self.outs = [torch.empty((50_000_000 + 63) // 64, dtype=torch.int64, device="cuda")
+                     for _ in range(self.RING)]
+
+
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))] if v else 0.0
+
+
+def served_run(pool, arrivals, sizes, max_batch=32, streams=3):
+    """Submit each block at its arrival time through pa_submit; a poller thread
+    completes the tickets in order. Returns the library's statistics and the
+    wall time from the first arrival to the last completion."""
+    import threading as th
 
     from paper_1910_04429_gb300 import binding
 
-    binding.load()
-    pool = inputs.make_block(100_000_000, 1, seed=1)
-    px, pa_, pb = (torch.from_numpy(v.view(np.int64)).cuda() for v in (pool.x, pool.a, pool.b))
-    arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=7)
-    sizes = inputs.batch_sizes(len(arrivals), 1_000_000, 100_000_000, seed=11)
-    ring = 512
-    outs = [torch.empty((50_000_000 + 63) // 64, dtype=torch.int64, device="cuda") for _ in range(ring)]
-    # footprint alone of the largest block sets no extra limit; default budget
     binding.serve_stop()
-    binding.serve_init(max_batch=32, streams=3)
-    for n, _ in sizes[:64]:
-        binding.prepare(n)
-    tickets = []
-    polled = [0]
+    binding.serve_init(max_batch=max_batch, streams=streams)
+    tickets, polled = [], [0]
     done_evt = th.Event()
 
     def poller():
         i = 0
         while i < len(arrivals):
             if i >= len(tickets):
-                time.sleep(0.0005)
+                time.sleep(0.0002)
                 continue
             rc, st = binding.poll(tickets[i], 1_000_000)
             if rc == binding.PA_OK:
@@ -628,44 +717,146 @@ def run_served(args):
     t_poll.start()
     t0 = time.perf_counter()
     for i, (t_arr, (n, m)) in enumerate(zip(arrivals, sizes)):
-        while i - polled[0] >= ring - 1:   # keep the output ring from wrapping
-            time.sleep(0.0002)
+        while i - polled[0] >= pool.RING - 1:   # keep the output ring from wrapping
+            time.sleep(0.0001)
         delay = t0 + t_arr - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets.append(binding.submit(px, pa_, pb, n, m, outs[i % ring]))
+        tickets.append(binding.submit(pool.x, pool.a, pool.b, n, m, pool.outs[i % pool.RING]))
     done_evt.wait(timeout=600)
     wall = time.perf_counter() - t0
     st = binding.serve_stats()
     binding.serve_stop()
+    return st, wall
+
+
+def plain_run(pool, arrivals, sizes):
+    """The same arrivals as plain pa_hash calls on one stream (no batching): each
+    block is queued at its arrival time with an event behind it; a poller thread
+    waits for the events in order. Latency = completion seen - arrival."""
+    import threading as th
+
+    import torch
+
+    from paper_1910_04429_gb300 import binding
+
+    stream = torch.cuda.Stream()
+    evs = [None] * len(arrivals)
+    queued, polled = [0], [0]
+    lat = [0.0] * len(arrivals)
+    t0 = [0.0]
+    done_evt = th.Event()
+    t_last = [0.0]
+
+    def poller():
+        for i in range(len(arrivals)):
+            while queued[0] <= i:
+                time.sleep(0.0001)
+            evs[i].synchronize()
+            t = time.perf_counter()
+            lat[i] = (t - (t0[0] + arrivals[i])) * 1e6
+            polled[0] = i + 1
+            t_last[0] = t
+        done_evt.set()
+
+    t_poll = th.Thread(target=poller, daemon=True)
+    t_poll.start()
+    t0[0] = time.perf_counter()
+    for i, (t_arr, (n, m)) in enumerate(zip(arrivals, sizes)):
+        while i - polled[0] >= pool.RING - 1:
+            time.sleep(0.0001)
+        delay = t0[0] + t_arr - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        binding.hash(pool.x, pool.a, pool.b, n, m, out=pool.outs[i % pool.RING], stream=stream)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        evs[i] = ev
+        queued[0] = i + 1
+    done_evt.wait(timeout=600)
+    return lat, t_last[0] - t0[0]
+
+
+def run_served(args):
+    """Poisson arrivals through pa_submit (the served workload: 200 blocks/s for
+    60 s, n log-uniform in [1e6, 1e8], r ~ U(0.1, 0.5)), against the same sizes
+    as plain launches timed alone."""
+    import torch
+
+    from paper_1910_04429_gb300 import binding
+
+    binding.load()
+    pool = _ServedPool()
+    arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=7)
+    sizes = inputs.batch_sizes(len(arrivals), 1_000_000, 100_000_000, seed=11)
+    for n, _ in sizes[:64]:
+        binding.prepare(n)
+    st, wall = served_run(pool, arrivals, sizes)
     bits = sum(n for n, _ in sizes)
     # latency of the same sizes hashed alone with plain launches (no queueing)
     alone = []
-    for n, m in sizes[:50]:
+    for n, m in sizes[:1000]:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        binding.hash(px, pa_, pb, n, m, out=outs[0])
+        binding.hash(pool.x, pool.a, pool.b, n, m, out=pool.outs[0])
         e1.record()
         torch.cuda.synchronize()
         alone.append(e0.elapsed_time(e1) * 1e3)
-    alone.sort()
     return {"metric": "served PA throughput (Mbps of key bits) and latency", "unit": UNIT,
             "workload": f"Poisson arrivals at {args.rate}/s for {args.duration} s ({len(arrivals)} blocks), "
                         f"n log-uniform in [1e6, 1e8], r ~ U(0.1, 0.5)",
             "offered_mbps": round(bits / args.duration / 1e6, 1),
             "sustained_mbps": round(st["bits"] / wall / 1e6, 1),
             "p50_latency_us": round(st["p50_us"], 1), "p99_latency_us": round(st["p99_us"], 1),
-            "max_latency_us": round(st["max_us"], 1), "batches": st["batches"],
+            "max_latency_us": round(st["max_us"], 1), "completed": st["completed"], "batches": st["batches"],
             "peak_inflight_blocks": st["peak_inflight_blocks"],
             "peak_inflight_bytes": st["peak_inflight_bytes"], "hbm_budget_bytes": st["hbm_budget_bytes"],
-            "plain_single_launch_p50_us": round(alone[len(alone) // 2], 1),
-            "plain_single_launch_p99_us": round(alone[min(len(alone) - 1, int(0.99 * len(alone)))], 1)}
+            "plain_single_launch_p50_us": round(_pct(alone, 0.5), 1),
+            "plain_single_launch_p99_us": round(_pct(alone, 0.99), 1),
+            "plain_note": f"the first {len(alone)} sizes hashed alone, events around each (device time only)"}
 
 
-def cpu_oracle_rate(n_sample: int, reps: int = 1):
+def run_served_sweep(args):
+    """Served (continuous batching) against plain back-to-back pa_hash calls on
+    one stream, at several Poisson arrival rates up to and past saturation, the
+    same arrival times and sizes (n log-uniform in [1e6, 1e8]) for both."""
+    from paper_1910_04429_gb300 import binding
+
+    binding.load()
+    pool = _ServedPool()
+    out = []
+    for k, rate in enumerate(float(r) for r in args.sweep_rates.split(",") if r):
+        arrivals = inputs.poisson_arrivals(rate, args.sweep_duration, seed=70 + k)
+        sizes = inputs.batch_sizes(len(arrivals), 1_000_000, 100_000_000, seed=110 + k)
+        bits = sum(n for n, _ in sizes)
+        st, wall = served_run(pool, arrivals, sizes)
+        lat, pwall = plain_run(pool, arrivals, sizes)
+        out.append({"rate_per_s": rate, "blocks": len(arrivals),
+                    "offered_mbps": round(bits / args.sweep_duration / 1e6, 1),
+                    "served": {"sustained_mbps": round(st["bits"] / wall / 1e6, 1),
+                               "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                               "batches": st["batches"], "peak_inflight_blocks": st["peak_inflight_blocks"]},
+                    "plain": {"sustained_mbps": round(bits / pwall / 1e6, 1),
+                              "p50_us": round(_pct(lat, 0.5), 1), "p99_us": round(_pct(lat, 0.99), 1)}})
+    return {"note": f"{args.sweep_duration} s of Poisson arrivals per rate; latency = arrival to completion "
+                    "seen on the host; sustained = bits / (last completion - first arrival)",
+            "rates": out}
+
+
+def bench_config(n: int, m: int, world: int) -> dict:
+    """The workload both arms of the benchmark name (the device arm's plan
+    details are reported beside it, under "plan")."""
+    return {"workload": f"G_cd hash, one key of n={n} bits, m={m} output bits per step",
+            "seeds": f"{ROTATE} rotating blocks per rank (SplitMix64 seeds 1 + rank*{ROTATE} + i)",
+            "l2": f"inputs rotate over {ROTATE} blocks ({ROTATE * 3 * ((n + 63) // 64) * 8 / 1e6:.0f} MB) "
+                  f"plus the transform workspace per step, > 129 MB L2",
+            "parallelism": f"replicas x{world}"}
+
+
+def cpu_oracle_rate(n_sample: int, reps: int = 1, m_sample=None):
     import oracle
 
-    blk = inputs.make_block(n_sample, max(1, n_sample // 4), seed=1)
+    blk = inputs.make_block(n_sample, m_sample or max(1, n_sample // 4), seed=1)
     th = oracle.default_threads()
     t0 = time.perf_counter()
     for _ in range(reps):
@@ -699,26 +890,32 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        # the oracle, as it stands, on the host cores: each step hashes one
-        # 10^7-bit block (a tenth of the 10^8-bit workload; the oracle's cost
-        # grows faster than linearly, so this favours the oracle)
-        n_s = min(args.n, 10_000_000)
+        # the oracle, as it stands, on the host cores, on the bench's own block
+        # (n = 10^8 by default): each step hashes one block of the workload. If
+        # the first warm-up step shows the whole run would exceed ~3 minutes,
+        # later steps hash a 10^7-bit block instead, and the sample says so.
+        n_s = args.n
         rates = []
         for i in range(args.warmup + args.steps):
-            r, th, dt = cpu_oracle_rate(n_s)
+            r, th, dt = cpu_oracle_rate(n_s, m_sample=args.m if n_s == args.n else None)
+            if i == 0 and dt * (args.warmup + args.steps - 1) > 180.0 and n_s > 10_000_000:
+                n_s = 10_000_000
             if i >= args.warmup:
                 rates.append(dt)
         total = sum(rates)
         value = args.steps * n_s / total / 1e6
+        m_s = args.m if n_s == args.n else n_s // 4
         line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": f"G_cd hash, key n={args.n} bits, m={args.m}",
-                           "sample": f"oracle on one block of n={n_s}, m={n_s // 4} per step"},
+                "config": bench_config(args.n, args.m, world),
                 "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": th,
                                  "kind": "oracle",
-                                 "sample": f"one n={n_s}-bit block per step, {th} threads"},
+                                 "sample": f"one block of n={n_s}, m={m_s} per step (seed 1), {th} threads"
+                                           + ("" if n_s == args.n else
+                                              f" (a smaller block than the workload's n={args.n}, "
+                                              f"to bound the run time)")},
                 "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0},
                 "gpu_launches": 0}
@@ -729,7 +926,7 @@ def main():
         import torch
 
         torch.cuda.set_device(local)
-        out = run_batched(args) if args.workload == "batched" else run_served(args)
+        out = {"batched": run_batched, "served": run_served, "served-sweep": run_served_sweep}[args.workload](args)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return 0
@@ -751,6 +948,7 @@ def main():
         name, (cnt, tot_ms) = max(res["kstats"].items(), key=lambda kv: kv[1][1])
         per_launch_s = tot_ms / cnt / 1e3
         hbm_peak, mhz, src = load_peaks()
+        SMS = res["sms"]
         alu_peak = SMS * ALU_LANES_PER_SM * mhz * 1e6 / 1e12   # T int ops / s
         ops = alu_ops(name, N)
         hbm_achieved = kernel_bytes(name, n, m, N) / per_launch_s / 1e9
@@ -773,6 +971,18 @@ def main():
         else:
             roofline.update({"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak,
                              "unit": "GB/s", "frac": round(hbm_achieved / hbm_peak, 4)})
+        # the metric's own fraction: the bytes the hash must move per block over
+        # the whole step, against the measured HBM copy bandwidth; and the whole
+        # step against the ALU peak by the same butterfly model
+        hb = hash_bytes(n, m)
+        roofline["hash_hbm"] = {"bytes_per_block": hb, "achieved": round(hb / (ms_step / 1e3) / 1e9, 1),
+                                "peak": hbm_peak, "unit": "GB/s",
+                                "frac": round(hb / (ms_step / 1e3) / 1e9 / hbm_peak, 4), "peak_source": src,
+                                "definition": "(3 ceil(n/64) + ceil(m/64)) x 8 bytes / ms_per_step"}
+        so = step_alu_ops(N)
+        roofline["step_alu"] = {"ops_per_block": so, "achieved": round(so / (ms_step / 1e3) / 1e12, 3),
+                                "peak": round(alu_peak, 2), "unit": "Tops/s",
+                                "frac": round(so / (ms_step / 1e3) / 1e12 / alu_peak, 4)}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -780,16 +990,16 @@ def main():
             "vs_baseline": round(value / PAPER_I9_N1E8_MBPS, 1),
             "baseline_ref": "paper Table 2, i9-9900k CPU, 100M-bit block: 140.96 Mbps (context)",
             "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"G_cd hash, one key of n={n} bits, m={m} output bits per step",
-                       "transform": f"Goldilocks NTT length {N}", "seeds": f"{ROTATE} rotating blocks",
-                       "product": ({"kind": "wrapped (cyclic) product, certified by the carry step",
-                                    "length": N, "full_length": plan["full"], "dropped_coefficients":
-                                    plan["dropped"], "full_product_runs_in_timed_steps": res["flags"]}
-                                   if plan["dropped"] else {"kind": "full-length product", "length": N}),
-                       "plan_variant": res["variant"],
-                       "l2": f"inputs rotate over {ROTATE} blocks ({ROTATE * 3 * ((n + 63) // 64) * 8 / 1e6:.0f}"
-                             f" MB) plus {2 * N * 8 / 1e6:.0f} MB workspace per step, > 129 MB L2",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(n, m, world),
+            "plan": {"transform": f"Goldilocks NTT length {N}", "plan_variant": res["variant"],
+                     "workspace_mb_per_step": round(2 * N * 8 / 1e6),
+                     "product": ({"kind": "wrapped (cyclic) product, certified by the carry step",
+                                  "length": N, "full_length": plan["full"], "dropped_coefficients":
+                                  plan["dropped"], "full_product_runs_in_timed_steps": res["flags"]}
+                                 if plan["dropped"] else {"kind": "full-length product", "length": N})},
+            "windows": {"count": len(res["windows"]), "steps_each": K,
+                        "ms_per_step": [round(w / K, 4) for w in res["windows"]],
+                        "note": "value and ms_per_step are the median window"},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"],
                     "api": "pa_hash_host_async back to back on pinned buffers, host clock to the final sync "
@@ -805,6 +1015,9 @@ def main():
                 "value": round(aggregate_mbps(world, 1, n, res["seeded_ms"]), 1), "unit": UNIT,
                 "note": "same workload, multiplier's transform computed once (pa_hash_seeded)"},
             "n1e6": res["small"],
+            "batched": res["batched"],
+            "served": res["served"],
+            "served_sweep": res["served_sweep"],
             "toeplitz": res["toeplitz"],
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in res["kstats"].items()},
             "roofline": roofline,

@@ -181,19 +181,27 @@ int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream);
  * alone. The block's buffers must stay valid until its ticket completes.
  * ------------------------------------------------------------------------ */
 typedef struct {
-    int device;                /* CUDA device of the serving loop; -1 = the current one */
     uint32_t max_batch;        /* blocks per device batch (0 = 64) */
     uint32_t streams;          /* concurrent device batches (0 = 2, at most 8) */
     uint32_t max_pending;      /* queue length before pa_submit returns PA_EAGAIN (0 = 65536) */
+    uint32_t idle_poll_us;     /* how long the loop keeps polling (for new requests and for
+                                  completions) after its last event before it sleeps until
+                                  the next pa_submit; 0 = always poll (lowest latency; the
+                                  loop then keeps one host core busy while it runs) */
     uint64_t hbm_budget_bytes; /* admission budget (0 = half of the free device memory) */
 } pa_config;
 
 /*
- * pa_init: start the serving loop with `cfg` (NULL = defaults on the current
- * device). Optional: the first pa_submit starts it with defaults. PA_EINVAL if
- * it is already running (stop it first).
+ * pa_init: start the serving loop on CUDA device `device` (-1 = the calling
+ * thread's current device) with `cfg` (NULL = defaults). Optional: the first
+ * pa_submit starts it with defaults on the current device. PA_EINVAL if it is
+ * already running (stop it first) or device is not a valid device number.
+ * Completion: the loop polls an event recorded behind each batch; a ticket
+ * completes when the loop has seen its batch's event, and its status is that
+ * of the batch's stream (PA_ETIMEOUT if a bounded wait of the library's
+ * kernels ran out in that batch, PA_ECUDA on a CUDA error).
  */
-int pa_init(const pa_config* cfg);
+int pa_init(int device, const pa_config* cfg);
 
 /*
  * pa_submit: queue one block (device pointers, as in pa_block) and return its
@@ -424,17 +432,29 @@ int pa_leftover_epsilon(double hmin_bits, uint64_t r, double eps, double* eps_ba
  * is available from pa_last_error().
  * The first call on a device does the set-up: it looks up the arrays' device
  * addresses, fills the twiddle tables on `stream` and waits for them. Make that
- * first call before any stream capture. Later calls only queue kernels.
+ * first call before any stream capture: a first call on a capturing stream
+ * returns PA_EINVAL and leaves the capture as it was. Later calls only queue
+ * kernels. pa_shutdown forgets the set-up; call it before a device reset
+ * (cudaDeviceReset), so that the next call sets up again on the new context.
  * All calls share the one scratch area and it keeps the previous call's
- * contents (every word is rewritten before it is read, so nothing needs
- * clearing). Calls whose work overlaps on the GPU (different streams, or
- * unordered use from several threads) race on the scratch and give wrong
- * results: order them on one stream or with events.
+ * contents: the transform buffers are rewritten before they are read, and the
+ * carry step's tile states, which must start at zero, are cleared by a
+ * cudaMemsetAsync on `stream` before each carry launch. Calls whose work
+ * overlaps on the GPU (different streams, or unordered use from several
+ * threads) race on the scratch and give wrong results: order them on one
+ * stream or with events. A bounded-wait timeout in this call is reported by
+ * pa_device_status only (the per-stream words of pa_stream_status are library
+ * allocations, which this entry point does not make).
  */
 int pa_hash_noalloc(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
                     uint64_t n, uint64_t m, uint64_t* out, void* stream);
 
-/* pa_shutdown: free tables and pooled memory of all devices (no work may be in flight). */
+/*
+ * pa_shutdown: free tables, pooled memory and status words of all devices, stop
+ * nothing else (no work may be in flight). Call it before resetting a device
+ * that the library has used (cudaDeviceReset): the next call then sets up
+ * again, including pa_hash_noalloc's scratch addresses.
+ */
 int pa_shutdown(void);
 
 /*
@@ -445,6 +465,23 @@ int pa_shutdown(void);
  * context stays usable), else PA_OK. clear != 0 resets the flag.
  */
 int pa_device_status(int clear);
+
+/*
+ * pa_stream_status: the status of the library's work queued on `stream` so far
+ * (cudaStream_t as void*, NULL = the legacy default stream), without waiting for
+ * other streams: it queues a copy of the stream's status word behind that work
+ * (and, with clear != 0, a reset of the word), waits for `stream` alone, and
+ * returns PA_ETIMEOUT if a kernel of this library on that stream has given up a
+ * bounded wait since the word was last cleared (that call's output is wrong; the
+ * context stays usable), PA_ECUDA if the stream reports a CUDA error, else
+ * PA_OK. The library keeps one word per stream handle for the first 4096
+ * handles it sees on a device (later ones share the last word); a stream
+ * created after another was destroyed may get the same handle, and then its
+ * word: clear it (clear != 0) before relying on it. Work replayed from a
+ * pa_batch graph marks the word of the stream it was captured on, and
+ * pa_hash_noalloc marks none: their timeouts are reported by pa_device_status.
+ */
+int pa_stream_status(void* stream, int clear);
 
 /* Fault injection for tests of the timeout path (faults nothing on the GPU). */
 #define PA_FAULT_CARRY_WAIT 1 /* the next carry launch never processes its first tile,

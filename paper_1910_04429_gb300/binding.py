@@ -62,7 +62,8 @@ _SIGS = {
     "pa_wrap_flags": ([ctypes.POINTER(ctypes.c_uint64), ctypes.c_int], ctypes.c_int),
     "pa_shutdown": ([], ctypes.c_int),
     "pa_profile": ([ctypes.c_int], ctypes.c_int),
-    "pa_init": ([ctypes.c_void_p], ctypes.c_int),
+    "pa_init": ([ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "pa_stream_status": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "pa_submit": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "pa_poll": ([ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pa_serve_stats": ([ctypes.c_void_p], ctypes.c_int),
@@ -91,8 +92,8 @@ class PaKernelStat(ctypes.Structure):
 class PaConfig(ctypes.Structure):
     """Mirror of ``pa_config`` in include/pa.h."""
 
-    _fields_ = [("device", ctypes.c_int), ("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32),
-                ("max_pending", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64)]
+    _fields_ = [("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("max_pending", ctypes.c_uint32),
+                ("idle_poll_us", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64)]
 
 
 class PaServeStats(ctypes.Structure):
@@ -338,9 +339,10 @@ def hash_batched(blocks, stream=None):
 
 
 def serve_init(device: int = -1, max_batch: int = 0, streams: int = 0, max_pending: int = 0,
-               hbm_budget_bytes: int = 0):
-    cfg = PaConfig(device, max_batch, streams, max_pending, hbm_budget_bytes)
-    _check(load().pa_init(ctypes.byref(cfg)), "pa_init")
+               hbm_budget_bytes: int = 0, idle_poll_us: int = 0):
+    """pa_init(device, cfg): start the serving loop (device -1: the current one)."""
+    cfg = PaConfig(max_batch, streams, max_pending, idle_poll_us, hbm_budget_bytes)
+    _check(load().pa_init(device, ctypes.byref(cfg)), "pa_init")
 
 
 def submit(key, seed_a, seed_b, n: int, m: int, out) -> int:
@@ -496,6 +498,12 @@ def profile_collect() -> dict:
 def device_status(clear: bool = False) -> int:
     """PA_OK, or PA_ETIMEOUT if a bounded device wait ran out since the last clear."""
     return int(load().pa_device_status(1 if clear else 0))
+
+
+def stream_status(stream=None, clear: bool = False) -> int:
+    """pa_stream_status: PA_OK, or PA_ETIMEOUT if a bounded wait of the library's
+    kernels ran out on this stream (waits for that stream only)."""
+    return int(load().pa_stream_status(_stream_ptr(stream), 1 if clear else 0))
 
 
 def fault_inject(what: int = PA_FAULT_CARRY_WAIT):

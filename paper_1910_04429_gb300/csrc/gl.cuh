@@ -7,7 +7,9 @@
 // and 8 = 2^3 a primitive 64-th root: DFTs of length <= 64 need no general
 // multiplies, only the shift-multiplies below.
 //
-// All values are kept canonical (in [0, p)).
+// Field values are kept in [0, p] (p may stand for 0 inside a transform; see
+// sub below), and canon() maps them to [0, p) where an exact integer leaves
+// the field.
 #pragma once
 #include <stdint.h>
 

@@ -47,7 +47,17 @@ struct Device {
     cudaStream_t copy = nullptr;
     cudaEvent_t xa_ready = nullptr, b_ready = nullptr, done[2] = {};
     u64 host_calls = 0;
+    // per-stream status words (pa_stream_status): a device slab of STATUS_SLOTS
+    // words, its pinned host mirror, and the slot of each stream seen (by stream id)
+    u32* status_dev = nullptr;
+    u32* status_host = nullptr;
+    bool status_failed = false;
+    std::unordered_map<const void*, int> status_slot;  // by stream handle
 };
+
+// Streams that get a status word of their own; later streams share the last
+// slot (their bounded-wait timeouts are then reported for all of them).
+constexpr int STATUS_SLOTS = 4096;
 
 std::mutex g_mu;
 std::unordered_map<int, Device> g_dev;
@@ -301,7 +311,9 @@ int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint
         state = (u32*)p;
     }
     CarryJob c{coef, L, seed_b, n, m, out, state, zeroed_state != nullptr};
-    cudaError_t e = launch_carry(c, st);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = launch_carry(c, st, status_word(dev, st));
     if (e != cudaSuccess) return cuda_fail(e, "carry launch");
     return PA_OK;
 }
@@ -414,16 +426,18 @@ int hash_product(HashPlan& hp, cudaStream_t st) {
 }
 
 // Steps 6-7: the carry step; after a wrapped product, the recomputation.
-int hash_finish(HashPlan& hp, const uint64_t* seed_b, uint64_t n, uint64_t m, uint64_t* out, cudaStream_t st) {
+int hash_finish(HashPlan& hp, const uint64_t* seed_b, uint64_t n, uint64_t m, uint64_t* out, cudaStream_t st,
+                int dev) {
     const u64 L = (n + 15) / 16;
     u32* flag = hp.wp.on ? hp.state + carry_flag_word(n) : nullptr;
+    u32* sw = status_word(dev, st);
     CarryJob c{hp.prod.buf_x, L, seed_b, n, m, out, hp.state, true, hp.wp.lo, flag, g_wrap_mode == 3};
-    cudaError_t e = launch_carry(c, st);
+    cudaError_t e = launch_carry(c, st, sw);
     if (e != cudaSuccess) return cuda_fail(e, "carry launch");
     if (hp.wp.on) {
         hp.fb.b = seed_b;
         hp.fb.out = out;
-        if ((e = launch_fallback(&hp.fb, 1, st)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
+        if ((e = launch_fallback(&hp.fb, 1, st, sw)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
     }
     return PA_OK;
 }
@@ -434,7 +448,7 @@ int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* see
     HashPlan hp;
     int rc = hash_prepare(key, seed_a, n, m, scr, dev, &hp);
     if (!rc) rc = hash_product(hp, st);
-    if (!rc) rc = hash_finish(hp, seed_b, n, m, out, st);
+    if (!rc) rc = hash_finish(hp, seed_b, n, m, out, st, dev);
     return rc;
 }
 
@@ -561,18 +575,55 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
             (e = cudaStreamWaitEvent(st, d.join[i], 0)) != cudaSuccess)
             return cuda_fail(e, "join");
     }
-    if ((e = launch_carry_batch(cj.data(), (int)count, st)) != cudaSuccess)
+    u32* sw = status_word(dev, st);
+    if ((e = launch_carry_batch(cj.data(), (int)count, st, sw)) != cudaSuccess)
         return cuda_fail(e, "batched carry launch");
-    if (!fj.empty() && (e = launch_fallback(fj.data(), (int)fj.size(), st)) != cudaSuccess)
+    if (!fj.empty() && (e = launch_fallback(fj.data(), (int)fj.size(), st, sw)) != cudaSuccess)
         return cuda_fail(e, "recomputation launch");
     return PA_OK;
+}
+
+// The device's status slab, allocated (and cleared) on the first call on the
+// device, which is also when the pool and the first tables are made.
+void status_slab(int dev) {
+    Device& d = g_dev[dev];
+    if (d.status_dev || d.status_failed) return;
+    u32* p = nullptr;
+    u32* h = nullptr;
+    cudaError_t e = cudaMalloc(&p, STATUS_SLOTS * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMemset(p, 0, STATUS_SLOTS * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMallocHost(&h, STATUS_SLOTS * sizeof(u32));
+    if (e != cudaSuccess) {
+        if (p) cudaFree(p);
+        d.status_failed = true;  // the kernels then report through the device-wide word only
+        cudaGetLastError();
+        return;
+    }
+    memset(h, 0, STATUS_SLOTS * sizeof(u32));
+    d.status_dev = p;
+    d.status_host = h;
 }
 
 int setup(int* dev, cudaMemPool_t* pool) {
     int rc = current_device(dev);
     if (rc) return rc;
     load_tune_cache(*dev);
+    status_slab(*dev);
     return get_pool(*dev, pool);
+}
+
+// Slot of stream st on device dev (-1 without a slab). Streams are told apart
+// by their handle, with no CUDA call (queries such as cudaStreamGetId are not
+// allowed while a stream is being captured into a graph).
+int status_slot_of(int dev, cudaStream_t st) {
+    Device& d = g_dev[dev];
+    if (!d.status_dev) return -1;
+    auto it = d.status_slot.find((const void*)st);
+    if (it != d.status_slot.end()) return it->second;
+    int slot = (int)d.status_slot.size();
+    if (slot >= STATUS_SLOTS) slot = STATUS_SLOTS - 1;
+    d.status_slot[(const void*)st] = slot;
+    return slot;
 }
 
 // Host buffers in, host buffer out, queued without waiting: x and a are copied
@@ -629,7 +680,7 @@ int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t*
         // the result goes to device memory and is copied back (writing it into a
         // mapped pinned buffer from the carry kernel measured slower)
         if ((rc = scr.get(out_bytes, &mo))) return rc;
-        if ((rc = hash_finish(hp, (const u64*)db, n, m, (u64*)mo, st))) return rc;
+        if ((rc = hash_finish(hp, (const u64*)db, n, m, (u64*)mo, st, dev))) return rc;
         if ((e = cudaMemcpyAsync(out, mo, out_bytes, cudaMemcpyDeviceToHost, st)))
             return cuda_fail(e, "cudaMemcpyAsync(D2H)");
     }
@@ -699,6 +750,31 @@ std::vector<ProfRec> g_prof;
 
 namespace pa {
 void set_error(const char* msg) { g_err = msg; }
+
+u32* status_word(int dev, cudaStream_t st) {
+    int slot = status_slot_of(dev, st);
+    return slot < 0 ? nullptr : g_dev[dev].status_dev + slot;
+}
+
+int queue_status_read(cudaStream_t st, bool clear, const volatile u32** host_word) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
+    int slot = status_slot_of(dev, st);
+    if (slot < 0) {
+        *host_word = nullptr;
+        return PA_OK;
+    }
+    Device& d = g_dev[dev];
+    cudaError_t e = cudaMemcpyAsync(d.status_host + slot, d.status_dev + slot, sizeof(u32),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && clear) e = cudaMemsetAsync(d.status_dev + slot, 0, sizeof(u32), st);
+    if (e != cudaSuccess) return cuda_fail(e, "status word read");
+    *host_word = d.status_host + slot;
+    return PA_OK;
+}
 
 void prof_begin(cudaStream_t st, const char* name) {
     if (!g_prof_on) return;
@@ -1051,15 +1127,16 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
         j.da = Digits{reinterpret_cast<const uint16_t*>(seed->limbs), j.L, top_digit_mask(n)};
         if ((e = launch_convolution_seeded(j, st)) != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
         u32* flag = state + carry_flag_word(n);
+        u32* sw = status_word(dev, st);
         CarryJob c{j.buf_x, j.L, seed_b, n, m, out, state, true, wp.lo, flag, g_wrap_mode == 3};
-        if ((e = launch_carry(c, st)) != cudaSuccess) return cuda_fail(e, "carry launch");
+        if ((e = launch_carry(c, st, sw)) != cudaSuccess) return cuda_fail(e, "carry launch");
         FallbackJob f;
         if ((rc = fallback_job(dev, n, m, j.dx, j.da, (u64*)bx, (u64*)ba, state + carry_state_words(n), flag,
                                &f)))
             return rc;
         f.b = seed_b;
         f.out = out;
-        if ((e = launch_fallback(&f, 1, st)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
+        if ((e = launch_fallback(&f, 1, st, sw)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
         return PA_OK;
     }
     NttJob j;
@@ -1332,6 +1409,8 @@ int pa_shutdown(void) {
             for (cudaEvent_t ev : kv.second.done) cudaEventDestroy(ev);
         }
         if (kv.second.pool) cudaMemPoolDestroy(kv.second.pool);
+        if (kv.second.status_dev) cudaFree(kv.second.status_dev);
+        if (kv.second.status_host) cudaFreeHost(kv.second.status_host);
         if (kv.second.fork) {
             cudaEventDestroy(kv.second.fork);
             for (int i = 0; i < SIDE_STREAMS; i++) {
@@ -1341,6 +1420,7 @@ int pa_shutdown(void) {
         }
     }
     g_dev.clear();
+    noalloc_reset();
     if (prev >= 0) cudaSetDevice(prev);
     return PA_OK;
 }
@@ -1354,6 +1434,18 @@ int pa_device_status(int clear) {
     if ((e = read_fallback_status(&fst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
     if (st & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (carry look-back)");
     if (fst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (recomputation barrier)");
+    return PA_OK;
+}
+
+int pa_stream_status(void* stream, int clear) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const volatile u32* word = nullptr;
+    int rc = queue_status_read(st, clear != 0, &word);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (word && (*word & PA_STATUS_TIMEOUT))
+        return fail(PA_ETIMEOUT, "a bounded device wait ran out on this stream");
     return PA_OK;
 }
 

@@ -26,6 +26,8 @@
 // output) and sets job.flag when it is all ones: only then can the dropped
 // coefficients change the output, and the exact recomputation queued behind
 // this launch (pa_fallback.cu) runs.
+#include <atomic>
+
 #include "carry.cuh"
 #include "pdl.cuh"
 
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
                                                  : (s & (ST_AGG | ST_INC)) != 0)) {
                         if (++spins > spin_limit) {
                             atomicOr(&g_status, PA_STATUS_TIMEOUT);
+                            if (cb.status) atomicOr(cb.status, PA_STATUS_TIMEOUT);
                             s = ST_INC;  // give up: treat as an inclusive prefix (0, 0)
                             break;
                         }
@@ -184,9 +187,10 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static u32 g_inject_ticket = 0;  // armed by fault_inject_carry(); consumed by the next launch
+// armed by fault_inject_carry() from any host thread; taken (and cleared) by the next launch
+static std::atomic<u32> g_inject_ticket{0};
 
-void fault_inject_carry() { g_inject_ticket = 1; }
+void fault_inject_carry() { g_inject_ticket.store(1); }
 
 template <int B>
 static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
@@ -199,9 +203,8 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
         cudaError_t e = cudaMemsetAsync(cb.job[i].state, 0, (tt + 1) * sizeof(u32), st);
         if (e != cudaSuccess) return e;
     }
-    u32 start = g_inject_ticket;
+    u32 start = g_inject_ticket.exchange(0);
     u32 limit = start ? 1000u : CARRY_SPIN_LIMIT;
-    g_inject_ticket = 0;
     bool vec = true;
     for (int i = 0; i < cb.count; i++)
         vec = vec && (uintptr_t)cb.job[i].coef % 16 == 0 && (uintptr_t)cb.job[i].b % 16 == 0 &&
@@ -214,17 +217,19 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     return e;
 }
 
-cudaError_t launch_carry(const CarryJob& c, cudaStream_t st) {
+cudaError_t launch_carry(const CarryJob& c, cudaStream_t st, u32* status) {
     CarryBatch<1> cb;
     cb.count = 1;
+    cb.status = status;
     cb.job[0] = c;
     return launch_carry_b<1>(cb, st);
 }
 
-cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st) {
+cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st, u32* status) {
     for (int i = 0; i < count; i += MAX_BATCH) {
         CarryBatch<MAX_BATCH> cb;
         cb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
+        cb.status = status;
         for (int k = 0; k < cb.count; k++) cb.job[k] = jobs[i + k];
         cudaError_t e = launch_carry_b<MAX_BATCH>(cb, st);
         if (e != cudaSuccess) return e;

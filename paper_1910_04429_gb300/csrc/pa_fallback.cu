@@ -36,6 +36,7 @@ struct GridBarrier {
     u32 ctas;
     u32 passed;  // barriers this CTA has passed
     u32 limit;
+    u32* status; // the launching stream's status word, or null
 };
 
 // All CTAs of the grid reach this point before any leaves it; their global
@@ -53,6 +54,7 @@ __device__ __forceinline__ void grid_sync(GridBarrier& g) {
             if (v >= target) break;
             if (++spins > g.limit) {
                 atomicOr(&g_fb_status, PA_STATUS_TIMEOUT);
+                if (g.status) atomicOr(g.status, PA_STATUS_TIMEOUT);
                 break;
             }
             __nanosleep(128);
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_fallback(const __grid_constan
     }
     __syncthreads();
     if (!any_sh) return;  // the common case: every wrapped product was certified
-    GridBarrier bar{fb.barrier, gridDim.x, 0, spin_limit};
+    GridBarrier bar{fb.barrier, gridDim.x, 0, spin_limit, fb.status};
     for (int i = 0; i < fb.count; i++) {
         const FallbackJob& f = fb.job[i];
         if (__ldcg(f.flag) == 0) continue;  // the same answer in every CTA
@@ -223,7 +225,7 @@ static int fb_grid(int dev) {  // CTAs that can all be resident at once
     return cached[dev];
 }
 
-cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st) {
+cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st, u32* status) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -232,6 +234,7 @@ cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st)
     for (int i = 0; i < count; i += FB_BATCH) {
         FallbackBatch<FB_BATCH> fb;
         fb.count = count - i < FB_BATCH ? count - i : FB_BATCH;
+        fb.status = status;
         for (int k = 0; k < fb.count; k++) fb.job[k] = jobs[i + k];
         // the barrier counter: the (zeroed, otherwise unused) ticket word of the first job's states
         fb.barrier = fb.job[0].state + carry_tiles(fb.job[0].n);

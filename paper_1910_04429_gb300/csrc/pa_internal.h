@@ -67,6 +67,7 @@ struct CarryJob {
 template <int B>
 struct CarryBatch {
     int count;
+    u32* status;      // the launching stream's status word (PA_STATUS_* bits), or null
     CarryJob job[B];
 };
 constexpr int CARRY_THREADS = 128;
@@ -85,9 +86,11 @@ GL_HD u64 first_out_tile(u64 n, u64 m, bool check = false) {
     u64 q = (n - m) / 64;
     return (check && q ? q - 1 : q) / CARRY_TILE_LIMBS;
 }
-cudaError_t launch_carry(const CarryJob& job, cudaStream_t st);
+// status: the stream's status word, which a launch that gives up a bounded wait
+// marks with PA_STATUS_TIMEOUT (as well as the device-wide sticky word), or null.
+cudaError_t launch_carry(const CarryJob& job, cudaStream_t st, u32* status = nullptr);
 // Carry steps of `count` independent blocks (any sizes), MAX_BATCH per launch.
-cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st);
+cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st, u32* status = nullptr);
 // The next carry launch leaves its first tile unprocessed, so the wait of the
 // second tile on it runs out (bounded, short limit): a host-armed test of the
 // timeout path that faults nothing.
@@ -117,10 +120,11 @@ template <int B>
 struct FallbackBatch {
     int count;
     u32* barrier;       // zeroed word: the grid barrier's counter
+    u32* status;        // the launching stream's status word, or null
     FallbackJob job[B];
 };
 // One cooperative launch per 64 jobs; it returns at once unless a flag is set.
-cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st);
+cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st, u32* status = nullptr);
 cudaError_t read_fallback_status(u32* out, bool clear);
 
 // Inter-pass twiddle tables of a strided pass (M = sub-problem size, S =
@@ -138,5 +142,19 @@ void prof_end(cudaStream_t st);
 
 // Sets the text pa_last_error() returns on the calling thread.
 void set_error(const char* msg);
+
+// Per-stream status words (pa_stream_status). status_word: the device word
+// the library's kernels on stream st mark when a bounded wait runs out (a slot
+// of a per-device slab; null if the slab could not be set up). The caller
+// holds the library lock. queue_status_read: queues on st a copy of st's word
+// into pinned host memory (then, with clear, a reset of the word) and returns
+// the host word's address, valid once st has passed the copy; PA_OK or a
+// status code.
+u32* status_word(int dev, cudaStream_t st);
+int queue_status_read(cudaStream_t st, bool clear, const volatile u32** host_word);
+
+// pa_hash_noalloc's per-device set-up is forgotten (pa_shutdown): the next
+// call looks its scratch up again.
+void noalloc_reset();
 
 }  // namespace pa

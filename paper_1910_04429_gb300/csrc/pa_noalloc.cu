@@ -15,11 +15,15 @@
 //
 // The first call on a device performs that set-up and also fills the twiddle
 // tables on the caller's stream and waits for them; make the first call before
-// any stream capture. All calls share the same arrays and the arrays keep the
-// last call's contents: every scratch word is written before it is read in a
-// call, so nothing needs clearing, but calls that overlap on the GPU (on
-// different streams, or on one stream from several threads without ordering)
-// race on the scratch and give wrong results.
+// any stream capture (a first call on a capturing stream is refused, leaving
+// the capture intact). pa_shutdown forgets the set-up, so that after a device
+// reset the next call looks the arrays up again. All calls share the same
+// arrays and the arrays keep the last call's contents: the transform buffers
+// are written before they are read in a call, and the carry step's tile
+// states, which must start at zero, are cleared on the stream by a memset
+// before each carry launch (a memset allocates nothing). Calls that overlap on
+// the GPU (on different streams, or on one stream from several threads
+// without ordering) race on the scratch and give wrong results.
 #include <mutex>
 
 #include "../../include/pa.h"
@@ -76,6 +80,17 @@ __global__ void k_na_tables(u64* tab, u64 nh, u64 w4, u64 w4i, u64 w, u64 wi, u6
 int na_setup(int dev, cudaStream_t st, NaDevice** out) {
     NaDevice& d = g_na_dev[dev];
     if (!d.ready) {
+        // the set-up launches kernels and waits for them: on a capturing stream
+        // that would end the caller's capture, so refuse and leave it intact
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+            set_error("pa_hash_noalloc: cudaStreamIsCapturing failed");
+            return PA_ECUDA;
+        }
+        if (cap != cudaStreamCaptureStatusNone) {
+            set_error("pa_hash_noalloc: the first call on a device (its set-up) must not be on a capturing stream");
+            return PA_EINVAL;
+        }
         cudaError_t e = cudaGetSymbolAddress((void**)&d.work, g_na_work);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.tables, g_na_tables);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.carry, g_na_carry);
@@ -103,6 +118,13 @@ int na_setup(int dev, cudaStream_t st, NaDevice** out) {
 }
 
 }  // namespace
+
+namespace pa {
+void noalloc_reset() {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    for (NaDevice& d : g_na_dev) d = NaDevice{};
+}
+}  // namespace pa
 
 extern "C" int pa_hash_noalloc(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
                                uint64_t n, uint64_t m, uint64_t* out, void* stream) {

@@ -95,13 +95,32 @@ inline Geom choose_geom_len(uint64_t need) {
 // ... that holds the linear convolution of two L-digit operands.
 inline Geom choose_geom(uint64_t L) { return choose_geom_len(2 * L - 1); }
 
+// Digit width. Algorithm 1 splits the operands into pieces of M bits; here a
+// piece (digit) has w bits, 16 <= w <= 20. The product's coefficients
+// t_k = sum_{i+j=k} x_i a_j are below L (2^w - 1)^2 (L = ceil(n/w) digits), and
+// the transform over GF(p) is exact when that bound is below p. Wider digits
+// mean fewer of them and a shorter transform: at n = 10^8 20-bit digits are
+// exact (5 * 10^6 digits, bound < 2^62.3) and need 3/4 of the 16-bit length.
+constexpr int DIGIT_MIN = 16, DIGIT_MAX = 20;
+
+inline uint64_t digits_for(uint64_t n, int w) { return (n + (uint64_t)w - 1) / (uint64_t)w; }
+
+// L (2^w - 1)^2 < p, i.e. L <= (p - 1) / (2^w - 1)^2
+inline bool width_exact(uint64_t n, int w) {
+    if (w < DIGIT_MIN || w > DIGIT_MAX) return false;
+    uint64_t d = (1ull << w) - 1;
+    return digits_for(n, w) <= (gl::P - 1) / (d * d);
+}
+
 // Wrapped product for the modular hash (the output is bits [n-m, n) of
 // (a x + b) mod 2^n). A cyclic convolution of length N, L <= N < 2L - 1, gives
 // c_k = t_k + t_{k+N}, where t_k is the linear coefficient; t_{k+N} = 0 for
-// k >= W = 2L - 1 - N, so every c_k with k >= lo (lo >= W) is exact. The
-// coefficients below lo are dropped: what they would add,
-// T = sum_{k<lo} t_k 2^(16k), is below lo * 2^(16(lo+1)) <= 2^wbits. The exact
-// Q = sum_{k>=lo} c_k 2^(16k) + b then differs from a x + b by T alone, and T
+// k >= W = 2L - 1 - N, so every c_k with k >= lo (lo >= W) is exact. (The
+// folded terms t_{k+N} weigh 2^(w(k+N)) >= 2^(wL) >= 2^n: they vanish mod 2^n
+// in the true product.) The coefficients below lo are dropped: what they would
+// add, T = sum_{k<lo} t_k 2^(wk) <= lo (2^w - 1)(2^(w lo) - 1), is below
+// lo * 2^(w(lo+1)) <= 2^wbits, wbits = w (lo + 1) + bit_length(lo). The exact
+// Q = sum_{k>=lo} c_k 2^(wk) + b then differs from a x + b by T alone, and T
 // changes the carry into bit n - m only if every bit of Q in [wbits, n - m)
 // is one. The carry step checks limb q - 1 of Q (q = floor((n - m)/64)), which
 // lies inside that range when wbits <= 64 (q - 1): if that limb is not all
@@ -120,12 +139,13 @@ inline int bit_length(uint64_t v) {
     return b;
 }
 
-// Whether a cyclic length N serves keys of n bits with m output bits (L digits).
-inline bool wrap_ok(uint64_t N, uint64_t L, uint64_t n, uint64_t m, uint64_t* lo_out) {
+// Whether a cyclic length N serves keys of n bits with m output bits (L digits
+// of w bits).
+inline bool wrap_ok(uint64_t N, uint64_t L, uint64_t n, uint64_t m, uint64_t* lo_out, int w = 16) {
     if (N < L || N >= 2 * L - 1) return false;
     uint64_t W = 2 * L - 1 - N, lo = W + (W & 1);
     uint64_t q = (n - m) / 64;
-    uint64_t wbits = 16 * (lo + 1) + (uint64_t)bit_length(lo);
+    uint64_t wbits = (uint64_t)w * (lo + 1) + (uint64_t)bit_length(lo);
     if (q < 1 || wbits > 64 * (q - 1)) return false;
     *lo_out = lo;
     return true;
@@ -136,16 +156,17 @@ inline bool wrap_ok(uint64_t N, uint64_t L, uint64_t n, uint64_t m, uint64_t* lo
 // recomputation's launch costs a few microseconds.
 constexpr uint64_t WRAP_MIN_FULL = 1ull << 19;
 
-// The shortest transform length that is a valid wrapped length; off when none
-// is shorter than the full-length product's, or that one is below min_full.
-inline WrapPlan wrap_plan(uint64_t n, uint64_t m, uint64_t min_full = WRAP_MIN_FULL) {
+// The shortest transform length that is a valid wrapped length for w-bit
+// digits; off when none is shorter than the full-length product's, or that one
+// is below min_full.
+inline WrapPlan wrap_plan(uint64_t n, uint64_t m, uint64_t min_full = WRAP_MIN_FULL, int w = 16) {
     WrapPlan wp;
-    uint64_t L = (n + 15) / 16;
+    uint64_t L = digits_for(n, w);
     Geom full = choose_geom(L);
     if (full.N < min_full) return wp;
     for (Geom g = choose_geom_len(L); g.N < full.N; g = choose_geom_len(g.N + 1)) {
         uint64_t lo;
-        if (wrap_ok(g.N, L, n, m, &lo)) {
+        if (wrap_ok(g.N, L, n, m, &lo, w)) {
             wp.on = true;
             wp.geom = g;
             wp.lo = lo;
@@ -153,6 +174,42 @@ inline WrapPlan wrap_plan(uint64_t n, uint64_t m, uint64_t min_full = WRAP_MIN_F
         }
     }
     return wp;
+}
+
+// The product one hash runs: the digit width, the digit count, the wrapped
+// plan (or off) and the full-length geometry at that width.
+struct DigitPlan {
+    int w = 16;
+    uint64_t L = 0;
+    WrapPlan wp;
+    Geom full;
+    uint64_t first_n() const { return wp.on ? wp.geom.N : full.N; }
+};
+
+// wrap: whether a wrapped product may run (min_full as for wrap_plan);
+// width: 0 chooses, among the exact widths, the one whose product is shortest
+// (the narrowest of equals: its digit split and carry are the cheapest), else
+// that width (16 when it is not exact for n).
+inline DigitPlan digit_plan(uint64_t n, uint64_t m, bool wrap, uint64_t min_full, int width = 0) {
+    DigitPlan best;
+    bool have = false;
+    for (int w = DIGIT_MIN; w <= DIGIT_MAX; w++) {
+        if (width && w != width) continue;
+        if (!width_exact(n, w)) continue;
+        DigitPlan d;
+        d.w = w;
+        d.L = digits_for(n, w);
+        d.full = choose_geom(d.L);
+        if (wrap) d.wp = wrap_plan(n, m, min_full, w);
+        if (!have || d.first_n() < best.first_n()) best = d, have = true;
+    }
+    if (!have) {  // a forced width that is not exact: 16-bit digits always are (n <= 2^31)
+        best.w = 16;
+        best.L = digits_for(n, 16);
+        best.full = choose_geom(best.L);
+        if (wrap) best.wp = wrap_plan(n, m, min_full, 16);
+    }
+    return best;
 }
 
 // A primitive (15 * 2^32)-th root W with W^(5 * 2^26) = 2, from which every

@@ -48,6 +48,12 @@ int main(int argc, char** argv) {
         fprintf(stderr, "pa_hash_host: %d %s\n", rc, pa_last_error());
         return 1;
     }
+    /* no bounded wait of the library's kernels ran out on this stream */
+    rc = pa_stream_status(NULL, 1);
+    if (rc != PA_OK) {
+        fprintf(stderr, "pa_stream_status: %d %s\n", rc, pa_last_error());
+        return 1;
+    }
     for (uint64_t i = 0; i < Mo; i++) printf("%016" PRIx64 "\n", out[i]);
     free(x), free(a), free(b), free(out);
     return pa_shutdown() == PA_OK ? 0 : 1;

@@ -15,6 +15,10 @@ def host(t) -> np.ndarray:
 def gpu_hash(binding, blk_x, blk_a, blk_b, n, m, stream=None):
     import torch
 
-    out = binding.hash(dev(blk_x), dev(blk_a), dev(blk_b), n, m, stream=stream)
+    if stream is None:
+        out = binding.hash(dev(blk_x), dev(blk_a), dev(blk_b), n, m)
+    else:
+        with torch.cuda.stream(stream):  # operands made and read on the hashing stream
+            out = binding.hash(dev(blk_x), dev(blk_a), dev(blk_b), n, m, stream=stream)
     torch.cuda.synchronize()
     return host(out)

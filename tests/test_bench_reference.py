@@ -41,6 +41,11 @@ def _check_line(line, gpus):
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     # value = steps * sample bits / total seconds, in the line's unit (Mbit/s)
     assert line["value"] == pytest.approx(100_000 / line["ms_per_step"] / 1e3, rel=1e-2)
+    # the same workload (config) as the device arm's line, on the bench's own block size
+    import bench
+
+    assert line["config"] == bench.bench_config(100_000, 25_000, gpus)
+    assert "n=100000, m=25000" in line["cpu_baseline"]["sample"]
 
 
 def test_reference_arm_single_process():

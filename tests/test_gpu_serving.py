@@ -1,8 +1,11 @@
-"""Batched and served forms: every result equals the block hashed alone.
+"""Batched and served forms: every result equals the block hashed alone and
+the oracle.
 
 The served loop admits blocks by device footprint and runs continuously
-formed batches on several streams; the tests compare each served result
-with pa_hash on the same block alone (exact equality: integer output).
+formed batches on several streams; the tests compare each served result with
+the oracle and with pa_hash on the same block alone (exact equality: integer
+output), so that a fault the served path shared with the plain path would
+still show.
 """
 import numpy as np
 import pytest
@@ -76,12 +79,24 @@ def test_captured_batch_replays_current_contents():
 
 
 def test_served_results_equal_alone():
+    """48 small blocks (10^3 to 4e6 bits) with five large ones (10^7 to 10^8 bits,
+    the top of the served workload's size range) mixed in: each served result
+    equals the oracle and the block hashed alone."""
     import torch
 
     binding.serve_stop()
     binding.serve_init(max_batch=8, streams=3)
     blks = inputs.make_batch(48, 1_000, 4_000_000, seed=77)
-    want = _alone(blks)
+    big = [inputs.make_block(n, int(n * r), seed=300 + i) for i, (n, r) in
+           enumerate([(10_000_019, 0.31), (23_456_789, 0.1), (47_000_001, 0.45), (71_234_567, 0.22),
+                      (100_000_000, 0.5)])]
+    for i, b in enumerate(big):  # spread through the stream of small ones
+        blks.insert(5 + 9 * i, b)
+    th = oracle.default_threads()
+    want = [oracle.pa_hash(b.x, b.a, b.b, b.n, b.m, threads=th) for b in blks]
+    alone = _alone(blks)
+    for w, a_ in zip(want, alone):
+        np.testing.assert_array_equal(a_, w)
     keep, tickets = [], []
     for b in blks:
         x, a, bb = dev(b.x), dev(b.a), dev(b.b)
@@ -92,8 +107,8 @@ def test_served_results_equal_alone():
         rc, st = binding.poll(tk, 30_000_000)
         assert rc == binding.PA_OK and st == binding.PA_OK
     torch.cuda.synchronize()
-    for (x, a, bb, o), w in zip(keep, want):
-        np.testing.assert_array_equal(host(o), w)
+    for b, (x, a, bb, o), w in zip(blks, keep, want):
+        np.testing.assert_array_equal(host(o), w, err_msg=f"n={b.n} m={b.m}")
     s = binding.serve_stats()
     assert s["completed"] == len(blks) and s["pending"] == 0
     assert 0 < s["p50_us"] <= s["p99_us"] <= s["max_us"]
