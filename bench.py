@@ -253,15 +253,15 @@ def kernel_src_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_bytes(name: str, n: int, m: int, N: int) -> float:
+def kernel_bytes(name: str, n: int, m: int, N: int, dbits: int = 16) -> float:
     """Bytes a launch of this kernel must read and write (its own inputs and
-    outputs; the transform's workspace words are 8 bytes)."""
-    L = (n + 15) // 16
+    outputs; the transform's workspace words are 8 bytes; digits of dbits bits)."""
+    L = -(-n // dbits)
     Ly = (n + 63) // 64
     Mo = (m + 63) // 64
     w = 8
     return {
-        "ntt_fwd_strided_first": 2 * L * 2 + 2 * N * w,       # digits of x, a in; both buffers out
+        "ntt_fwd_strided_first": 2 * n / 8 + 2 * N * w,       # bits of x, a in; both buffers out
         "ntt_fwd_strided_r64": 2 * (2 * N * w),               # both operands, read + write
         "ntt_contig_seed": 2 * N * w,
         "ntt_contig_fused": 3 * N * w,                        # x tile, a spectrum in; product out
@@ -450,7 +450,8 @@ def run_ours(args, rank, world, local):
     e2e_ms, e2e_sync_ms = max_over_ranks([e2e_ms, e2e_sync_ms], world, dev)
     return dict(ms_total=ms_total, windows=windows, e2e_ms=e2e_ms, e2e_sync_ms=e2e_sync_ms, kstats=kstats,
                 clocks=clk, latency=latency, h2d=3 * L * 8, d2h=Mo * 8, seeded_ms=seeded_ms, variant=variant,
-                small=small, toeplitz=toep, flags=flags, plan=binding.plan_info(n, m), full_ms=full_ms,
+                small=small, toeplitz=toep, flags=flags,
+                plan=dict(binding.plan_info(n, m), digit_bits=binding.plan_digits(n, m)), full_ms=full_ms,
                 batched=batched, served=served, served_sweep=sweep, sms=sm_count(dev))
 
 
@@ -951,7 +952,7 @@ def main():
         SMS = res["sms"]
         alu_peak = SMS * ALU_LANES_PER_SM * mhz * 1e6 / 1e12   # T int ops / s
         ops = alu_ops(name, N)
-        hbm_achieved = kernel_bytes(name, n, m, N) / per_launch_s / 1e9
+        hbm_achieved = kernel_bytes(name, n, m, N, plan["digit_bits"]) / per_launch_s / 1e9
         traffic = None
         if TRAFFIC["kernel"] == name and TRAFFIC["src_sha"] == kernel_src_sha():
             traffic = TRAFFIC["bytes"]
@@ -992,6 +993,7 @@ def main():
             "dtype": "u64", "data": "synthetic",
             "config": bench_config(n, m, world),
             "plan": {"transform": f"Goldilocks NTT length {N}", "plan_variant": res["variant"],
+                     "digit_bits": plan["digit_bits"],
                      "workspace_mb_per_step": round(2 * N * 8 / 1e6),
                      "product": ({"kind": "wrapped (cyclic) product, certified by the carry step",
                                   "length": N, "full_length": plan["full"], "dropped_coefficients":

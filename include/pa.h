@@ -10,7 +10,7 @@
  * public seed (c, d) (Sec. 2.2: Alice and Bob publicly pick one g from the
  * family and apply it to their identical strings). Here c is called seed_a
  * and d seed_b. The product is exact: an NTT over the Goldilocks prime
- * 2^64 - 2^32 + 1 on 16-bit digits (Algorithm 1, Sec. 3.2.2, with GF(p) in
+ * 2^64 - 2^32 + 1 on 16- to 20-bit digits (Algorithm 1, Sec. 3.2.2, with GF(p) in
  * place of GMP's Fermat ring), then carry resolve, + d, mod 2^n and
  * extraction of the m most significant bits of the n-bit field (Sec. 3.2.3-
  * 3.2.5).
@@ -72,7 +72,7 @@ extern "C" {
  *
  * Only bits [n-m, n) of the product mod 2^n reach the output, so where it is
  * shorter the product runs as a cyclic convolution of length N < 2L - 1
- * (L = ceil(n/16) digits) whose wrapped-around part lands on the lowest
+ * (L = ceil(n/w) digits of w bits, see pa_digit_width) whose wrapped-around part lands on the lowest
  * coefficients; those are dropped. The carry step then checks the limb of the
  * exact remaining sum just below bit n - m: unless all 64 of its bits are one,
  * the dropped part cannot reach the output and the result is exact. If they
@@ -273,7 +273,8 @@ int pa_prepare(uint64_t n);
  * that length on the current device; later calls (single, batched, seeded,
  * served) use it. With the environment variable PA_TUNE_CACHE naming a file,
  * choices are saved there per GPU name and loaded on first use.
- * pa_plan_override forces a variant for the length of n (-1 clears; for
+ * pa_plan_override forces a variant for the length of the full-length
+ * (unwrapped) product of n-bit keys at the current digit width (-1 clears; for
  * tests). Results are identical under every plan.
  */
 #define PA_PLAN_R0_LAST 1
@@ -282,6 +283,9 @@ int pa_prepare(uint64_t n);
 #define PA_PLAN_NARROW 8
 int pa_autotune(uint64_t n, int reps, int* variant_out);
 int pa_plan_override(uint64_t n, int variant);
+/* pa_plan_override_length: the same for the transform length N itself (a length
+ * pa_plan_info reports); PA_EINVAL if N is not one of the library's lengths. */
+int pa_plan_override_length(uint64_t N, int variant);
 
 /* pa_workspace_bytes: device workspace one pa_hash of n bits draws from the pool
  * (two buffers of the recomputation's power-of-two length, which also hold the
@@ -312,6 +316,25 @@ uint64_t pa_workspace_bytes(uint64_t n);
 int pa_plan_info(uint64_t n, uint64_t m, uint64_t info[3]);
 int pa_wrap_mode(int mode);
 int pa_wrap_flags(uint64_t* count, int clear);
+
+/*
+ * Digit width. Algorithm 1 (Sec. 3.2.2) splits the operands into pieces; here
+ * a piece (digit) has w bits, 16 <= w <= 20, and the product of the pieces is
+ * exact in GF(p) when ceil(n/w) (2^w - 1)^2 < p. Wider digits mean a shorter
+ * transform (at n = 10^8, m = n/4: 3 * 2^21 points with 20-bit digits against
+ * 2^23 with 16-bit ones). By default each hash takes, among the exact widths,
+ * the one whose product (wrapped where the wrapping rule allows) is shortest,
+ * the narrowest of equals. The wrapped product's rule of pa_hash holds for w-bit
+ * digits with L = ceil(n/w) and the dropped part below lo * 2^(w (lo + 1)). The
+ * exact recomputation behind a wrapped product always uses 16-bit digits.
+ * pa_plan_digits: host only; stores the width a hash of n bits with m output
+ *   bits uses under the current modes (pa_plan_info gives its lengths).
+ * pa_digit_width: 0 (default) chooses as above; 16 .. 20 forces that width
+ *   where it is exact (else 16). Returns the previous setting, or PA_EINVAL.
+ *   Applies to later calls on every thread (tests of each width).
+ */
+int pa_plan_digits(uint64_t n, uint64_t m, uint32_t* width);
+int pa_digit_width(int width);
 
 /*
  * Toeplitz-hash privacy amplification on the same NTT engine: the hash family

@@ -49,6 +49,7 @@ _SIGS = {
     "pa_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "pa_autotune": ([ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "pa_plan_override": ([ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
+    "pa_plan_override_length": ([ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
     "pa_hash_host": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_hash_host_async": ([ctypes.c_void_p] * 3 + [ctypes.c_uint64] * 2 + [ctypes.c_void_p] * 2, ctypes.c_int),
     "pa_convolve16": ([ctypes.c_void_p] * 2 + [ctypes.c_uint64] + [ctypes.c_void_p] * 2, ctypes.c_int),
@@ -59,6 +60,8 @@ _SIGS = {
     "pa_workspace_bytes": ([ctypes.c_uint64], ctypes.c_uint64),
     "pa_plan_info": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "pa_wrap_mode": ([ctypes.c_int], ctypes.c_int),
+    "pa_digit_width": ([ctypes.c_int], ctypes.c_int),
+    "pa_plan_digits": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "pa_wrap_flags": ([ctypes.POINTER(ctypes.c_uint64), ctypes.c_int], ctypes.c_int),
     "pa_shutdown": ([], ctypes.c_int),
     "pa_profile": ([ctypes.c_int], ctypes.c_int),
@@ -448,6 +451,11 @@ def plan_override(n: int, variant: int):
     _check(load().pa_plan_override(n, variant), "pa_plan_override")
 
 
+def plan_override_length(N: int, variant: int):
+    """Force a plan variant for the transform length N itself (-1 clears)."""
+    _check(load().pa_plan_override_length(N, variant), "pa_plan_override_length")
+
+
 def prepare(n: int):
     _check(load().pa_prepare(n), "pa_prepare")
 
@@ -472,6 +480,22 @@ def wrap_mode(mode: int) -> int:
     if rc < 0:
         _check(rc, "pa_wrap_mode")
     return int(rc)
+
+
+def digit_width(width: int) -> int:
+    """0: each hash takes the exact digit width whose product is shortest
+    (default); 16 .. 20: that width where exact. Returns the previous setting."""
+    rc = load().pa_digit_width(width)
+    if rc < 0:
+        _check(rc, "pa_digit_width")
+    return int(rc)
+
+
+def plan_digits(n: int, m: int) -> int:
+    """The digit width a hash of n bits with m output bits uses (host only)."""
+    w = ctypes.c_uint32(0)
+    _check(load().pa_plan_digits(n, m, ctypes.byref(w)), "pa_plan_digits")
+    return int(w.value)
 
 
 def wrap_flags(clear: bool = False) -> int:

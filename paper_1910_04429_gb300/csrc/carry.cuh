@@ -4,12 +4,15 @@
 // staging of one tile of digits and addend limbs in shared memory. Shared by
 // the carry kernel and the exact recomputation behind a wrapped product.
 //
-// With c_k < 2^64 the convolution digits and b the addend, define per 64-bit
-// limb j
-//   V_j = sum_{i<4} c_{4j+i} 2^(16 i) + b_j            (< 2^115)
-//   E_j = lo64(V_j) + hi64(V_{j-1}) = e_j + f_j 2^64   (f_j in {0, 1})
-//   u_j = e_j + f_{j-1}                                (in [0, 2^64])
-// so that y = sum_j u_j 2^(64 j) exactly. What remains is a one-bit carry
+// With c_k < 2^64 the convolution digits (digit k weighing 2^(W k), W the digit
+// width, 16 .. 20) and b the addend, define per 64-bit limb j
+//   V_j = sum of c_k 2^(W k - 64 j) over the digits k with floor(W k / 64) = j,
+//         plus b_j                                      (< 2^128: at most four
+//         digits, their shifts W k - 64 j distinct and below 64)
+//   E_j = lo64(V_j) + hi64(V_{j-1}) = e_j + f_j 2^64    (f_j in {0, 1})
+//   u_j = e_j + f_{j-1}                                 (in [0, 2^64])
+// so that y = sum_j u_j 2^(64 j) exactly. (With W = 16 limb j holds digits
+// 4j .. 4j + 3 at shifts 0, 16, 32, 48.) What remains is a one-bit carry
 // chain: carry_{j+1} = [u_j + carry_j >= 2^64], whose generate / propagate
 // pairs (g_j = [u_j = 2^64], p_j = [u_j = 2^64 - 1]) compose associatively.
 #pragma once
@@ -41,16 +44,54 @@ struct Limb {
     int gp;   // (g_j, p_j)
 };
 
-// V of the limb at shared-memory position l (limb J0 + l)
-__device__ __forceinline__ void limb_v(const u64* cs, const u64* bs, int l, u64* vlo, u64* vhi) {
+// The first digit of limb J, ceil(64 J / W) (J < 0: the halo below limb 0).
+template <int W>
+__device__ __forceinline__ long long first_digit(long long J) {
+    const long long t = 64 * J;
+    return t >= 0 ? (t + W - 1) / W : -((-t) / W);
+}
+
+// Where a staged carry tile starts: limb J0 = TILE_LIMBS tt - HALO_LO, digit k0
+// (the first digit of limb J0, rounded down to even: whole 16-byte pairs).
+struct TileBase {
+    long long J0, k0;
+};
+template <int W>
+__device__ __forceinline__ TileBase tile_base(long long tt) {
+    const long long J0 = tt * TILE_LIMBS - HALO_LO;
+    return TileBase{J0, W == 16 ? 4 * J0 : (first_digit<W>(J0) & ~1ll)};
+}
+
+// V of the limb at shared-memory position l (limb J0 + l), its digits staged
+// from digit k0 on
+template <int W>
+__device__ __forceinline__ void limb_v(const u64* cs, const u64* bs, int l, const TileBase& tb, u64* vlo,
+                                       u64* vhi) {
     u64 lo = 0, hi = 0;
+    if constexpr (W == 16) {
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        u64 ck = cs[4 * l + i];
-        u64 plo = i ? (ck << (16 * i)) : ck;
-        u64 phi = i ? (ck >> (64 - 16 * i)) : 0;
-        lo += plo;
-        hi += phi + (lo < plo);
+        for (int i = 0; i < 4; i++) {
+            u64 ck = cs[4 * l + i];
+            u64 plo = i ? (ck << (16 * i)) : ck;
+            u64 phi = i ? (ck >> (64 - 16 * i)) : 0;
+            lo += plo;
+            hi += phi + (lo < plo);
+        }
+    } else {
+        const long long J = tb.J0 + l, kf = first_digit<W>(J);
+        const int base = (int)(kf - tb.k0);
+        const int s0 = (int)(W * kf - 64 * J);  // 0 .. W - 1
+#pragma unroll
+        for (int i = 0; i < (64 + W - 1) / W; i++) {
+            const int sh = s0 + W * i;
+            if (sh < 64) {
+                u64 ck = cs[base + i];
+                u64 plo = ck << sh;
+                u64 phi = sh ? (ck >> (64 - sh)) : 0;
+                lo += plo;
+                hi += phi + (lo < plo);
+            }
+        }
     }
     u64 bj = bs[l];
     lo += bj;
@@ -60,11 +101,11 @@ __device__ __forceinline__ void limb_v(const u64* cs, const u64* bs, int l, u64*
 }
 
 // u of CNT limbs starting at shared position l0 (needs V at l0-2 .. l0+CNT-1)
-template <int CNT>
-__device__ __forceinline__ void limbs_u(const u64* cs, const u64* bs, int l0, Limb* u) {
+template <int CNT, int W>
+__device__ __forceinline__ void limbs_u(const u64* cs, const u64* bs, int l0, const TileBase& tb, Limb* u) {
     u64 vlo[CNT + 2], vhi[CNT + 2];
 #pragma unroll
-    for (int i = 0; i < CNT + 2; i++) limb_v(cs, bs, l0 - 2 + i, &vlo[i], &vhi[i]);
+    for (int i = 0; i < CNT + 2; i++) limb_v<W>(cs, bs, l0 - 2 + i, tb, &vlo[i], &vhi[i]);
     u64 e[CNT + 1];
     int f[CNT + 1];
 #pragma unroll
@@ -129,19 +170,21 @@ __device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long 
 }
 
 // VEC: coef and b are 16-byte aligned (staged with cp.async), else plain loads.
-// Digits [4 J0, 4 J0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS) of tile tt
-// (J0 = TILE_LIMBS tt - 4) into cs / bs; positions outside the operands read 0.
-template <bool VEC>
-__device__ __forceinline__ void stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs) {
-    const long long J0 = tt * TILE_LIMBS - HALO_LO;
+// Digits [k0, k0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS) of tile tt (tile_base)
+// into cs / bs; positions outside the operands read 0. (SM_COEF covers the
+// digits of SM_LIMBS limbs for every width W >= 16, plus the rounding of k0.)
+template <bool VEC, int W>
+__device__ __forceinline__ TileBase stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs) {
+    const TileBase tb = tile_base<W>(tt);
+    const long long J0 = tb.J0;
     if (VEC) {
-        stage_pairs(cs, c.coef, 4 * J0, SM_COEF / 2, c.L, c.lo);
+        stage_pairs(cs, c.coef, tb.k0, SM_COEF / 2, c.L, c.lo);
         stage_pairs(bs, c.b, J0, SM_LIMBS_PAD / 2, Ly);
         cp_async_commit();
         cp_async_wait<0>();
     } else {
         for (int i = threadIdx.x; i < SM_COEF; i += CARRY_THREADS) {
-            long long k = 4 * J0 + i;
+            long long k = tb.k0 + i;
             cs[i] = (k >= (long long)c.lo && (u64)k < c.L) ? c.coef[k] : 0;
         }
         for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
@@ -149,6 +192,7 @@ __device__ __forceinline__ void stage_tile(const CarryJob& c, u64 Ly, long long 
             bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
         }
     }
+    return tb;
 }
 
 // The output limbs among the carried limbs y[0 .. CARRY_LIMBS] of limbs

@@ -58,9 +58,30 @@ __device__ __forceinline__ void stage_digits(uint16_t* stage, const Digits& dig,
     }
 }
 
-template <int R, int C, bool PACK>
+// Wider digits (width > 16): each row's 16-byte limb chunks, from the chunk that
+// holds the row's first digit bit, into its slot of wide_row_chunks(C) chunks;
+// chunks past the end of the limbs are zero-filled (never read from memory).
+template <int R, int C>
+__device__ __forceinline__ void stage_wide(u64* stage, const Digits& dig, const StridedGeom& g,
+                                           const TilePos& tp, bool upper_zero) {
+    constexpr int CHR = wide_row_chunks(C);
+    const int CH = (upper_zero ? R / 2 : R) * CHR;
+    const u64 bytes = dig.nlimbs * 8;
+    const char* src = reinterpret_cast<const char*>(dig.src);
+    for (int ch = threadIdx.x; ch < CH; ch += NT) {
+        int d = ch / CHR, k = ch - d * CHR;
+        u64 P = tp.base + g.S * (u64)d;
+        u64 off = (((P * dig.width) >> 7) + (u64)k) * 16;
+        int live = off >= bytes ? 0 : (bytes - off >= 16 ? 16 : (int)(bytes - off));
+        cp_async16(reinterpret_cast<char*>(stage) + (size_t)ch * 16, live ? src + off : src, live);
+    }
+}
+
+template <int R, int C, bool PACK, bool WIDE = false>
 struct StageSize {
-    static constexpr int WORDS = PACK ? R * C / 4 : R * C;  // one staged tile, in 8-byte words
+    // one staged tile, in 8-byte words: a [R][C] tile of words, of 16-bit digits,
+    // or (WIDE) R rows of limb chunks
+    static constexpr int WORDS = !PACK ? R * C : WIDE ? R * wide_row_chunks(C) * 2 : R * C / 4;
     static constexpr size_t BYTES = (size_t)(TILE + 2 * WORDS) * sizeof(u64);
 };
 
@@ -68,13 +89,13 @@ struct StageSize {
 // only, when a's spectrum is reused): the twiddles computed for x are kept in
 // registers and reused for a. STAGED: the operands' tiles are copied into
 // shared memory asynchronously first, so a's loads overlap x's arithmetic.
-template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS>
+template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS, bool WIDE = false>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     pdl_begin();
     clear_states(nb, NT);
     using S = Strided<RA, RB, C>;
-    using SZ = StageSize<S::R, C, PACK>;
+    using SZ = StageSize<S::R, C, PACK, WIDE>;
     extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
     u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
@@ -85,7 +106,9 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
         for (int op = 0; op < OPS; op++) {
             if (PACK) {
                 const Digits& dg = op ? io.da : io.dx;
-                stage_digits<S::R, C>((uint16_t*)st[op], dg, g, tp, S::template upper_rows_zero<PACK>(g, dg));
+                const bool uz = S::template upper_rows_zero<PACK>(g, dg);
+                if (WIDE) stage_wide<S::R, C>(st[op], dg, g, tp, uz);
+                else stage_digits<S::R, C>((uint16_t*)st[op], dg, g, tp, uz);
             }
             else stage_words<S::R, C>(st[op], op ? io.buf_a : io.buf_x, g, tp);
             cp_async_commit();
@@ -111,9 +134,9 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
             int it = threadIdx.x + i * NT;
             if (S::NA % NT == 0 || it < S::NA) {
                 if (STAGED)
-                    S::template fwd_a_staged<PACK>(g, tp, it, st[op], (const uint16_t*)st[op], d, sm);
+                    S::template fwd_a_staged<PACK, WIDE>(g, tp, it, st[op], (const uint16_t*)st[op], d, sm);
                 else
-                    S::template fwd_a<PACK>(g, tp, it, buf, d, sm);
+                    S::template fwd_a<PACK, WIDE>(g, tp, it, buf, d, sm);
             }
         }
         __syncthreads();
@@ -372,11 +395,11 @@ struct Launcher {
 
     int ops;               // 2: transform x and a; 1: x only (a's spectrum reused)
 
-    template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS>
+    template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS, bool WIDE = false>
     void fwd_k() const {
         dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
-        size_t smem = STAGED ? StageSize<RA * RB, C, PACK>::BYTES : TILE * sizeof(u64);
-        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS>;
+        size_t smem = STAGED ? StageSize<RA * RB, C, PACK, WIDE>::BYTES : TILE * sizeof(u64);
+        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS, WIDE>;
         allow_smem(k, smem);
         launch_pdl(k, grid, dim3(NT), smem, st, *g, *nb, *tw);
     }
@@ -388,6 +411,7 @@ struct Launcher {
             if (stage_fwd) return fwd_k<RA, RB, C, false, true, OPS>();
             return fwd_k<RA, RB, C, false, false, OPS>();
         }
+        if (wide) return fwd_k<RA, RB, C, true, true, OPS, true>();  // wider digits: staged only
         if (stage_digits_ok && stage_fwd) return fwd_k<RA, RB, C, true, true, OPS>();
         fwd_k<RA, RB, C, true, false, OPS>();
     }
@@ -416,8 +440,15 @@ struct Launcher {
     // plan variant PLAN_NARROW (single blocks, single-pass plans): a quarter of
     // the columns per tile, four times the CTAs for transforms of few tiles
     bool narrow = false;
+    // digits wider than 16 bits (every digit source then 16-byte aligned: the
+    // wide first pass always stages its rows)
+    bool wide = false;
     template <int RA, int RB, int C>
     void fwd_narrow() const {  // the only strided pass: digits in
+        if (wide) {
+            if (ops == 1) return fwd_k<RA, RB, C, true, true, 1, true>();
+            return fwd_k<RA, RB, C, true, true, 2, true>();
+        }
         if (ops == 1) {
             if (stage_digits_ok && stage_fwd) return fwd_k<RA, RB, C, true, true, 1>();
             return fwd_k<RA, RB, C, true, false, 1>();
@@ -478,6 +509,12 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
                   !nb.io[i].dx.one_bit && !nb.io[i].da.one_bit;
+    // digits wider than 16 bits: every block of the launch, staged (aligned) sources
+    const bool wide = nb.io[0].dx.width > 16;
+    for (int i = 0; i < nb.count; i++)
+        if ((nb.io[i].dx.width > 16) != wide || (ops == 2 && (nb.io[i].da.width > 16) != wide))
+            return cudaErrorInvalidValue;
+    if (wide && !aligned && G.nstrided > 0) return cudaErrorInvalidValue;
     // only the first launch clears the carry states
     NttBatch<B> later = nb;
     later.zero = nullptr;
@@ -486,7 +523,8 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, tw, p, narrow);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, cur, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow}.dispatch_fwd(G.pass[p].R, p == 0);
+        Launcher<B>{&g, cur, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow, wide}.dispatch_fwd(G.pass[p].R,
+                                                                                                     p == 0);
         prof_end(st);
         cur = &later;
     }

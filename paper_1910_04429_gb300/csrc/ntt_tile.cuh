@@ -55,21 +55,70 @@ GL_HD u64 omega_n(const Twiddles& tw, u64 e) {  // w_N^(+-e), e < N
 }
 
 // ---------------------------------------------------------------------------
-// key digits: the 16-bit coefficients of Algorithm 1's split step
+// key digits: the w-bit coefficients of Algorithm 1's split step
 // ---------------------------------------------------------------------------
 struct Digits {
-    const uint16_t* src;  // little-endian limbs viewed as 16-bit digits
-    u64 L;                // live digits: ceil(n / 16), or n with one_bit
-    uint16_t top_mask;    // mask of digit L-1 (bits >= n cleared); unused with one_bit
+    const uint16_t* src;  // little-endian limbs (viewed as 16-bit digits when width is 16)
+    u64 L;                // live digits: ceil(n / width), or n with one_bit
+    u32 top_mask;         // mask of digit L-1 (bits >= n cleared); unused with one_bit
     uint16_t one_bit;     // 1: every bit is a digit (GF(2) vectors as 0/1 coefficients)
+    uint16_t width;       // digit bits, 16 .. 20: digit k = bits [w k, w k + w) of the key
+    u64 nlimbs;           // 64-bit limbs of the source (bits beyond them are never read)
 };
 
-GL_HD u64 digit_at(const Digits& d, u64 pos) {
+// digits of w bits of an n-bit integer held in ceil(n/64) limbs
+GL_HD Digits make_digits(const uint64_t* limbs, u64 n, int w) {
+    u64 L = (n + (u64)w - 1) / (u64)w;
+    u32 top = (u32)(n - (u64)w * (L - 1));  // live bits of the top digit, 1 .. w
+    u32 mask = top >= 32 ? 0xFFFFFFFFu : (1u << top) - 1;
+    return Digits{reinterpret_cast<const uint16_t*>(limbs), L, mask, 0, (uint16_t)w, (n + 63) / 64};
+}
+
+// 16-bit digits (or one-bit ones): the hot first pass reads these without the
+// wider-digit code, which would cost its kernels registers
+GL_HD u64 digit_at16(const Digits& d, u64 pos) {
     if (pos >= d.L) return 0;  // zero fill (Algorithm 1, step 1)
     if (d.one_bit) return (d.src[pos >> 4] >> (pos & 15)) & 1u;
     uint16_t v = d.src[pos];
+    if (pos == d.L - 1) v &= (uint16_t)d.top_mask;
+    return v;
+}
+
+// any width
+GL_HD u64 digit_at(const Digits& d, u64 pos) {
+    if (pos >= d.L) return 0;  // zero fill (Algorithm 1, step 1)
+    if (d.one_bit) return (d.src[pos >> 4] >> (pos & 15)) & 1u;
+    if (d.width == 16) {
+        uint16_t v = d.src[pos];
+        if (pos == d.L - 1) v &= (uint16_t)d.top_mask;
+        return v;
+    }
+    const u64* limbs = reinterpret_cast<const u64*>(d.src);
+    const u64 bit = pos * d.width, li = bit >> 6;
+    const unsigned sh = (unsigned)(bit & 63);
+    u64 v = limbs[li] >> sh;
+    if (sh + d.width > 64 && li + 1 < d.nlimbs) v |= limbs[li + 1] << (64 - sh);
+    v &= (1ull << d.width) - 1;
     if (pos == d.L - 1) v &= d.top_mask;
     return v;
+}
+
+// Staged wide digits (width > 16): row d of a strided tile (digits P_d .. P_d + C - 1)
+// is staged as the 16-byte chunks of the limbs from chunk floor(w P_d / 128) on, in a
+// slot of wide_row_chunks(C) chunks (enough for 20-bit digits, plus the misalignment
+// and the second word of the last digit's read).
+GL_HD constexpr int wide_row_chunks(int C) { return (20 * C + 127) / 128 + 2; }
+
+// digit c of a staged row: bit offset r0 + w c, r0 = (w P_d) mod 128
+GL_HD u64 wide_digit(const u32* row, u32 r0, int w, int c) {
+    u32 o = r0 + (u32)(w * c);
+    u32 lo = row[o >> 5], hi = row[(o >> 5) + 1];
+#if defined(__CUDA_ARCH__)
+    u32 v = __funnelshift_r(lo, hi, o & 31);
+#else
+    u32 v = (u32)((((u64)hi << 32) | lo) >> (o & 31));
+#endif
+    return v & ((1u << w) - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -111,7 +160,8 @@ struct Strided {
     static GL_HD bool upper_rows_zero(const StridedGeom& g, const Digits& dig) {
         return PACK && (RB == 2 || RB == 4 || RB == 8) && 2 * dig.L <= g.N;
     }
-    template <bool PACK>
+    // WIDE: digits wider than 16 bits (a separate instantiation)
+    template <bool PACK, bool WIDE = false>
     static GL_HD void fwd_a(const StridedGeom& g, const TilePos& tp, int it, const u64* buf,
                             const Digits& dig, u64* sm) {
         int j0 = it / C, c = it % C;
@@ -120,7 +170,7 @@ struct Strided {
 #pragma unroll
         for (int j1 = 0; j1 < RB; j1++) {
             u64 p = tp.base + c + g.S * (u64)(j0 + RA * j1);
-            v[j1] = (half && 2 * j1 >= RB) ? 0 : PACK ? digit_at(dig, p) : buf[p];
+            v[j1] = (half && 2 * j1 >= RB) ? 0 : PACK ? (WIDE ? digit_at(dig, p) : digit_at16(dig, p)) : buf[p];
         }
         if constexpr (PACK && (RB == 2 || RB == 4 || RB == 8)) {
             if (half) gl::dft_fwd_upper_zero<RB>(v);
@@ -134,8 +184,9 @@ struct Strided {
     }
 
     // fwd_a reading the tile from a [R][C] staging copy: words, or (PACK) 16-bit
-    // digits already zero past the last live digit
-    template <bool PACK>
+    // digits already zero past the last live digit, or (PACK, wider digits) each
+    // row's limb chunks (digits past the last live one read as zero here)
+    template <bool PACK, bool WIDE = false>
     static GL_HD void fwd_a_staged(const StridedGeom& g, const TilePos& tp, int it, const u64* st64,
                                    const uint16_t* st16, const Digits& dig, u64* sm) {
         int j0 = it / C, c = it % C;
@@ -146,9 +197,16 @@ struct Strided {
             int d = j0 + RA * j1;
             if (half && 2 * j1 >= RB) {
                 v[j1] = 0;
-            } else if (PACK) {
+            } else if (PACK && !WIDE) {
                 uint16_t x = st16[d * C + c];
-                if (tp.base + c + g.S * (u64)d == dig.L - 1) x &= dig.top_mask;
+                if (tp.base + c + g.S * (u64)d == dig.L - 1) x &= (uint16_t)dig.top_mask;
+                v[j1] = x;
+            } else if (PACK) {
+                const u64 P = tp.base + g.S * (u64)d, pos = P + c;
+                const u32* row = reinterpret_cast<const u32*>(st64) + d * wide_row_chunks(C) * 4;
+                u64 x = wide_digit(row, (u32)((P * dig.width) & 127), dig.width, c);
+                if (pos >= dig.L) x = 0;
+                else if (pos == dig.L - 1) x &= dig.top_mask;
                 v[j1] = x;
             } else {
                 v[j1] = st64[d * C + c];

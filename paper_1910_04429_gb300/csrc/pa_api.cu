@@ -261,10 +261,6 @@ void save_tune_cache(int dev) {
     rename(tmp.c_str(), path);
 }
 
-uint16_t top_digit_mask(uint64_t n) {
-    return (n & 15) ? (uint16_t)((1u << (n & 15)) - 1) : (uint16_t)0xFFFF;
-}
-
 // Queue steps 1-5 of Algorithm 1; on success *coef points at the digits (k < L).
 int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, cudaStream_t st,
                       Scratch& scr, int dev, u64** coef) {
@@ -279,9 +275,8 @@ int queue_convolution(const uint64_t* key, const uint64_t* seed_a, uint64_t n, c
     if ((rc = scr.get(j.geom.N * sizeof(u64), &ba))) return rc;
     j.buf_x = (u64*)bx;
     j.buf_a = (u64*)ba;
-    uint16_t top = top_digit_mask(n);
-    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top};
-    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top};
+    j.dx = make_digits(key, n, 16);
+    j.da = make_digits(seed_a, n, 16);
     cudaError_t e = launch_convolution(j, st);
     if (e != cudaSuccess) return cuda_fail(e, "NTT launch");
     *coef = j.buf_x;
@@ -324,10 +319,18 @@ int queue_carry(const u64* coef, u64 L, const uint64_t* seed_b, uint64_t n, uint
 // test of that path).
 int g_wrap_mode = 1;
 
-WrapPlan wrap_for(uint64_t n, uint64_t m) {
-    if (g_wrap_mode == 0) return WrapPlan{};
-    return wrap_plan(n, m, g_wrap_mode == 1 ? WRAP_MIN_FULL : 0);
+// Digit width: 0 (default) the width whose product is shortest among the exact
+// ones, 16 .. 20 that width where it is exact (tests; pa_digit_width).
+int g_digit_width = 0;
+
+// The product a single hash of n bits (m output bits) runs under the current
+// modes. Digits wider than 16 bits are read by staged 16-byte copies, so they
+// need 16-byte-aligned key and seed limbs; other operands take 16-bit digits.
+DigitPlan plan_digits(uint64_t n, uint64_t m, bool aligned = true) {
+    return digit_plan(n, m, g_wrap_mode != 0, g_wrap_mode == 1 ? WRAP_MIN_FULL : 0, aligned ? g_digit_width : 16);
 }
+
+bool aligned16(const void* a, const void* b) { return (uintptr_t)a % 16 == 0 && (uintptr_t)b % 16 == 0; }
 
 // One hash's plans and scratch. Without wrapping: the full-length product.
 // With it: the wrapped product, then its carry step (which sets the flag when
@@ -336,21 +339,22 @@ WrapPlan wrap_for(uint64_t n, uint64_t m) {
 // recomputation's power-of-two length, which the wrapped product's prefix of
 // them precedes.
 struct HashPlan {
-    WrapPlan wp;
+    DigitPlan dp;     // digit width, digit count, wrapped plan
+    WrapPlan wp;      // dp.wp
     NttJob prod;      // the product that runs first
     FallbackJob fb;   // with wp.on: the recomputation
     u32* state;       // carry states: one set, or two (wrapped, recomputation)
 };
 
-NttJob product_job(const Geom& G, u64* bx, u64* ba, const uint64_t* key, const uint64_t* seed_a, uint64_t n) {
+NttJob product_job(const Geom& G, u64* bx, u64* ba, const uint64_t* key, const uint64_t* seed_a, uint64_t n,
+                   int w) {
     NttJob j;
     j.geom = G;
-    j.L = (n + 15) / 16;
+    j.dx = make_digits(key, n, w);
+    j.da = make_digits(seed_a, n, w);
+    j.L = j.dx.L;
     j.buf_x = bx;
     j.buf_a = ba;
-    uint16_t top = top_digit_mask(n);
-    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top};
-    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), j.L, top};
     return j;
 }
 
@@ -363,18 +367,19 @@ u64 buffer_words(uint64_t n) {
     return full > fb ? full : fb;
 }
 
-// The recomputation of one wrapped hash: digits dx, da; buffers X, A of the
-// power-of-two length's words; its own (zeroed) carry states; the wrapped
+// The recomputation of one wrapped hash: the key's and the seed's limbs (read
+// as 16-bit digits, whatever width the wrapped product used); buffers X, A of
+// the power-of-two length's words; its own (zeroed) carry states; the wrapped
 // product's flag. b and out are filled in when the carry step is queued.
-int fallback_job(int dev, uint64_t n, uint64_t m, const Digits& dx, const Digits& da, u64* X, u64* A,
+int fallback_job(int dev, uint64_t n, uint64_t m, const uint64_t* key, const uint64_t* seed_a, u64* X, u64* A,
                  u32* state, const u32* flag, FallbackJob* f) {
     const Geom fg = fallback_geom(n);
     Twiddles t;
     int rc = get_base_tables(dev, fg, &t);
     if (rc) return rc;
     *f = FallbackJob{};
-    f->dx = dx;
-    f->da = da;
+    f->dx = make_digits(key, n, 16);
+    f->da = make_digits(seed_a, n, 16);
     f->n = n;
     f->m = m;
     f->flag = flag;
@@ -394,8 +399,9 @@ int fallback_job(int dev, uint64_t n, uint64_t m, const Digits& dx, const Digits
 // transform kernel).
 int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, Scratch& scr, int dev,
                  HashPlan* hp) {
-    hp->wp = wrap_for(n, m);
-    const Geom first = hp->wp.on ? plan_for_base(dev, hp->wp.geom) : plan_for(dev, n);
+    hp->dp = plan_digits(n, m, aligned16(key, seed_a));
+    hp->wp = hp->dp.wp;
+    const Geom first = plan_for_base(dev, hp->wp.on ? hp->wp.geom : hp->dp.full);
     const Geom fg = fallback_geom(n);
     const u64 words = hp->wp.on ? (fg.N > first.N ? fg.N : first.N) : first.N;
     int rc;
@@ -405,10 +411,10 @@ int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64
     if ((rc = scr.get(2 * words * sizeof(u64) + state_words * sizeof(u32), &ws))) return rc;
     u64* bx = (u64*)ws;
     u64* ba = bx + words;
-    hp->prod = product_job(first, bx, ba, key, seed_a, n);
+    hp->prod = product_job(first, bx, ba, key, seed_a, n, hp->dp.w);
     if ((rc = get_tables(dev, first, &hp->prod.tw))) return rc;
     hp->state = (u32*)(ba + words);
-    if (hp->wp.on && (rc = fallback_job(dev, n, m, hp->prod.dx, hp->prod.da, bx, ba,
+    if (hp->wp.on && (rc = fallback_job(dev, n, m, key, seed_a, bx, ba,
                                         hp->state + carry_state_words(n), hp->state + carry_flag_word(n),
                                         &hp->fb)))
         return rc;
@@ -428,10 +434,10 @@ int hash_product(HashPlan& hp, cudaStream_t st) {
 // Steps 6-7: the carry step; after a wrapped product, the recomputation.
 int hash_finish(HashPlan& hp, const uint64_t* seed_b, uint64_t n, uint64_t m, uint64_t* out, cudaStream_t st,
                 int dev) {
-    const u64 L = (n + 15) / 16;
     u32* flag = hp.wp.on ? hp.state + carry_flag_word(n) : nullptr;
     u32* sw = status_word(dev, st);
-    CarryJob c{hp.prod.buf_x, L, seed_b, n, m, out, hp.state, true, hp.wp.lo, flag, g_wrap_mode == 3};
+    CarryJob c{hp.prod.buf_x, hp.dp.L, seed_b, n, m, out, hp.state, true, hp.wp.lo, flag, g_wrap_mode == 3,
+               (u32)hp.dp.w};
     cudaError_t e = launch_carry(c, st, sw);
     if (e != cudaSuccess) return cuda_fail(e, "carry launch");
     if (hp.wp.on) {
@@ -478,7 +484,9 @@ int side_streams(int dev) {
 // recomputation's launches (which return at once unless a flag is set). A
 // batch fills the GPU, so its blocks wrap wherever a shorter length exists
 // (mode 1 as well as 2); mode 0 never wraps, mode 3 forces the recomputation.
-WrapPlan batch_wrap(uint64_t n, uint64_t m) { return g_wrap_mode ? wrap_plan(n, m, 0) : WrapPlan{}; }
+DigitPlan batch_digits(uint64_t n, uint64_t m, bool aligned) {
+    return digit_plan(n, m, g_wrap_mode != 0, 0, aligned ? g_digit_width : 16);
+}
 
 u64 batch_workspace_bytes(const pa_block* blocks, uint32_t count) {
     u64 bytes = 0;
@@ -494,11 +502,12 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     int rc = side_streams(dev);
     if (rc) return rc;
     Device& d = g_dev[dev];
-    std::vector<WrapPlan> wps(count);
-    std::vector<std::pair<u64, std::vector<uint32_t>>> groups;  // first length N -> block indices
+    std::vector<DigitPlan> dps(count);
+    std::vector<std::pair<u64, std::vector<uint32_t>>> groups;  // (first length, wide) -> block indices
     for (uint32_t i = 0; i < count; i++) {
-        wps[i] = batch_wrap(blocks[i].n, blocks[i].m);
-        u64 N = wps[i].on ? wps[i].geom.N : geom_for_bits(blocks[i].n).N;
+        dps[i] = batch_digits(blocks[i].n, blocks[i].m, aligned16(blocks[i].key, blocks[i].seed_a));
+        // a group shares one transform length and one kind of first pass (16-bit or wider digits)
+        u64 N = dps[i].first_n() * 2 + (dps[i].w > 16 ? 1 : 0);
         size_t g = 0;
         while (g < groups.size() && groups[g].first != N) g++;
         if (g == groups.size()) groups.push_back({N, {}});
@@ -537,23 +546,25 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     for (size_t g = 0; g < groups.size(); g++) {
         const auto& idx = groups[g].second;
         const pa_block& b0 = blocks[idx[0]];
-        Geom G = wps[idx[0]].on ? plan_for_base(dev, wps[idx[0]].geom) : plan_for(dev, b0.n);
+        const DigitPlan& d0 = dps[idx[0]];
+        Geom G = plan_for_base(dev, d0.wp.on ? d0.wp.geom : d0.full);
         Twiddles tw;
         if ((rc = get_tables(dev, G, &tw))) return rc;
         std::vector<BlockIO> io(idx.size());
         for (size_t k = 0; k < idx.size(); k++) {
             const uint32_t i = idx[k];
             const pa_block& b = blocks[i];
-            const u64 L = (b.n + 15) / 16, bw = buffer_words(b.n);
-            uint16_t top = top_digit_mask(b.n);
-            Digits dx{(const uint16_t*)b.key, L, top}, da{(const uint16_t*)b.seed_a, L, top};
+            const DigitPlan& dp = dps[i];
+            const u64 L = dp.L, bw = buffer_words(b.n);
+            Digits dx = make_digits(b.key, b.n, dp.w), da = make_digits(b.seed_a, b.n, dp.w);
             io[k] = BlockIO{wbuf[i], wbuf[i] + bw, dx, da, L};
-            const WrapPlan& wp = wps[i];
+            const WrapPlan& wp = dp.wp;
             u32* flag = wp.on ? sbuf[i] + carry_flag_word(b.n) : nullptr;
-            cj[i] = CarryJob{wbuf[i], L, b.seed_b, b.n, b.m, b.out, sbuf[i], true, wp.lo, flag, g_wrap_mode == 3};
+            cj[i] = CarryJob{wbuf[i], L, b.seed_b, b.n, b.m, b.out, sbuf[i], true, wp.lo, flag, g_wrap_mode == 3,
+                             (u32)dp.w};
             if (wp.on) {
                 FallbackJob f;
-                if ((rc = fallback_job(dev, b.n, b.m, dx, da, wbuf[i], wbuf[i] + bw,
+                if ((rc = fallback_job(dev, b.n, b.m, b.key, b.seed_a, wbuf[i], wbuf[i] + bw,
                                        sbuf[i] + carry_state_words(b.n), flag, &f)))
                     return rc;
                 f.b = b.seed_b;
@@ -987,10 +998,12 @@ int pa_batch_destroy(pa_batch batch) {
 
 }  // extern "C"
 
-// A spectrum of the seed at a wrapped length, built on first use on the
-// caller's stream; later uses on any stream wait for `ready`.
+// A spectrum of the seed for one product (transform length and digit width),
+// built on first use on the caller's stream; later uses on any stream wait for
+// `ready`.
 struct SeedSpectrum {
     Geom G;
+    int w;
     u64* spec;
     cudaEvent_t ready;
 };
@@ -999,16 +1012,57 @@ struct pa_seed_s {
     int dev;
     uint64_t n;
     Geom G;
-    u64* spec;  // the seed's spectrum, N words (tile register order, times N^-1)
+    u64* spec;  // Toeplitz handles: the seed's spectrum, N words (tile register order, times N^-1)
     uint64_t m = 0;         // Toeplitz handles: output bits
     bool toeplitz = false;  // a Toeplitz seed (one-bit digits, n + m - 1 bits)
     u64* limbs = nullptr;   // modular-hash handles: a copy of the seed's limbs (the digits of
-                            // the wrapped spectra and of the recomputation)
-    std::vector<SeedSpectrum> wrapped;
+                            // every spectrum and of the recomputation)
+    std::vector<SeedSpectrum> spectra;  // modular-hash handles: one per (length, width) used
 };
+
+namespace {
+
+// The handle's spectrum for a product of length G0.N on w-bit digits (plan for
+// that length taken on first use).
+int seed_spectrum(pa_seed seed, const Geom& G0, int w, cudaStream_t st, int dev, SeedSpectrum** out) {
+    for (SeedSpectrum& s : seed->spectra)
+        if (s.G.N == G0.N && s.w == w) {
+            cudaError_t e = cudaStreamWaitEvent(st, s.ready, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent(seed spectrum)");
+            *out = &s;
+            return PA_OK;
+        }
+    SeedSpectrum s{plan_for_base(dev, G0), w, nullptr, nullptr};
+    NttJob j;
+    j.geom = s.G;
+    int rc = get_tables(dev, s.G, &j.tw);
+    if (rc) return rc;
+    cudaError_t e = cudaMalloc(&s.spec, s.G.N * sizeof(u64));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        j.buf_x = j.buf_a = s.spec;
+        j.da = j.dx = make_digits(seed->limbs, seed->n, w);
+        j.L = j.dx.L;
+        e = launch_seed_spectrum(j, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s.ready, st);
+    if (e != cudaSuccess) {
+        if (s.ready) cudaEventDestroy(s.ready);
+        cudaFree(s.spec);
+        return cuda_fail(e, "seed spectrum");
+    }
+    seed->spectra.push_back(s);
+    *out = &seed->spectra.back();
+    return PA_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
+// The seed's limbs are copied into the handle (the spectra of the products it
+// serves are built from them), and the spectrum of the full-length product at
+// the width a hash of n bits uses when it does not wrap is built now.
 int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* out) {
     if (n < 1 || n > PA_MAX_BITS) return fail(PA_EINVAL, "pa_seed_create: need 1 <= n <= PA_MAX_BITS");
     if (!seed_a || !out) return fail(PA_EINVAL, "pa_seed_create: null pointer");
@@ -1017,75 +1071,32 @@ int pa_seed_create(const uint64_t* seed_a, uint64_t n, void* stream, pa_seed* ou
     cudaMemPool_t pool;
     int rc = setup(&dev, &pool);
     if (rc) return rc;
-    NttJob j;
-    j.geom = plan_for(dev, n);
-    j.L = (n + 15) / 16;
-    if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
-    u64* spec = nullptr;
-    cudaError_t e = cudaMalloc(&spec, j.geom.N * sizeof(u64));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(seed spectrum)");
-    j.buf_x = j.buf_a = spec;
-    j.da = j.dx = Digits{reinterpret_cast<const uint16_t*>(seed_a), j.L, top_digit_mask(n)};
-    if ((e = launch_seed_spectrum(j, (cudaStream_t)stream)) != cudaSuccess) {
-        cudaFree(spec);
-        return cuda_fail(e, "seed transform launch");
-    }
+    cudaStream_t st = (cudaStream_t)stream;
     u64* limbs = nullptr;
     const size_t limb_bytes = ((n + 63) / 64) * sizeof(u64);
-    if ((e = cudaMalloc(&limbs, limb_bytes)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(limbs, seed_a, limb_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)) !=
-            cudaSuccess) {
+    cudaError_t e = cudaMalloc(&limbs, limb_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(limbs, seed_a, limb_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
         cudaFree(limbs);
-        cudaFree(spec);
         return cuda_fail(e, "seed limbs copy");
     }
-    pa_seed_s* h = new pa_seed_s{dev, n, j.geom, spec};
+    pa_seed_s* h = new pa_seed_s{dev, n, Geom{}, nullptr};
     h->limbs = limbs;
+    const DigitPlan dp = digit_plan(n, n, false, 0, g_digit_width);
+    SeedSpectrum* ss = nullptr;
+    if ((rc = seed_spectrum(h, dp.full, dp.w, st, dev, &ss))) {
+        cudaFree(limbs);
+        delete h;
+        return rc;
+    }
+    h->G = ss->G;
     *out = h;
     return PA_OK;
 }
 
-}  // extern "C"
-
-namespace {
-
-// The handle's spectrum at wrapped length G0 (plan for it taken on first use).
-int seed_spectrum(pa_seed seed, const Geom& G0, cudaStream_t st, int dev, SeedSpectrum** out) {
-    for (SeedSpectrum& s : seed->wrapped)
-        if (s.G.N == G0.N) {
-            cudaError_t e = cudaStreamWaitEvent(st, s.ready, 0);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent(seed spectrum)");
-            *out = &s;
-            return PA_OK;
-        }
-    SeedSpectrum s{plan_for_base(dev, G0), nullptr, nullptr};
-    NttJob j;
-    j.geom = s.G;
-    j.L = (seed->n + 15) / 16;
-    int rc = get_tables(dev, s.G, &j.tw);
-    if (rc) return rc;
-    cudaError_t e = cudaMalloc(&s.spec, s.G.N * sizeof(u64));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) {
-        j.buf_x = j.buf_a = s.spec;
-        j.da = j.dx = Digits{reinterpret_cast<const uint16_t*>(seed->limbs), j.L, top_digit_mask(seed->n)};
-        e = launch_seed_spectrum(j, st);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(s.ready, st);
-    if (e != cudaSuccess) {
-        if (s.ready) cudaEventDestroy(s.ready);
-        cudaFree(s.spec);
-        return cuda_fail(e, "wrapped seed spectrum");
-    }
-    seed->wrapped.push_back(s);
-    *out = &seed->wrapped.back();
-    return PA_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
+// x's transform at the product's length against the seed's spectrum there,
+// the carry step (certified when the product is wrapped) and, behind a
+// wrapped product, the recomputation (a's digits from the handle's copy).
 int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, uint64_t m,
                    uint64_t* out, void* stream) {
     if (!seed || !key || !seed_b || !out) return fail(PA_EINVAL, "pa_hash_seeded: null pointer");
@@ -1100,60 +1111,43 @@ int pa_hash_seeded(pa_seed seed, const uint64_t* key, const uint64_t* seed_b, ui
     cudaStream_t st = (cudaStream_t)stream;
     Scratch scr(st, pool);
     const uint64_t n = seed->n;
-    WrapPlan wp = wrap_for(n, m);
-    if (wp.on) {
-        // x's transform at the wrapped length against the seed's spectrum there,
-        // the certified carry step, the recomputation (a's digits from the copy)
-        SeedSpectrum* ss = nullptr;
-        if ((rc = seed_spectrum(seed, wp.geom, st, dev, &ss))) return rc;
-        const Geom fg = fallback_geom(n);
-        const u64 words = fg.N > ss->G.N ? fg.N : ss->G.N;
-        void *bx, *ba, *sp;
-        const size_t state_words = 2 * carry_state_words(n);
-        if ((rc = scr.get(words * sizeof(u64), &bx)) || (rc = scr.get(fg.N * sizeof(u64), &ba)) ||
-            (rc = scr.get(state_words * sizeof(u32), &sp)))
-            return rc;
-        u32* state = (u32*)sp;
-        cudaError_t e;
-        NttJob j;
-        j.zero = state;  // cleared by the first transform kernel
-        j.zero_words = (u32)state_words;
-        j.geom = ss->G;
-        j.L = (n + 15) / 16;
-        if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
-        j.buf_x = (u64*)bx;
-        j.buf_a = ss->spec;
-        j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top_digit_mask(n)};
-        j.da = Digits{reinterpret_cast<const uint16_t*>(seed->limbs), j.L, top_digit_mask(n)};
-        if ((e = launch_convolution_seeded(j, st)) != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
-        u32* flag = state + carry_flag_word(n);
-        u32* sw = status_word(dev, st);
-        CarryJob c{j.buf_x, j.L, seed_b, n, m, out, state, true, wp.lo, flag, g_wrap_mode == 3};
-        if ((e = launch_carry(c, st, sw)) != cudaSuccess) return cuda_fail(e, "carry launch");
-        FallbackJob f;
-        if ((rc = fallback_job(dev, n, m, j.dx, j.da, (u64*)bx, (u64*)ba, state + carry_state_words(n), flag,
-                               &f)))
-            return rc;
-        f.b = seed_b;
-        f.out = out;
-        if ((e = launch_fallback(&f, 1, st, sw)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
-        return PA_OK;
-    }
+    const DigitPlan dp = plan_digits(n, m, aligned16(key, seed->limbs));
+    const WrapPlan& wp = dp.wp;
+    SeedSpectrum* ss = nullptr;
+    if ((rc = seed_spectrum(seed, wp.on ? wp.geom : dp.full, dp.w, st, dev, &ss))) return rc;
+    const Geom fg = fallback_geom(n);
+    const u64 words = wp.on && fg.N > ss->G.N ? fg.N : ss->G.N;
+    const size_t state_words = (wp.on ? 2 : 1) * carry_state_words(n);
+    void *bx, *ba = nullptr, *sp;
+    if ((rc = scr.get(words * sizeof(u64), &bx)) || (wp.on && (rc = scr.get(fg.N * sizeof(u64), &ba))) ||
+        (rc = scr.get(state_words * sizeof(u32), &sp)))
+        return rc;
+    u32* state = (u32*)sp;
     NttJob j;
-    j.geom = seed->G;
-    j.L = (seed->n + 15) / 16;
+    j.zero = state;  // cleared by the first transform kernel
+    j.zero_words = (u32)state_words;
+    j.geom = ss->G;
     if ((rc = get_tables(dev, j.geom, &j.tw))) return rc;
-    u32* state = nullptr;
-    if ((rc = carry_states(seed->n, st, scr, &state))) return rc;
-    void* bx;
-    if ((rc = scr.get(j.geom.N * sizeof(u64), &bx))) return rc;
     j.buf_x = (u64*)bx;
-    j.buf_a = seed->spec;
-    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), j.L, top_digit_mask(seed->n)};
-    j.da = j.dx;
-    cudaError_t e = launch_convolution_seeded(j, st);
-    if (e != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
-    return queue_carry(j.buf_x, j.L, seed_b, seed->n, m, out, st, scr, state);
+    j.buf_a = ss->spec;
+    j.dx = make_digits(key, n, dp.w);
+    j.da = make_digits(seed->limbs, n, dp.w);
+    j.L = dp.L;
+    cudaError_t e;
+    if ((e = launch_convolution_seeded(j, st)) != cudaSuccess) return cuda_fail(e, "seeded NTT launch");
+    u32* flag = wp.on ? state + carry_flag_word(n) : nullptr;
+    u32* sw = status_word(dev, st);
+    CarryJob c{j.buf_x, j.L, seed_b, n, m, out, state, true, wp.lo, flag, g_wrap_mode == 3, (u32)dp.w};
+    if ((e = launch_carry(c, st, sw)) != cudaSuccess) return cuda_fail(e, "carry launch");
+    if (!wp.on) return PA_OK;
+    FallbackJob f;
+    if ((rc = fallback_job(dev, n, m, key, seed->limbs, (u64*)bx, (u64*)ba, state + carry_state_words(n), flag,
+                           &f)))
+        return rc;
+    f.b = seed_b;
+    f.out = out;
+    if ((e = launch_fallback(&f, 1, st, sw)) != cudaSuccess) return cuda_fail(e, "recomputation launch");
+    return PA_OK;
 }
 
 int pa_toeplitz(const uint64_t* key, const uint64_t* seed, uint64_t n, uint64_t m, uint64_t* out,
@@ -1252,10 +1246,11 @@ int pa_seed_destroy(pa_seed seed) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(seed->dev);
-    cudaError_t e = cudaFree(seed->spec);
+    cudaError_t e = seed->spec ? cudaFree(seed->spec) : cudaSuccess;
     if (seed->limbs) cudaFree(seed->limbs);
-    for (SeedSpectrum& s : seed->wrapped) {
-        cudaFree(s.spec);
+    for (SeedSpectrum& s : seed->spectra) {
+        cudaError_t es = cudaFree(s.spec);
+        if (e == cudaSuccess) e = es;
         cudaEventDestroy(s.ready);
     }
     if (prev >= 0) cudaSetDevice(prev);
@@ -1271,7 +1266,23 @@ int pa_plan_override(uint64_t n, int variant) {
     cudaMemPool_t pool;
     int rc = setup(&dev, &pool);
     if (rc) return rc;
-    u64 N = geom_for_bits(n).N;
+    // the length of the full-length product a hash of n bits runs at the current digit width
+    u64 N = digit_plan(n, n, false, 0, g_digit_width).full.N;
+    if (variant < 0) g_dev[dev].forced.erase(N);
+    else g_dev[dev].forced[N] = variant;
+    return PA_OK;
+}
+
+int pa_plan_override_length(uint64_t N, int variant) {
+    if (variant < -1 || variant >= PLAN_VARIANTS)
+        return fail(PA_EINVAL, "pa_plan_override_length: need -1 <= variant < 16");
+    if (N < 4096 || N > (1ull << MAX_LOGN) || choose_geom_len(N).N != N)
+        return fail(PA_EINVAL, "pa_plan_override_length: not a transform length of the library");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev;
+    cudaMemPool_t pool;
+    int rc = setup(&dev, &pool);
+    if (rc) return rc;
     if (variant < 0) g_dev[dev].forced.erase(N);
     else g_dev[dev].forced[N] = variant;
     return PA_OK;
@@ -1300,10 +1311,13 @@ int pa_autotune(uint64_t n, int reps, int* variant_out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0x5A, in_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a, 0xC3, in_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b, 0x3C, in_bytes, st);
-    // The lengths a hash of n bits (m = n / 4) runs: the full-length product's,
-    // timed with wrapping off, and the wrapped product's when there is one.
-    WrapPlan wp = wrap_plan(n, m);  // the default mode's choice
-    const Geom lens[2] = {geom_for_bits(n), wp.geom};
+    // The lengths a hash of n bits (m = n / 4) runs, at the digit width each
+    // would use: the full-length product's, timed with wrapping off, and the
+    // wrapped product's when there is one (the default mode's choice).
+    const DigitPlan dfull = digit_plan(n, m, false, 0, g_digit_width);
+    const DigitPlan dwrap = digit_plan(n, m, true, WRAP_MIN_FULL, g_digit_width);
+    const WrapPlan& wp = dwrap.wp;
+    const Geom lens[2] = {dfull.full, wp.geom};
     const int saved_mode = g_wrap_mode;
     int best_full = 0;
     for (int li = 0; li < (wp.on ? 2 : 1) && e == cudaSuccess && rc == PA_OK; li++) {
@@ -1347,12 +1361,24 @@ int pa_prepare(uint64_t n) {
     int rc = setup(&dev, &pool);
     if (rc) return rc;
     Twiddles tw;
-    if ((rc = get_tables(dev, plan_for(dev, n), &tw))) return rc;
-    // the recomputation's length, and every shorter length a wrapped product of n bits may run
+    // the recomputation's length; for every digit width a hash of n bits may use
+    // (all exact ones when the width is chosen), its full-length product and
+    // every shorter length a wrapped product may run (which depends on m)
     if ((rc = get_base_tables(dev, fallback_geom(n), &tw))) return rc;
-    const u64 L = (n + 15) / 16, full = geom_for_bits(n).N;
-    for (Geom g = choose_geom_len(L); g.N < full; g = choose_geom_len(g.N + 1))
-        if ((rc = get_tables(dev, plan_for_base(dev, g), &tw))) return rc;
+    for (int w = DIGIT_MIN; w <= DIGIT_MAX; w++) {
+        if ((g_digit_width && w != g_digit_width) || !width_exact(n, w)) continue;
+        const u64 L = digits_for(n, w);
+        const Geom full = choose_geom(L);
+        if ((rc = get_tables(dev, plan_for_base(dev, full), &tw))) return rc;
+        for (Geom g = choose_geom_len(L); g.N < full.N; g = choose_geom_len(g.N + 1))
+            if ((rc = get_tables(dev, plan_for_base(dev, g), &tw))) return rc;
+    }
+    if (g_digit_width && !width_exact(n, g_digit_width)) {  // the forced width falls back to 16
+        const Geom full = choose_geom(digits_for(n, 16));
+        if ((rc = get_tables(dev, plan_for_base(dev, full), &tw))) return rc;
+        for (Geom g = choose_geom_len(digits_for(n, 16)); g.N < full.N; g = choose_geom_len(g.N + 1))
+            if ((rc = get_tables(dev, plan_for_base(dev, g), &tw))) return rc;
+    }
     return PA_OK;
 }
 
@@ -1364,15 +1390,33 @@ uint64_t pa_workspace_bytes(uint64_t n) {
 int pa_plan_info(uint64_t n, uint64_t m, uint64_t info[3]) {
     if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_plan_info: need 1 <= m <= n <= PA_MAX_BITS");
     if (!info) return fail(PA_EINVAL, "pa_plan_info: null pointer");
-    WrapPlan wp;
+    DigitPlan dp, df;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        wp = wrap_for(n, m);
+        dp = plan_digits(n, m);
+        df = digit_plan(n, m, false, 0, g_digit_width);
     }
-    info[1] = geom_for_bits(n).N;
-    info[0] = wp.on ? wp.geom.N : info[1];
-    info[2] = wp.on ? wp.lo : 0;
+    info[0] = dp.first_n();
+    info[1] = df.full.N;
+    info[2] = dp.wp.on ? dp.wp.lo : 0;
     return PA_OK;
+}
+
+int pa_plan_digits(uint64_t n, uint64_t m, uint32_t* width) {
+    if (!check_sizes(n, m)) return fail(PA_EINVAL, "pa_plan_digits: need 1 <= m <= n <= PA_MAX_BITS");
+    if (!width) return fail(PA_EINVAL, "pa_plan_digits: null pointer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    *width = (uint32_t)plan_digits(n, m).w;
+    return PA_OK;
+}
+
+int pa_digit_width(int width) {
+    if (width != 0 && (width < DIGIT_MIN || width > DIGIT_MAX))
+        return fail(PA_EINVAL, "pa_digit_width: width must be 0 or 16 .. 20");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int prev = g_digit_width;
+    g_digit_width = width;
+    return prev;
 }
 
 int pa_wrap_mode(int mode) {

@@ -4,6 +4,10 @@
 // significant bits; Eq. 7). The per-limb sums u_j and their carry chain of
 // generate / propagate pairs are defined in carry.cuh.
 //
+// Digit k of the product weighs 2^(W k) for the digit width W of the launch
+// (16 .. 20, a template argument: the digits of a limb and their shifts are
+// then multiply-and-shift arithmetic).
+//
 // One kernel over the tiles of 256 limbs that hold output limbs (from limb
 // (n - m) / 64 up; the limbs below matter only through the carry into the
 // first of them). Each CTA takes the next such tile from an atomic ticket (so
@@ -42,7 +46,7 @@ __device__ unsigned long long g_flags;  // carry launches that set their wrapped
 // count along x). ticket_start > 0 (fault injection) leaves the first output
 // tiles unprocessed and makes every tile take the look-back path, so that the
 // wait on them runs out.
-template <int B, bool VEC>
+template <int B, bool VEC, int W>
 __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
                                                          u32 ticket_start, u32 spin_limit) {
     __shared__ __align__(16) u64 cs[SM_COEF];
@@ -59,13 +63,13 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
     const u64 t = t0 + tile_sh;
     if (t >= tiles) return;
 
-    stage_tile<VEC>(c, Ly, (long long)t, cs, bs);
+    const TileBase tb = stage_tile<VEC, W>(c, Ly, (long long)t, cs, bs);
     __syncthreads();
 
     const int l0 = HALO_LO + CARRY_LIMBS * threadIdx.x;  // shared position of the thread's first limb
     const u64 j0 = t * TILE_LIMBS + CARRY_LIMBS * threadIdx.x;
     Limb u[CARRY_LIMBS + 1];
-    limbs_u<CARRY_LIMBS + 1>(cs, bs, l0, u);
+    limbs_u<CARRY_LIMBS + 1, W>(cs, bs, l0, tb, u);
     int acc = GP_IDENTITY;
 #pragma unroll
     for (int i = 0; i < CARRY_LIMBS; i++)
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
         int decided = 0, cin = 0;
         if (ticket_start == 0) {
             Limb h[2];  // limbs TILE_LIMBS t - 2 and TILE_LIMBS t - 1 (zero below limb 0)
-            limbs_u<2>(cs, bs, HALO_LO - 2, h);
+            limbs_u<2, W>(cs, bs, HALO_LO - 2, tb, h);
             if (!(h[1].gp & 2)) decided = 1, cin = h[1].gp & 1;  // generate or kill
             else if (!(h[0].gp & 2)) decided = 1, cin = h[0].gp & 1;
         }
@@ -99,10 +103,10 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__
                     break;
                 }
                 __syncthreads();  // cs / bs free again
-                stage_tile<VEC>(c, Ly, tc, cs, bs);
+                const TileBase tbc = stage_tile<VEC, W>(c, Ly, tc, cs, bs);
                 __syncthreads();
                 Limb w[CARRY_LIMBS];
-                limbs_u<CARRY_LIMBS>(cs, bs, l0, w);
+                limbs_u<CARRY_LIMBS, W>(cs, bs, l0, tbc, w);
                 int a = GP_IDENTITY;
 #pragma unroll
                 for (int i = 0; i < CARRY_LIMBS; i++) a = compose(a, w[i].gp);  // below tile t: all < Ly
@@ -211,8 +215,16 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
               cb.job[i].lo % 2 == 0;
     dim3 grid((unsigned)tiles, (unsigned)cb.count);
     prof_begin(st, "carry_lookback");
-    cudaError_t e = vec ? launch_pdl(k_carry<B, true>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)
-                        : launch_pdl(k_carry<B, false>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cb.job[0].width) {  // every job of a launch has the same digit width
+#define PA_CARRY_W(w)                                                                                    \
+    case w:                                                                                              \
+        e = vec ? launch_pdl(k_carry<B, true, w>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)   \
+                : launch_pdl(k_carry<B, false, w>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit); \
+        break;
+        PA_CARRY_W(16) PA_CARRY_W(17) PA_CARRY_W(18) PA_CARRY_W(19) PA_CARRY_W(20)
+#undef PA_CARRY_W
+    }
     prof_end(st);
     return e;
 }
@@ -226,13 +238,19 @@ cudaError_t launch_carry(const CarryJob& c, cudaStream_t st, u32* status) {
 }
 
 cudaError_t launch_carry_batch(const CarryJob* jobs, int count, cudaStream_t st, u32* status) {
-    for (int i = 0; i < count; i += MAX_BATCH) {
+    // one launch per digit width present, MAX_BATCH jobs at most each
+    for (int w = 16; w <= 20; w++) {
         CarryBatch<MAX_BATCH> cb;
-        cb.count = count - i < MAX_BATCH ? count - i : MAX_BATCH;
+        cb.count = 0;
         cb.status = status;
-        for (int k = 0; k < cb.count; k++) cb.job[k] = jobs[i + k];
-        cudaError_t e = launch_carry_b<MAX_BATCH>(cb, st);
-        if (e != cudaSuccess) return e;
+        for (int i = 0; i <= count; i++) {
+            if (i < count && jobs[i].width == (u32)w) cb.job[cb.count++] = jobs[i];
+            if (cb.count == MAX_BATCH || (i == count && cb.count)) {
+                cudaError_t e = launch_carry_b<MAX_BATCH>(cb, st);
+                if (e != cudaSuccess) return e;
+                cb.count = 0;
+            }
+        }
     }
     return cudaSuccess;
 }

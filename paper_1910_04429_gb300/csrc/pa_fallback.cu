@@ -113,19 +113,19 @@ __device__ void fb_product(const FallbackJob& f, GridBarrier& bar) {
     grid_sync(bar);
 }
 
-// Steps 6-7 over every limb: f.state[t] first holds tile t's aggregate, then
-// the carry into tile t.
+// Steps 6-7 over every limb (the recomputation's 16-bit digits): f.state[t]
+// first holds tile t's aggregate, then the carry into tile t.
 __device__ void fb_carry(const FallbackJob& f, GridBarrier& bar, u64* cs, u64* bs) {
     const CarryJob c{f.X, f.dx.L, f.b, f.n, f.m, f.out, f.state, true, 0, nullptr, false};
     const u64 Ly = (f.n + 63) / 64, tiles = carry_tiles(f.n), t0 = first_out_tile(f.n, f.m);
     const int l0 = HALO_LO + CARRY_LIMBS * threadIdx.x;
     for (u64 t = blockIdx.x; t < tiles; t += gridDim.x) {
         __syncthreads();  // cs, bs free again
-        stage_tile<false>(c, Ly, (long long)t, cs, bs);
+        const TileBase tb = stage_tile<false, 16>(c, Ly, (long long)t, cs, bs);
         __syncthreads();
         const u64 j0 = t * TILE_LIMBS + CARRY_LIMBS * threadIdx.x;
         Limb u[CARRY_LIMBS];
-        limbs_u<CARRY_LIMBS>(cs, bs, l0, u);
+        limbs_u<CARRY_LIMBS, 16>(cs, bs, l0, tb, u);
         int acc = GP_IDENTITY;
 #pragma unroll
         for (int i = 0; i < CARRY_LIMBS; i++)
@@ -157,11 +157,11 @@ __device__ void fb_carry(const FallbackJob& f, GridBarrier& bar, u64* cs, u64* b
     grid_sync(bar);
     for (u64 t = t0 + blockIdx.x; t < tiles; t += gridDim.x) {
         __syncthreads();
-        stage_tile<false>(c, Ly, (long long)t, cs, bs);
+        const TileBase tb = stage_tile<false, 16>(c, Ly, (long long)t, cs, bs);
         __syncthreads();
         const u64 j0 = t * TILE_LIMBS + CARRY_LIMBS * threadIdx.x;
         Limb u[CARRY_LIMBS + 1];
-        limbs_u<CARRY_LIMBS + 1>(cs, bs, l0, u);
+        limbs_u<CARRY_LIMBS + 1, 16>(cs, bs, l0, tb, u);
         int acc = GP_IDENTITY;
 #pragma unroll
         for (int i = 0; i < CARRY_LIMBS; i++)

@@ -52,7 +52,7 @@ cudaError_t launch_convolution_batch(const Geom& G, const Twiddles& tw, const Bl
 // steps 6-7, Sec. 3.2.2-3.2.5), one kernel over the output tiles (carry-in from
 // a halo, else bounded look-back).
 struct CarryJob {
-    const u64* coef;  // convolution digits, coefficient k weighs 2^(16k)
+    const u64* coef;  // convolution digits, coefficient k weighs 2^(width k)
     u64 L;            // digits present (coef[k] = 0 for k >= L)
     const u64* b;     // addend limbs, ceil(n/64)
     u64 n, m;
@@ -63,6 +63,7 @@ struct CarryJob {
     u32* flag;        // non-null: set to 1 when limb floor((n-m)/64) - 1 of the sum is all
                       // ones (the dropped coefficients could carry into the output)
     bool force_flag;  // set the flag whatever the limb holds (tests of the fallback)
+    u32 width = 16;   // digit width W: coefficient k weighs 2^(W k) (16 .. 20)
 };
 template <int B>
 struct CarryBatch {
@@ -104,7 +105,7 @@ cudaError_t read_flag_count(unsigned long long* out, bool clear);
 // wrapped product's carry step set its flag: the full product by a radix-2
 // transform of length N = 2^logN >= 2L - 1, then the carry step over every limb.
 struct FallbackJob {
-    Digits dx, da;      // the key's and the seed's digits (dx.L = L)
+    Digits dx, da;      // the key's and the seed's 16-bit digits (dx.L = L = ceil(n/16))
     const u64* b;       // addend limbs
     u64 n, m;
     u64* out;           // overwritten when the flag is set

@@ -161,9 +161,8 @@ extern "C" int pa_hash_noalloc(const uint64_t* key, const uint64_t* seed_a, cons
     j.tw = Twiddles{tab, tab + 4096, tab + 8192, tab + 12288, tab + 16384, tab + 16384 + nh};
     j.buf_x = d->work;
     j.buf_a = d->work + j.geom.N;
-    uint16_t top = (n & 15) ? (uint16_t)((1u << (n & 15)) - 1) : (uint16_t)0xFFFF;
-    j.dx = Digits{reinterpret_cast<const uint16_t*>(key), L, top};
-    j.da = Digits{reinterpret_cast<const uint16_t*>(seed_a), L, top};
+    j.dx = make_digits(key, n, 16);
+    j.da = make_digits(seed_a, n, 16);
     if (launch_convolution(j, st) != cudaSuccess) {
         set_error("pa_hash_noalloc: NTT launch failed");
         return PA_ECUDA;

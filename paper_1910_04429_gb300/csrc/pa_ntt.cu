@@ -44,10 +44,11 @@ cudaError_t launch_seed_spectrum(const NttJob& j, cudaStream_t st) {
     bool aligned = (uintptr_t)j.da.src % 16 == 0 && !j.da.one_bit;
     const Geom& G = j.geom;
     bool narrow = narrow_plan<1>(G);
+    if (j.da.width > 16 && !aligned && G.nstrided > 0) return cudaErrorInvalidValue;  // wider digits: staged only
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, j.tw, p, narrow);
         prof_begin(st, "ntt_seed_strided");
-        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1, !(G.variant & PLAN_DIRECT_FWD), true, narrow}
+        Launcher<1>{&g, &nb, &j.tw, st, aligned, 1, !(G.variant & PLAN_DIRECT_FWD), true, narrow, j.da.width > 16}
             .dispatch_fwd(G.pass[p].R, p == 0);
         prof_end(st);
     }

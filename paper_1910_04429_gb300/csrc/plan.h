@@ -188,8 +188,9 @@ struct DigitPlan {
 
 // wrap: whether a wrapped product may run (min_full as for wrap_plan);
 // width: 0 chooses, among the exact widths, the one whose product is shortest
-// (the narrowest of equals: its digit split and carry are the cheapest), else
-// that width (16 when it is not exact for n).
+// (of equals an unwrapped product, which needs no recomputation launch, then
+// the narrowest width: its digit split and carry are the cheapest), else that
+// width (16 when it is not exact for n).
 inline DigitPlan digit_plan(uint64_t n, uint64_t m, bool wrap, uint64_t min_full, int width = 0) {
     DigitPlan best;
     bool have = false;
@@ -201,7 +202,8 @@ inline DigitPlan digit_plan(uint64_t n, uint64_t m, bool wrap, uint64_t min_full
         d.L = digits_for(n, w);
         d.full = choose_geom(d.L);
         if (wrap) d.wp = wrap_plan(n, m, min_full, w);
-        if (!have || d.first_n() < best.first_n()) best = d, have = true;
+        if (!have || d.first_n() < best.first_n() || (d.first_n() == best.first_n() && best.wp.on && !d.wp.on))
+            best = d, have = true;
     }
     if (!have) {  // a forced width that is not exact: 16-bit digits always are (n <= 2^31)
         best.w = 16;

@@ -7,9 +7,12 @@ is dense, so every pass of the product runs on general data, while x and b are
 uniform. Then a x + b is a sum of a few shifted single-digit products, which
 Python's integers form exactly in linear time.
 
-Plans at this size: the wrapped products at 3 * 2^26 points (m = n/4) and
-5 * 2^25 points (m = 1); the full product, the recomputation and m = n at
-2^28 points, the longest transform (radix 16, 64, 64, then the 4096-point tile).
+Plans at this size with 16-bit digits: the wrapped products at 3 * 2^26 points
+(m = n/4) and 5 * 2^25 points (m = 1); the full product, the recomputation and
+m = n at 2^28 points, the longest transform (radix 16, 64, 64, then the
+4096-point tile). With the default width (17-bit digits here: 18 is the widest
+exact one and gives no shorter product) m = n/4 wraps to 5 * 2^25 points and
+m = 1 to 2^27.
 """
 import numpy as np
 import pytest
@@ -41,23 +44,30 @@ def case():
     return blk.x, a, blk.b, y
 
 
-@pytest.mark.parametrize("m,mode,length,flags", [
-    (N // 4, 1, 3 << 26, 0),   # wrapped, certified
-    (1, 1, 5 << 25, 0),        # wrapped, one output bit
-    (N // 4, 0, 1 << 28, 0),   # full product
-    (N // 4, 3, 3 << 26, 1),   # wrapped, certificate forced to fail: recomputation at 2^28
-    (N, 1, 1 << 28, 0),        # every bit out
+@pytest.mark.parametrize("m,mode,width,length,flags", [
+    (N // 4, 1, 16, 3 << 26, 0),   # wrapped, certified (16-bit digits)
+    (1, 1, 16, 5 << 25, 0),        # wrapped, one output bit
+    (N // 4, 0, 16, 1 << 28, 0),   # full product
+    (N // 4, 3, 16, 3 << 26, 1),   # wrapped, certificate forced to fail: recomputation at 2^28
+    (N, 1, 16, 1 << 28, 0),        # every bit out
+    (N // 4, 1, 0, 5 << 25, 0),    # the default width here: 17-bit digits (18 is as short)
+    (1, 1, 0, 1 << 27, 0),         # 17-bit digits, one output bit
+    (N // 4, 3, 0, 5 << 25, 1),    # 17-bit wrapped product, then the 16-bit recomputation
 ])
-def test_maximum_key_size(case, m, mode, length, flags):
+def test_maximum_key_size(case, m, mode, width, length, flags):
     x, a, b, y = case
     prev = binding.wrap_mode(mode)
+    prev_w = binding.digit_width(width)
     try:
         assert binding.plan_info(N, m)["first"] == length
+        if width == 0:
+            assert binding.plan_digits(N, m) == 17
         binding.wrap_flags(clear=True)
         got = gpu_hash(binding, x, a, b, N, m)
         assert binding.wrap_flags() == flags
     finally:
         binding.wrap_mode(prev)
+        binding.digit_width(prev_w)
     assert got.size == -(-m // 64)
     assert int.from_bytes(got.astype("<u8").tobytes(), "little") == y >> (N - m)
     assert binding.device_status() == 0

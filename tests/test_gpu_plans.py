@@ -21,33 +21,36 @@ SIZES = [1000, 100_003, 1_000_000, 1_536_000, 3_000_001, 4_800_000, 300_000_017,
          163_840, 327_680, 655_360, 1_310_720, 10_485_760]
 
 
+@pytest.mark.parametrize("w", [16, 20])
 @pytest.mark.parametrize("n", SIZES)
-def test_every_plan_variant_is_exact(n):
+def test_every_plan_variant_is_exact(n, w):
     """Each variant of the full-length product (wrapping off) and, where the
-    hash wraps, of the wrapped length (forced through the key size whose
-    full-length product has that length, 16 N / 2 bits)."""
+    hash wraps, of the wrapped length, on 16-bit and (where exact) 20-bit
+    digits."""
     m = n // 3 or 1
     blk = inputs.make_block(n, m, seed=n)
     want = oracle.pa_hash(blk.x, blk.a, blk.b, blk.n, blk.m, threads=oracle.default_threads())
+    prev_w = binding.digit_width(w)
     prev = binding.wrap_mode(2)  # wrapped wherever a shorter length exists
     first = binding.plan_info(n, m)["first"]
-    n_first = 16 * (first // 2)
     binding.wrap_mode(0)
+    full = binding.plan_info(n, m)["full"]
     try:
         for v in range(16):
-            binding.plan_override(n, v)
+            binding.plan_override_length(full, v)
             np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
-                                          err_msg=f"full length, variant {v}")
-        binding.plan_override(n, -1)
+                                          err_msg=f"full length {full}, variant {v}")
+        binding.plan_override_length(full, -1)
         binding.wrap_mode(2)
         for v in range(16):
-            binding.plan_override(n_first, v)
+            binding.plan_override_length(first, v)
             np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, blk.n, blk.m), want,
                                           err_msg=f"first length {first}, variant {v}")
     finally:
-        binding.plan_override(n, -1)
-        binding.plan_override(n_first, -1)
+        binding.plan_override_length(full, -1)
+        binding.plan_override_length(first, -1)
         binding.wrap_mode(prev)
+        binding.digit_width(prev_w)
 
 
 def test_seed_keeps_its_plan():
@@ -81,7 +84,9 @@ def test_autotune_choice_is_exact_and_cached(tmp_path):
         del os.environ["PA_TUNE_CACHE"]
     assert 0 <= v < 8
     lines = cache.read_text().splitlines()
-    assert any(line.split("\t")[1:] == [str(3 << 18), str(v)] for line in lines), lines
+    full = binding.plan_info(n, m)["full"]  # the unwrapped product's length (20-bit digits here)
+    assert full == 1 << 19
+    assert any(line.split("\t")[1:] == [str(full), str(v)] for line in lines), lines
     blk = inputs.make_block(n, m, seed=8)
     np.testing.assert_array_equal(gpu_hash(binding, blk.x, blk.a, blk.b, n, m),
                                   oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads()))

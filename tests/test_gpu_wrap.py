@@ -25,7 +25,7 @@ def wrap_wherever_shorter():
 # 3 * 2^k and 5 * 2^k wrapped lengths, one and two strided passes, and the
 # 10^6-bit block
 WRAPPED = [(100_000, 25_000), (100_003, 12_345), (1_000_000, 250_000), (1_000_003, 100_001),
-           (3_000_017, 300_001), (4_800_000, 1_200_000), (10_000_000, 1_000_000),
+           (3_000_017, 300_001), (6_000_000, 600_000), (4_800_000, 240_000), (10_000_000, 1_000_000),
            # floor((n - m)/64) = 10 * 1024: the certificate's limb lies in the carry
            # tile below the first output tile (the carry kernel starts one tile lower),
            # with n - m a multiple of 64 and not
@@ -47,7 +47,7 @@ def _int(arr):
 @pytest.mark.parametrize("n,m", WRAPPED)
 def test_wrapped_matches_oracle(n, m):
     info = binding.plan_info(n, m)
-    assert info["dropped"] > 0 and info["first"] < info["full"]
+    assert info["dropped"] > 0 and info["first"] < info["full"]  # the full product at the width chosen unwrapped
     binding.wrap_flags(clear=True)
     for seed in (1, 2):
         blk = inputs.make_block(n, m, seed=seed)
@@ -140,13 +140,14 @@ def test_host_buffers_wrapped_and_forced():
 
 
 def test_full_size_wrapped_sampled():
-    """n = 10^8, m = 2.5e7 (wrapped length 2^23): the certificate holds, and
-    the output equals the full-length product's bit for bit (the full-length
-    path is itself checked against the oracle by the other parity tests)."""
+    """n = 10^8, m = 2.5e7 (wrapped length 3 * 2^21 on 20-bit digits): the
+    certificate holds, and the output equals the full-length product's and the
+    16-bit wrapped product's (2^23 points) bit for bit (the full-length path is
+    itself checked against the oracle by the other parity tests)."""
     import torch
 
     n, m = 100_000_000, 25_000_000
-    assert binding.plan_info(n, m)["first"] == 1 << 23
+    assert binding.plan_info(n, m)["first"] == 3 << 21 and binding.plan_digits(n, m) == 20
     blk = inputs.make_block(n, m, seed=1)
     tx, ta, tb = dev(blk.x), dev(blk.a), dev(blk.b)
     binding.wrap_flags(clear=True)
@@ -159,8 +160,17 @@ def test_full_size_wrapped_sampled():
     binding.wrap_mode(3)  # the recomputation at length 2^24 as well
     forced = host(binding.hash(tx, ta, tb, n, m))
     torch.cuda.synchronize()
+    binding.wrap_mode(1)
+    prev_w = binding.digit_width(16)
+    try:
+        assert binding.plan_info(n, m)["first"] == 1 << 23
+        w16 = host(binding.hash(tx, ta, tb, n, m))
+        torch.cuda.synchronize()
+    finally:
+        binding.digit_width(prev_w)
     np.testing.assert_array_equal(got, ref)
     np.testing.assert_array_equal(forced, ref)
+    np.testing.assert_array_equal(w16, ref)
     assert binding.device_status() == 0  # no bounded wait ran out
 
 

@@ -1,18 +1,22 @@
-"""The wrapped product of the modular hash, on the CPU.
+"""The wrapped product of the modular hash and the digit width, on the CPU.
 
 The hash needs only bits [n-m, n) of a x + b mod 2^n. A cyclic convolution of
-the 16-bit digits of length N, L <= N < 2L - 1 (L = ceil(n/16)), folds the
+the w-bit digits of length N, L <= N < 2L - 1 (L = ceil(n/w)), folds the
 linear coefficients t_{k+N} onto c_k for k < W = 2L - 1 - N and leaves every
 c_k with k >= W exact. The library drops the coefficients below lo (W rounded
 up to even) and certifies the result: the dropped part is below 2^wbits,
-wbits = 16 (lo + 1) + bit_length(lo), so unless limb q - 1 (q = floor((n-m)/64))
+wbits = w (lo + 1) + bit_length(lo), so unless limb q - 1 (q = floor((n-m)/64))
 of the exact remaining sum Q is all ones -- which needs wbits <= 64 (q - 1) --
 the output taken from Q is exact; otherwise the full-length product runs.
+A width w is exact when L (2^w - 1)^2 < p; by default the library takes, of
+the exact widths 16 .. 20, the one whose product is shortest (the narrowest
+of equals).
 
-Here: pa_plan_info (host logic of the library, no device) against that rule,
-and an exact-integer model of the fold and of the certificate against the
-oracle on small sizes (cyclic lengths of any size, so that wrapping happens
-at a few hundred digits), including inputs built to fail the certificate.
+Here: pa_plan_info / pa_plan_digits (host logic of the library, no device)
+against those rules, and an exact-integer model of the fold and of the
+certificate against the oracle on small sizes (cyclic lengths of any size, so
+that wrapping happens at a few hundred digits), for every width, including
+inputs built to fail the certificate.
 """
 import random
 
@@ -38,18 +42,39 @@ def _lengths(lo_len, hi_len):
     return sorted(out)
 
 
-def _wbits(lo):
-    return 16 * (lo + 1) + lo.bit_length()
+P = (1 << 64) - (1 << 32) + 1
+WIDTHS = [16, 17, 18, 19, 20]
 
 
-def _certifiable(N, L, n, m):
+def _wbits(lo, w=16):
+    return w * (lo + 1) + lo.bit_length()
+
+
+def _certifiable(N, L, n, m, w=16):
     """(ok, lo) of the rule above for cyclic length N."""
     if N < L or N >= 2 * L - 1:
         return False, 0
     W = 2 * L - 1 - N
     lo = W + (W & 1)
     q = (n - m) // 64
-    return q >= 1 and _wbits(lo) <= 64 * (q - 1), lo
+    return q >= 1 and _wbits(lo, w) <= 64 * (q - 1), lo
+
+
+def _exact(n, w):
+    return -(-n // w) * ((1 << w) - 1) ** 2 < P
+
+
+def _first_length(n, m, w, mode):
+    """(first length, dropped) of one width under a wrap mode (the rule above)."""
+    L = -(-n // w)
+    full = _lengths(max(4096, 2 * L - 1), 1 << 40)[0]
+    if mode == 0 or (mode == 1 and full < 1 << 19):
+        return full, 0, full
+    for N in _lengths(max(4096, L), full - 1):
+        ok, lo = _certifiable(N, L, n, m, w)
+        if ok:
+            return N, lo, full
+    return full, 0, full
 
 
 SIZES = [(1, 1), (64, 1), (5000, 100), (65_536, 1), (65_537, 16_000), (100_000, 25_000), (100_000, 50_000),
@@ -57,6 +82,14 @@ SIZES = [(1, 1), (64, 1), (5000, 100), (65_536, 1), (65_537, 16_000), (100_000, 
          (10_000_000, 1_000_000), (10_000_000, 5_000_000), (100_000_000, 10_000_000),
          (100_000_000, 25_000_000), (100_000_000, 50_000_000), (1_000_000_000, 250_000_000),
          (2 ** 31, 2 ** 29), (2 ** 31, 1)]
+
+
+@pytest.fixture
+def width16():
+    """16-bit digits for one test (pa_digit_width, a host-side setting)."""
+    prev = binding.digit_width(16)
+    yield
+    binding.digit_width(prev)
 
 
 @pytest.fixture
@@ -74,9 +107,10 @@ def wrap_mode():
 
 @pytest.mark.parametrize("mode", [1, 2, 0])
 @pytest.mark.parametrize("n,m", SIZES)
-def test_plan_info_follows_the_rule(n, m, mode, wrap_mode):
-    """Mode 1 (default): the rule where the full product has >= 2^19 points;
-    mode 2: wherever a shorter length is certifiable; mode 0: never."""
+def test_plan_info_follows_the_rule(n, m, mode, wrap_mode, width16):
+    """16-bit digits. Mode 1 (default): the rule where the full product has
+    >= 2^19 points; mode 2: wherever a shorter length is certifiable; mode 0:
+    never."""
     wrap_mode(mode)
     info = binding.plan_info(n, m)
     L = -(-n // 16)
@@ -93,7 +127,7 @@ def test_plan_info_follows_the_rule(n, m, mode, wrap_mode):
         assert (info["first"], info["dropped"]) == (full, 0)
 
 
-def test_headline_sizes_wrap(wrap_mode):
+def test_headline_sizes_wrap(wrap_mode, width16):
     """The 10^8-bit block (m = n/4) runs 2^23 points instead of 3 * 2^22, and
     5 * 2^21 at m = n/2; the 10^9-bit block 5 * 2^24 instead of 2^27; the
     10^7-bit block's full product is 5 * 2^18 (2L - 1 = 1249999). The 10^6-bit
@@ -111,6 +145,57 @@ def test_headline_sizes_wrap(wrap_mode):
     assert binding.plan_info(10 ** 6, 250_000)["first"] == 5 << 14
 
 
+@pytest.mark.parametrize("mode", [1, 2, 0])
+@pytest.mark.parametrize("n,m", SIZES)
+def test_width_choice_follows_the_rule(n, m, mode, wrap_mode):
+    """Chosen width (the default): of the exact widths, the one whose first
+    product is shortest; of equals an unwrapped one, then the narrowest; its
+    lengths as for that width."""
+    wrap_mode(mode)
+    best = None
+    for w in WIDTHS:
+        if not _exact(n, w):
+            continue
+        first, lo, full = _first_length(n, m, w, mode)
+        if best is None or first < best[1] or (first == best[1] and best[2] > 0 and lo == 0):
+            best = (w, first, lo)
+    info = binding.plan_info(n, m)
+    assert binding.plan_digits(n, m) == best[0]
+    assert (info["first"], info["dropped"]) == best[1:]
+    # the full-length (unwrapped) product, at the width chosen without wrapping
+    fulls = [(_first_length(n, m, w, 0)[0], w) for w in WIDTHS if _exact(n, w)]
+    assert info["full"] == min(fulls)[0]
+
+
+@pytest.mark.parametrize("w", WIDTHS)
+def test_forced_width_where_exact(w):
+    prev = binding.digit_width(w)
+    try:
+        for n in (1000, 10 ** 6, 10 ** 8, 3 * 10 ** 8, 10 ** 9, 2 ** 31):
+            assert binding.plan_digits(n, n // 4) == (w if _exact(n, w) else 16)
+    finally:
+        binding.digit_width(prev)
+    with pytest.raises(binding.PaError):
+        binding.digit_width(15)
+    with pytest.raises(binding.PaError):
+        binding.digit_width(21)
+
+
+def test_headline_widths():
+    """20-bit digits are exact up to n = 3.355e8 bits: at n = 10^8 (m = n/4) the
+    product is 3 * 2^21 points instead of 2^23 (m = n/2: 18-bit digits, 2^23
+    instead of 5 * 2^21); at 10^9 bits 19-bit digits are the widest exact ones
+    and certify 2^26 points instead of 5 * 2^24."""
+    assert _exact(10 ** 8, 20) and not _exact(4 * 10 ** 8, 20)
+    assert _exact(10 ** 9, 19) and not _exact(10 ** 9, 20)
+    assert binding.plan_digits(10 ** 8, 25 * 10 ** 6) == 20
+    assert binding.plan_info(10 ** 8, 25 * 10 ** 6)["first"] == 3 << 21
+    assert binding.plan_digits(10 ** 8, 5 * 10 ** 7) == 18
+    assert binding.plan_info(10 ** 8, 5 * 10 ** 7)["first"] == 1 << 23
+    assert binding.plan_digits(10 ** 9, 25 * 10 ** 7) == 19
+    assert binding.plan_info(10 ** 9, 25 * 10 ** 7)["first"] == 1 << 26
+
+
 def test_plan_info_rejects_bad_sizes():
     for n, m in [(0, 0), (10, 11), (10, 0), (2 ** 31 + 1, 1)]:
         with pytest.raises(binding.PaError):
@@ -120,17 +205,17 @@ def test_plan_info_rejects_bad_sizes():
 # ---------------------------------------------------------------------------
 # exact-integer model of the wrapped product and its certificate
 # ---------------------------------------------------------------------------
-def _digits(v, L):
-    return [(v >> (16 * i)) & 0xFFFF for i in range(L)]
+def _digits(v, L, w=16):
+    return [(v >> (w * i)) & ((1 << w) - 1) for i in range(L)]
 
 
-def _model(x, a, b, n, m, N):
+def _model(x, a, b, n, m, N, w=16):
     """(output or None, lo): the output taken from the certified sum Q, or None
     when the certificate fails (the library then runs the full product)."""
-    L = -(-n // 16)
-    ok, lo = _certifiable(N, L, n, m)
+    L = -(-n // w)
+    ok, lo = _certifiable(N, L, n, m, w)
     assert ok
-    dx, da = _digits(x, L), _digits(a, L)
+    dx, da = _digits(x, L, w), _digits(a, L, w)
     c = [0] * N
     t = [0] * (2 * L - 1)
     for i in range(L):
@@ -140,9 +225,10 @@ def _model(x, a, b, n, m, N):
                 t[i + j] += da[i] * dx[j]
     # the fold: every c_k with k >= lo is the linear coefficient
     assert all(c[k] == t[k] for k in range(lo, min(N, 2 * L - 1)))
-    T = sum(t[k] << (16 * k) for k in range(lo))
-    assert T < 1 << _wbits(lo)  # the dropped part's bound
-    Q = sum(c[k] << (16 * k) for k in range(lo, L)) + b
+    assert max(t) < P  # the width is exact: every coefficient below p
+    T = sum(t[k] << (w * k) for k in range(lo))
+    assert T < 1 << _wbits(lo, w)  # the dropped part's bound
+    Q = sum(c[k] << (w * k) for k in range(lo, L)) + b
     assert (Q + T) % (1 << n) == (a * x + b) % (1 << n)
     q = (n - m) // 64
     if (Q >> (64 * (q - 1))) & ((1 << 64) - 1) == (1 << 64) - 1:
@@ -150,11 +236,11 @@ def _model(x, a, b, n, m, N):
     return (Q % (1 << n)) >> (n - m), lo
 
 
-def _small_case(n, m):
+def _small_case(n, m, w=16):
     """The shortest cyclic length (any integer) that the rule certifies."""
-    L = -(-n // 16)
+    L = -(-n // w)
     for N in range(L, 2 * L - 1):
-        if _certifiable(N, L, n, m)[0]:
+        if _certifiable(N, L, n, m, w)[0]:
             return N
     return None
 
@@ -167,20 +253,22 @@ def _from_limbs(arr):
     return sum(int(w) << (64 * i) for i, w in enumerate(arr))
 
 
+@pytest.mark.parametrize("w", WIDTHS)
 @pytest.mark.parametrize("n,m", [(1600, 160), (2000, 500), (3001, 750), (4096, 1024), (2500, 250)])
-def test_model_matches_oracle_on_random_inputs(n, m):
-    N = _small_case(n, m)
-    assert N is not None and N < 2 * (-(-n // 16)) - 1
-    rng = random.Random(n * 7 + m)
+def test_model_matches_oracle_on_random_inputs(n, m, w):
+    N = _small_case(n, m, w)
+    assert N is not None and N < 2 * (-(-n // w)) - 1
+    rng = random.Random(n * 7 + m + w)
     for _ in range(6):
         x, a, b = (rng.getrandbits(n) for _ in range(3))
-        got, _ = _model(x, a, b, n, m, N)
+        got, _ = _model(x, a, b, n, m, N, w)
         want = _from_limbs(oracle.pa_hash(_to_limbs(x, n), _to_limbs(a, n), _to_limbs(b, n), n, m, threads=1))
         assert got is not None  # a uniform b fails the certificate with probability 2^-64
         assert got == want
 
 
-def test_model_certificate_fails_exactly_where_needed():
+@pytest.mark.parametrize("w", WIDTHS)
+def test_model_certificate_fails_exactly_where_needed(w):
     """Inputs built so that limb q - 1 of Q is all ones fail the certificate:
     x = 0 with b = 2^n - 1; a = 1 with x = 2^n - 1; and b chosen so that the
     low n - m bits of Q are 2^(n-m) - T, where T > 0 is the dropped part. In
@@ -188,23 +276,23 @@ def test_model_certificate_fails_exactly_where_needed():
     taken from Q alone would be wrong: the fallback is needed there."""
     n, m = 2000, 500
     s = n - m
-    N = _small_case(n, m)
-    L = -(-n // 16)
-    lo = _certifiable(N, L, n, m)[1]
+    N = _small_case(n, m, w)
+    L = -(-n // w)
+    lo = _certifiable(N, L, n, m, w)[1]
     full = (1 << n) - 1
-    assert _model(0, 5, full, n, m, N)[0] is None
-    assert _model(full, 1, 0, n, m, N)[0] is None
-    rng = random.Random(3)
+    assert _model(0, 5, full, n, m, N, w)[0] is None
+    assert _model(full, 1, 0, n, m, N, w)[0] is None
+    rng = random.Random(3 + w)
     x, a = rng.getrandbits(n), rng.getrandbits(n) | 1
     t = [0] * (2 * L - 1)
-    for i, ai in enumerate(_digits(a, L)):
-        for j, xj in enumerate(_digits(x, L)):
+    for i, ai in enumerate(_digits(a, L, w)):
+        for j, xj in enumerate(_digits(x, L, w)):
             t[i + j] += ai * xj
-    T = sum(t[k] << (16 * k) for k in range(lo))
+    T = sum(t[k] << (w * k) for k in range(lo))
     assert T > 0
     q_target = (rng.getrandbits(m) << s) + ((1 << s) - T)
     b = (q_target - a * x + T) % (1 << n)  # then a x + b = Q + T (mod 2^n) with Q = q_target
-    assert _model(x, a, b, n, m, N)[0] is None
+    assert _model(x, a, b, n, m, N, w)[0] is None
     want = ((a * x + b) % (1 << n)) >> s
     assert want != (q_target % (1 << n)) >> s
     assert want == _from_limbs(oracle.pa_hash(_to_limbs(x, n), _to_limbs(a, n), _to_limbs(b, n), n, m, threads=1))
