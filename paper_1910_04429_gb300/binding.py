@@ -61,6 +61,7 @@ _SIGS = {
     "pa_plan_info": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "pa_wrap_mode": ([ctypes.c_int], ctypes.c_int),
     "pa_digit_width": ([ctypes.c_int], ctypes.c_int),
+    "pa_batch_mode": ([ctypes.c_int], ctypes.c_int),
     "pa_plan_digits": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "pa_wrap_flags": ([ctypes.POINTER(ctypes.c_uint64), ctypes.c_int], ctypes.c_int),
     "pa_shutdown": ([], ctypes.c_int),
@@ -488,6 +489,15 @@ def digit_width(width: int) -> int:
     rc = load().pa_digit_width(width)
     if rc < 0:
         _check(rc, "pa_digit_width")
+    return int(rc)
+
+
+def batch_mode(mode: int) -> int:
+    """1: batched transforms in one persistent kernel where the plan allows
+    (default); 0: by size class. Returns the previous mode."""
+    rc = load().pa_batch_mode(mode)
+    if rc < 0:
+        _check(rc, "pa_batch_mode")
     return int(rc)
 
 

@@ -89,18 +89,16 @@ struct StageSize {
 // only, when a's spectrum is reused): the twiddles computed for x are kept in
 // registers and reused for a. STAGED: the operands' tiles are copied into
 // shared memory asynchronously first, so a's loads overlap x's arithmetic.
-template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS, bool WIDE = false>
-__global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
-                                                       Twiddles tw) {
-    pdl_begin();
-    clear_states(nb, NT);
+// (the body: one tile of block io, dynamic shared memory dsm; the kernel below
+// and the persistent batched kernel run it)
+template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS, bool WIDE>
+__device__ __forceinline__ void fwd_strided_tile(const StridedGeom& g, const BlockIO& io, const Twiddles& tw,
+                                                 u64 tile, u64* dsm) {
     using S = Strided<RA, RB, C>;
     using SZ = StageSize<S::R, C, PACK, WIDE>;
-    extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
     u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
-    const BlockIO& io = nb.io[blockIdx.y];
-    TilePos tp = S::tile(g, blockIdx.x);
+    TilePos tp = S::tile(g, tile);
     if (STAGED) {
 #pragma unroll
         for (int op = 0; op < OPS; op++) {
@@ -148,21 +146,27 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
     }
 }
 
+template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS, bool WIDE = false>
+__global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
+                                                       Twiddles tw) {
+    pdl_begin();
+    clear_states(nb, NT);
+    extern __shared__ __align__(16) u64 dsm[];
+    fwd_strided_tile<RA, RB, C, PACK, STAGED, OPS, WIDE>(g, nb.io[blockIdx.y], tw, blockIdx.x, dsm);
+}
+
 // Inverse strided pass over one tile. STAGED: the tile is copied into shared
 // memory asynchronously while the inverse twiddles are read; otherwise the
 // first phase loads it directly (the autotuner picks per transform length).
 // Three CTAs per SM (40 registers): the extra warps hide the global-load latency
 // this one-operand pass is exposed to.
-template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
-__global__ void __launch_bounds__(NT, 3) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
-                                                       Twiddles tw) {
-    pdl_begin();
+template <int RA, int RB, int C, bool LAST, bool STAGED>
+__device__ __forceinline__ void inv_strided_tile(const StridedGeom& g, const BlockIO& io, const Twiddles& tw,
+                                                 u64 tile, u64* dsm) {
     using S = Strided<RA, RB, C>;
-    extern __shared__ __align__(16) u64 dsm[];
     u64* sm = dsm;
     u64* st = dsm + TILE;
-    const BlockIO& io = nb.io[blockIdx.y];
-    TilePos tp = S::tile(g, blockIdx.x);
+    TilePos tp = S::tile(g, tile);
     if (STAGED) {
         stage_words<S::R, C>(st, io.buf_x, g, tp);
         cp_async_commit();
@@ -192,6 +196,14 @@ __global__ void __launch_bounds__(NT, 3) k_inv_strided(StridedGeom g, const __gr
         int it = threadIdx.x + i * NT;
         if (S::NA % NT == 0 || it < S::NA) S::template inv_a<LAST>(g, tp, it, io.buf_x, sm, io.L);
     }
+}
+
+template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
+__global__ void __launch_bounds__(NT, 3) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
+                                                       Twiddles tw) {
+    pdl_begin();
+    extern __shared__ __align__(16) u64 dsm[];
+    inv_strided_tile<RA, RB, C, LAST, STAGED>(g, nb.io[blockIdx.y], tw, blockIdx.x, dsm);
 }
 
 // Forward contiguous pass of one tile; leaves the spectrum in registers.
@@ -277,16 +289,12 @@ __global__ void __launch_bounds__(NT) k_contig_fused(const __grid_constant__ Ntt
 // inverse contiguous pass, as k_contig_seed followed by k_contig_fused but
 // without a's spectrum going through global memory. Dynamic shared memory: the
 // working tile, then a's spectrum word-interleaved by thread ([k * NT + t]).
-template <bool PACK, int B>
-__global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ NttBatch<B> nb, u64 ninv,
-                                                    Twiddles tw) {
-    pdl_begin();
-    clear_states(nb, NT);
-    extern __shared__ __align__(16) u64 dsm[];
+template <bool PACK>
+__device__ __forceinline__ void contig_both_tile(const BlockIO& io, u64 ninv, const Twiddles& tw, u64 tile,
+                                                 u64* dsm) {
     u64* sm = dsm;
     u64* ah = dsm + TILE_SM;
-    const BlockIO& io = nb.io[blockIdx.y];
-    u64 base = (u64)blockIdx.x * TILE;
+    u64 base = tile * TILE;
     int t = threadIdx.x;
     u64 v[8];
     const bool scaled = tw.w4096s != nullptr;
@@ -309,6 +317,15 @@ __global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ N
     c_inv_col_b_store(t, sm, v);
     __syncthreads();
     c_inv_col_a<PACK>(t, sm, io.buf_x + base, base, io.L);
+}
+
+template <bool PACK, int B>
+__global__ void __launch_bounds__(NT, 2) k_contig_both(const __grid_constant__ NttBatch<B> nb, u64 ninv,
+                                                    Twiddles tw) {
+    pdl_begin();
+    clear_states(nb, NT);
+    extern __shared__ __align__(16) u64 dsm[];
+    contig_both_tile<PACK>(nb.io[blockIdx.y], ninv, tw, blockIdx.x, dsm);
 }
 
 __device__ __forceinline__ void bar_sync_half() {  // named barrier 1 over NT threads

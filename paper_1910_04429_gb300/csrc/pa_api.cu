@@ -396,9 +396,10 @@ int fallback_job(int dev, uint64_t n, uint64_t m, const uint64_t* key, const uin
 }
 
 // Plans, twiddle tables, buffers and the carry states (cleared by the first
-// transform kernel).
+// transform kernel). fixed_ws: a caller-provided workspace of
+// pa_workspace_bytes(n) (captured graphs), else one allocation from the pool.
 int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64_t m, Scratch& scr, int dev,
-                 HashPlan* hp) {
+                 HashPlan* hp, void* fixed_ws = nullptr) {
     hp->dp = plan_digits(n, m, aligned16(key, seed_a));
     hp->wp = hp->dp.wp;
     const Geom first = plan_for_base(dev, hp->wp.on ? hp->wp.geom : hp->dp.full);
@@ -407,8 +408,8 @@ int hash_prepare(const uint64_t* key, const uint64_t* seed_a, uint64_t n, uint64
     int rc;
     // one pool allocation per hash: both transform buffers, then the carry states
     const size_t state_words = (hp->wp.on ? 2 : 1) * carry_state_words(n);
-    void* ws;
-    if ((rc = scr.get(2 * words * sizeof(u64) + state_words * sizeof(u32), &ws))) return rc;
+    void* ws = fixed_ws;
+    if (!ws && (rc = scr.get(2 * words * sizeof(u64) + state_words * sizeof(u32), &ws))) return rc;
     u64* bx = (u64*)ws;
     u64* ba = bx + words;
     hp->prod = product_job(first, bx, ba, key, seed_a, n, hp->dp.w);
@@ -449,10 +450,10 @@ int hash_finish(HashPlan& hp, const uint64_t* seed_b, uint64_t n, uint64_t m, ui
 }
 
 int hash_device(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
-                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool) {
+                uint64_t m, uint64_t* out, cudaStream_t st, int dev, cudaMemPool_t pool, void* fixed_ws = nullptr) {
     Scratch scr(st, pool);
     HashPlan hp;
-    int rc = hash_prepare(key, seed_a, n, m, scr, dev, &hp);
+    int rc = hash_prepare(key, seed_a, n, m, scr, dev, &hp, fixed_ws);
     if (!rc) rc = hash_product(hp, st);
     if (!rc) rc = hash_finish(hp, seed_b, n, m, out, st, dev);
     return rc;
@@ -484,6 +485,11 @@ int side_streams(int dev) {
 // recomputation's launches (which return at once unless a flag is set). A
 // batch fills the GPU, so its blocks wrap wherever a shorter length exists
 // (mode 1 as well as 2); mode 0 never wraps, mode 3 forces the recomputation.
+// Batched calls: 1 (default) the blocks whose plan has one or two strided
+// passes run their transforms in the persistent kernel (one cooperative
+// launch), the rest by size class; 0 every block by size class (pa_batch_mode).
+int g_batch_mode = 1;
+
 DigitPlan batch_digits(uint64_t n, uint64_t m, bool aligned) {
     return digit_plan(n, m, g_wrap_mode != 0, 0, aligned ? g_digit_width : 16);
 }
@@ -492,7 +498,7 @@ u64 batch_workspace_bytes(const pa_block* blocks, uint32_t count) {
     u64 bytes = 0;
     for (uint32_t i = 0; i < count; i++)
         bytes += 2 * buffer_words(blocks[i].n) * sizeof(u64) + 2 * carry_state_words(blocks[i].n) * sizeof(u32);
-    return bytes;
+    return bytes + count * sizeof(u32);  // the persistent launches' barrier counters
 }
 
 // fixed_ws: a caller-provided workspace of batch_workspace_bytes() (used for
@@ -519,6 +525,9 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
         words += 2 * buffer_words(blocks[i].n);
         carry_bytes += 2 * carry_state_words(blocks[i].n) * sizeof(u32);
     }
+    u32* barriers = nullptr;  // after the carry states, cleared with them
+    const u64 barrier_off = carry_bytes;
+    carry_bytes += count * sizeof(u32);
     Scratch scr(st, pool);
     void* ws = fixed_ws;
     if (!ws && (rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
@@ -533,7 +542,9 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
             sbuf[i] = cb;
             cb += 2 * carry_state_words(blocks[i].n);
         }
+        barriers = (u32*)((char*)((u64*)ws + words) + barrier_off);
     }
+    std::vector<PersistJob> pj;
     std::vector<CarryJob> cj(count);
     std::vector<FallbackJob> fj;
 
@@ -543,21 +554,30 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
     e = cudaEventRecord(d.fork, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(fork)");
     int used = 0;
+    int sgroups = 0;  // groups run by size class, on the side streams
     for (size_t g = 0; g < groups.size(); g++) {
         const auto& idx = groups[g].second;
-        const pa_block& b0 = blocks[idx[0]];
         const DigitPlan& d0 = dps[idx[0]];
-        Geom G = plan_for_base(dev, d0.wp.on ? d0.wp.geom : d0.full);
+        const Geom& base = d0.wp.on ? d0.wp.geom : d0.full;
+        Geom G = plan_for_base(dev, base);
         Twiddles tw;
         if ((rc = get_tables(dev, G, &tw))) return rc;
-        std::vector<BlockIO> io(idx.size());
+        // the persistent kernel runs the plan with the odd radix first, staged
+        const Geom P = make_geom(base.logN, base.odd, 0);
+        const bool persist = g_batch_mode == 1 && persist_eligible(P);
+        Twiddles ptw;
+        if (persist && (rc = get_tables(dev, P, &ptw))) return rc;
+        std::vector<BlockIO> io;
         for (size_t k = 0; k < idx.size(); k++) {
             const uint32_t i = idx[k];
             const pa_block& b = blocks[i];
             const DigitPlan& dp = dps[i];
             const u64 L = dp.L, bw = buffer_words(b.n);
             Digits dx = make_digits(b.key, b.n, dp.w), da = make_digits(b.seed_a, b.n, dp.w);
-            io[k] = BlockIO{wbuf[i], wbuf[i] + bw, dx, da, L};
+            if (persist && aligned16(b.key, b.seed_a))
+                pj.push_back(PersistJob{wbuf[i], wbuf[i] + bw, b.key, b.seed_a, b.n, dp.w, P, ptw});
+            else
+                io.push_back(BlockIO{wbuf[i], wbuf[i] + bw, dx, da, L});
             const WrapPlan& wp = dp.wp;
             u32* flag = wp.on ? sbuf[i] + carry_flag_word(b.n) : nullptr;
             cj[i] = CarryJob{wbuf[i], L, b.seed_b, b.n, b.m, b.out, sbuf[i], true, wp.lo, flag, g_wrap_mode == 3,
@@ -572,15 +592,21 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
                 fj.push_back(f);
             }
         }
-        cudaStream_t s = d.side[g % SIDE_STREAMS];
-        if (g < SIDE_STREAMS) {
+        if (io.empty()) continue;
+        cudaStream_t s = d.side[sgroups % SIDE_STREAMS];
+        if (sgroups < SIDE_STREAMS) {
             if ((e = cudaStreamWaitEvent(s, d.fork, 0)) != cudaSuccess)
                 return cuda_fail(e, "cudaStreamWaitEvent(fork)");
             used++;
         }
+        sgroups++;
         if ((e = launch_convolution_batch(G, tw, io.data(), (int)io.size(), s)) != cudaSuccess)
             return cuda_fail(e, "batched NTT launch");
     }
+    // the persistent kernel on st, beside the size-class groups on the side streams
+    if (!pj.empty() && (e = launch_persistent(pj.data(), (int)pj.size(), barriers, st, status_word(dev, st))) !=
+                           cudaSuccess)
+        return cuda_fail(e, "persistent transform launch");
     for (int i = 0; i < used; i++) {
         if ((e = cudaEventRecord(d.join[i], d.side[i])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(st, d.join[i], 0)) != cudaSuccess)
@@ -962,14 +988,21 @@ int pa_batch_create(const pa_block* blocks, uint32_t count, pa_batch* out) {
     };
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    // A batch of one runs the single-block path (its own plan variants, the
+    // programmatic launch chain between its kernels), into the same workspace.
+    auto run = [&](cudaStream_t s) {
+        const pa_block& b = blocks[0];
+        return count == 1 ? hash_device(b.key, b.seed_a, b.seed_b, b.n, b.m, b.out, s, dev, pool, ws)
+                          : hash_batch_device(blocks, count, s, dev, pool, ws);
+    };
     // one eager run first: builds every twiddle table and kernel attribute the
     // capture will use (neither may happen during capture)
-    if ((rc = hash_batch_device(blocks, count, cs, dev, pool, ws))) return cleanup(rc);
+    if ((rc = run(cs))) return cleanup(rc);
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cleanup(cuda_fail(e, "warm-up run"));
     g_prof_on = false;
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaStreamBeginCapture"));
-    rc = hash_batch_device(blocks, count, cs, dev, pool, ws);
+    rc = run(cs);
     e = cudaStreamEndCapture(cs, &graph);
     if (rc) return cleanup(rc);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamEndCapture"));
@@ -1410,6 +1443,14 @@ int pa_plan_digits(uint64_t n, uint64_t m, uint32_t* width) {
     return PA_OK;
 }
 
+int pa_batch_mode(int mode) {
+    if (mode < 0 || mode > 1) return fail(PA_EINVAL, "pa_batch_mode: mode must be 0 or 1");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int prev = g_batch_mode;
+    g_batch_mode = mode;
+    return prev;
+}
+
 int pa_digit_width(int width) {
     if (width != 0 && (width < DIGIT_MIN || width > DIGIT_MAX))
         return fail(PA_EINVAL, "pa_digit_width: width must be 0 or 16 .. 20");
@@ -1474,8 +1515,10 @@ int pa_device_status(int clear) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     u32 st = 0;
     if ((e = read_device_status(&st, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
-    u32 fst = 0;
+    u32 fst = 0, pst = 0;
     if ((e = read_fallback_status(&fst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
+    if ((e = read_persist_status(&pst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
+    if (pst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (persistent transforms)");
     if (st & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (carry look-back)");
     if (fst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (recomputation barrier)");
     return PA_OK;

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "carry.cuh"
+#include "grid_sync.cuh"
 
 namespace pa {
 
@@ -30,39 +31,6 @@ __device__ u32 g_fb_status;  // sticky status bits of this kernel (PA_STATUS_*)
 
 constexpr u32 FB_SPIN_LIMIT = 1u << 24;  // polls of a grid barrier before giving up (seconds)
 constexpr int FB_BATCH = 64;             // jobs per launch (kernel parameter array, 11 KB)
-
-struct GridBarrier {
-    u32* count;  // zeroed before the launch; every CTA adds one per barrier
-    u32 ctas;
-    u32 passed;  // barriers this CTA has passed
-    u32 limit;
-    u32* status; // the launching stream's status word, or null
-};
-
-// All CTAs of the grid reach this point before any leaves it; their global
-// writes before it are visible to all after it.
-__device__ __forceinline__ void grid_sync(GridBarrier& g) {
-    __syncthreads();
-    g.passed++;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(g.count, 1u);
-        const u32 target = g.passed * g.ctas;
-        u32 spins = 0, v;
-        while (true) {
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(g.count) : "memory");
-            if (v >= target) break;
-            if (++spins > g.limit) {
-                atomicOr(&g_fb_status, PA_STATUS_TIMEOUT);
-                if (g.status) atomicOr(g.status, PA_STATUS_TIMEOUT);
-                break;
-            }
-            __nanosleep(128);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
 
 __device__ __forceinline__ u64 fb_omega(const FallbackJob& f, bool inv, u64 e) {  // w_N^(+-e), e < N
     const u64* lo = inv ? f.wloi : f.wlo;
@@ -197,7 +165,7 @@ __global__ void __launch_bounds__(CARRY_THREADS) k_fallback(const __grid_constan
     }
     __syncthreads();
     if (!any_sh) return;  // the common case: every wrapped product was certified
-    GridBarrier bar{fb.barrier, gridDim.x, 0, spin_limit, fb.status};
+    GridBarrier bar{fb.barrier, gridDim.x, 0, spin_limit, &g_fb_status, fb.status};
     for (int i = 0; i < fb.count; i++) {
         const FallbackJob& f = fb.job[i];
         if (__ldcg(f.flag) == 0) continue;  // the same answer in every CTA

@@ -128,6 +128,25 @@ struct FallbackBatch {
 cudaError_t launch_fallback(const FallbackJob* jobs, int count, cudaStream_t st, u32* status = nullptr);
 cudaError_t read_fallback_status(u32* out, bool clear);
 
+// Persistent batched transforms (pa_persist.cu): the products of many blocks in
+// one cooperative launch. A block's plan must be persist_eligible: one or two
+// strided passes with the odd radix first (the second, if any, radix 64), its
+// digit sources 16-byte aligned. barriers: one zeroed word per launch (at most
+// one launch per job). The carry steps follow separately.
+struct PersistJob {
+    u64* buf_x;
+    u64* buf_a;
+    const uint64_t* key;
+    const uint64_t* seed;
+    u64 n;
+    int w;         // digit width
+    Geom G;        // the plan of its first product
+    Twiddles tw;   // G's tables (get_tables)
+};
+bool persist_eligible(const Geom& G);
+cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* barriers, cudaStream_t st, u32* status);
+cudaError_t read_persist_status(u32* out, bool clear);
+
 // Inter-pass twiddle tables of a strided pass (M = sub-problem size, S =
 // stride): out[0 .. M) = w_M^(j k) at k S + j, out[M .. 2M) = w_M^-(j k).
 cudaError_t launch_pass_twiddles(const Twiddles& tw, u64 N, u64 M, u64 S, u64* out, cudaStream_t st);

@@ -4,8 +4,9 @@
 r ~ U(0.1, 0.5), block i seeded 1 + i (the input recipe of the batched
 benchmark). Every block's output is Eq. 7 of its own (x, a, b), so each one is
 compared bit for bit with the oracle, for the batched call (pa_hash_batched)
-and for the same batch captured once and replayed as a CUDA graph
-(pa_batch_create / pa_batch_run).
+both with the persistent kernel and by size class (pa_batch_mode), and for
+the same batch captured once and replayed as a CUDA graph (pa_batch_create /
+pa_batch_run).
 """
 import numpy as np
 import pytest
@@ -48,13 +49,19 @@ def test_shape_of_the_workload(batch):
     assert len(lens) >= 4
 
 
-def test_batched_call_matches_oracle(batch):
+@pytest.mark.parametrize("mode", [1, 0])
+def test_batched_call_matches_oracle(batch, mode):
+    """Mode 1: the persistent kernel; mode 0: launches by size class."""
     import torch
 
     blks, t, want = batch
     outs = _outs(blks)
-    binding.hash_batched([(x, a, bb, b.n, b.m, o) for b, (x, a, bb), o in zip(blks, t, outs)])
-    torch.cuda.synchronize()
+    prev = binding.batch_mode(mode)
+    try:
+        binding.hash_batched([(x, a, bb, b.n, b.m, o) for b, (x, a, bb), o in zip(blks, t, outs)])
+        torch.cuda.synchronize()
+    finally:
+        binding.batch_mode(prev)
     for b, o, w in zip(blks, outs, want):
         np.testing.assert_array_equal(host(o), w, err_msg=f"n={b.n} m={b.m} seed={b.seed}")
     assert binding.stream_status() == binding.PA_OK
