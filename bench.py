@@ -647,40 +647,65 @@ def run_batched(args):
             binding.hash(x, a, bb, n, m, out=o)
 
     steps = max(3, min(args.steps, 20))
-    prev_mode = binding.batch_mode(1)      # the persistent kernel
+
+    def profiled(mode):
+        binding.batch_mode(mode)
+        binding.profile(True)
+        for _ in range(steps):
+            batched()
+        torch.cuda.synchronize()
+        binding.profile(False)
+        return {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in binding.profile_collect().items()}
+
+    prev_mode = binding.batch_mode(2)      # the default: chosen by the batch's tile count
     ms_b = timed(batched, steps)
     ref = [o.clone() for o in outs]
-    binding.profile(True)
-    for _ in range(steps):
-        batched()
-    torch.cuda.synchronize()
-    binding.profile(False)
-    kstats = binding.profile_collect()
     graph = binding.Batch(spec)
     ms_g = timed(graph.run, steps)
     same = all(torch.equal(r, o) for r, o in zip(ref, outs))
     graph.close()
+    binding.batch_mode(1)                  # the persistent kernel
+    ms_k = timed(batched, steps)
+    same = same and all(torch.equal(r, o) for r, o in zip(ref, outs))
+    k_persist = profiled(1)
     binding.batch_mode(0)                  # launches by size class on forked streams
     ms_c = timed(batched, steps)
     same = same and all(torch.equal(r, o) for r, o in zip(ref, outs))
-    binding.batch_mode(prev_mode)
+    k_class = profiled(0)
     ms_p = timed(plain, steps)
     same = same and all(torch.equal(r, o) for r, o in zip(ref, outs))
+    # a small batch, where the launches dominate: 16 blocks of 1e6 .. 2e6 bits
+    sb = inputs.make_batch(16, 1_000_000, 2_000_000, seed=11)
+    sd = [tuple(torch.from_numpy(v.view(np.int64)).cuda() for v in (b.x, b.a, b.b)) for b in sb]
+    so = [torch.empty((b.m + 63) // 64, dtype=torch.int64, device="cuda") for b in sb]
+    sspec = [(x, a, bb, b.n, b.m, o) for (x, a, bb), b, o in zip(sd, sb, so)]
+    sbits = sum(b.n for b in sb)
+    small = {}
+    for mode, name in ((2, "default"), (1, "persistent"), (0, "size_class")):
+        binding.batch_mode(mode)
+        ms = timed(lambda: binding.hash_batched(sspec), 50)
+        small[name] = {"value": round(sbits / ms / 1e3, 1), "ms_per_batch": round(ms, 4)}
+    binding.batch_mode(prev_mode)
     lens = sorted({binding.plan_info(b.n, b.m)["first"] for b in blks})
     return {"metric": "PA input throughput (Mbps of key bits), batched blocks", "unit": UNIT,
             "workload": f"{len(blks)} blocks, n log-uniform in [1e6, 1e7] (sum {bits} bits), "
                         f"m = floor(n r), r ~ U(0.1, 0.5), seeds 1..{len(blks)}",
             "transform_lengths": len(lens),
             "batched": {"value": round(bits / ms_b / 1e3, 1), "ms_per_batch": round(ms_b, 3),
-                        "form": "persistent kernel: every block's transforms in one cooperative launch, "
-                                "then one batched carry launch and the recomputation check",
-                        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kstats.items()}},
+                        "form": "pa_hash_batched in its default mode (by size class at this tile count)"},
+            "persistent_kernel": {"value": round(bits / ms_k / 1e3, 1), "ms_per_batch": round(ms_k, 3),
+                                  "form": "every block's transforms in one cooperative launch (pa_batch_mode 1), "
+                                          "then one batched carry launch and the recomputation check",
+                                  "kernels": k_persist},
             "size_class_launches": {"value": round(bits / ms_c / 1e3, 1), "ms_per_batch": round(ms_c, 3),
-                                    "form": "launches per pass and transform length on forked streams"},
+                                    "form": "launches per pass and transform length on forked streams "
+                                            "(pa_batch_mode 0)", "kernels": k_class},
+            "small_batch": dict(small, workload=f"16 blocks, n log-uniform in [1e6, 2e6] (sum {sbits} bits)",
+                                unit=UNIT),
             "plain_single_launches": {"value": round(bits / ms_p / 1e3, 1),
                                       "ms_per_batch": round(ms_p, 3)},
             "captured_graph": {"value": round(bits / ms_g / 1e3, 1), "ms_per_batch": round(ms_g, 3),
-                               "form": "the persistent form captured once (pa_batch_create), replayed"},
+                               "form": "the default form captured once (pa_batch_create), replayed"},
             "results_identical": same, "steps": steps}
 
 

@@ -171,17 +171,22 @@ int pa_hash_batched(const pa_block* blocks, uint32_t count, void* stream);
 
 /*
  * pa_batch_mode: how pa_hash_batched (and pa_batch_create) run the transforms.
- *   1 (default): every block whose product has one or two strided passes
- *     before the 4096-point tile pass (up to about 2^24 points) and whose key
- *     and seed_a are 16-byte aligned runs in one persistent cooperative kernel:
- *     two CTAs per SM walk all those blocks' passes, phase by phase (first
- *     forward pass, radix-64 pass, tile pass with the pointwise product,
- *     inverse passes) with a bounded grid barrier between phases, up to 256
- *     blocks and 16 transform lengths per launch; the other blocks run by size
- *     class on forked streams at the same time.
+ *   1: every block whose product has one or two strided passes before the
+ *     4096-point tile pass (up to about 2^24 points) and whose key and seed_a
+ *     are 16-byte aligned runs in one persistent cooperative kernel: two CTAs
+ *     per SM take the tiles of all those blocks' passes from one work counter
+ *     (first forward pass, radix-64 pass, tile pass with the pointwise
+ *     product, inverse passes, in that order), each tile waiting only for its
+ *     own block's previous pass (bounded waits), up to 256 blocks and 16
+ *     transform lengths per launch; the other blocks run by size class on
+ *     forked streams at the same time.
  *   0: every block by size class (one launch per pass and length).
+ *   2 (default): mode 1 when the blocks the persistent kernel would take have
+ *     at most 8 tiles (4096 points each) per SM in all, else mode 0: the single
+ *     kernel is faster where launches dominate (small batches), the per-pass
+ *     kernels where the work does.
  * The carry steps of all blocks follow in one batched launch either way.
- * Returns the previous mode, or PA_EINVAL. Results are identical in both modes.
+ * Returns the previous mode, or PA_EINVAL. Results are identical in every mode.
  */
 int pa_batch_mode(int mode);
 

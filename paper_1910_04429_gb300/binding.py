@@ -493,8 +493,9 @@ def digit_width(width: int) -> int:
 
 
 def batch_mode(mode: int) -> int:
-    """1: batched transforms in one persistent kernel where the plan allows
-    (default); 0: by size class. Returns the previous mode."""
+    """1: batched transforms in one persistent kernel where the plan allows;
+    0: by size class; 2 (default): persistent for small batches, else by size
+    class. Returns the previous mode."""
     rc = load().pa_batch_mode(mode)
     if rc < 0:
         _check(rc, "pa_batch_mode")

@@ -485,10 +485,18 @@ int side_streams(int dev) {
 // recomputation's launches (which return at once unless a flag is set). A
 // batch fills the GPU, so its blocks wrap wherever a shorter length exists
 // (mode 1 as well as 2); mode 0 never wraps, mode 3 forces the recomputation.
-// Batched calls: 1 (default) the blocks whose plan has one or two strided
-// passes run their transforms in the persistent kernel (one cooperative
-// launch), the rest by size class; 0 every block by size class (pa_batch_mode).
-int g_batch_mode = 1;
+// Batched calls (pa_batch_mode): 1 the blocks whose plan has one or two
+// strided passes run their transforms in the persistent kernel (one
+// cooperative launch), the rest by size class; 0 every block by size class;
+// 2 (default) the persistent kernel when those blocks' tiles number at most
+// PERSIST_AUTO_TILES_PER_SM per SM, else by size class. (Measured on the
+// GB300: 16 blocks of 1e6..2e6 bits, about 770 tiles, 0.126 ms persistent
+// against 0.169 ms by size class; 64 such blocks 0.413 against 0.372 ms; the
+// 256-block workload of 1e6..1e7 bits 5.13 against 4.17 ms. Per-pass kernels
+// keep their own occupancy and overlap across size classes, which a single
+// kernel serving every pass cannot; it wins where launches dominate.)
+int g_batch_mode = 2;
+constexpr u64 PERSIST_AUTO_TILES_PER_SM = 8;
 
 DigitPlan batch_digits(uint64_t n, uint64_t m, bool aligned) {
     return digit_plan(n, m, g_wrap_mode != 0, 0, aligned ? g_digit_width : 16);
@@ -498,7 +506,7 @@ u64 batch_workspace_bytes(const pa_block* blocks, uint32_t count) {
     u64 bytes = 0;
     for (uint32_t i = 0; i < count; i++)
         bytes += 2 * buffer_words(blocks[i].n) * sizeof(u64) + 2 * carry_state_words(blocks[i].n) * sizeof(u32);
-    return bytes + count * sizeof(u32);  // the persistent launches' barrier counters
+    return bytes + count * PERSIST_SCRATCH_WORDS * sizeof(u32);  // the persistent launches' counters
 }
 
 // fixed_ws: a caller-provided workspace of batch_workspace_bytes() (used for
@@ -525,9 +533,9 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
         words += 2 * buffer_words(blocks[i].n);
         carry_bytes += 2 * carry_state_words(blocks[i].n) * sizeof(u32);
     }
-    u32* barriers = nullptr;  // after the carry states, cleared with them
+    u32* barriers = nullptr;  // the persistent launches' counters, after the carry states, cleared with them
     const u64 barrier_off = carry_bytes;
-    carry_bytes += count * sizeof(u32);
+    carry_bytes += count * PERSIST_SCRATCH_WORDS * sizeof(u32);
     Scratch scr(st, pool);
     void* ws = fixed_ws;
     if (!ws && (rc = scr.get(words * sizeof(u64) + carry_bytes, &ws))) return rc;
@@ -545,6 +553,18 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
         barriers = (u32*)((char*)((u64*)ws + words) + barrier_off);
     }
     std::vector<PersistJob> pj;
+    bool use_persist = g_batch_mode == 1;
+    if (g_batch_mode == 2) {  // the tiles the persistent kernel would take
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        u64 tiles = 0;
+        for (uint32_t i = 0; i < count; i++) {
+            const Geom& base = dps[i].wp.on ? dps[i].wp.geom : dps[i].full;
+            if (persist_eligible(make_geom(base.logN, base.odd, 0)) && aligned16(blocks[i].key, blocks[i].seed_a))
+                tiles += base.N / TILE;
+        }
+        use_persist = tiles <= PERSIST_AUTO_TILES_PER_SM * (u64)sms;
+    }
     std::vector<CarryJob> cj(count);
     std::vector<FallbackJob> fj;
 
@@ -564,7 +584,7 @@ int hash_batch_device(const pa_block* blocks, uint32_t count, cudaStream_t st, i
         if ((rc = get_tables(dev, G, &tw))) return rc;
         // the persistent kernel runs the plan with the odd radix first, staged
         const Geom P = make_geom(base.logN, base.odd, 0);
-        const bool persist = g_batch_mode == 1 && persist_eligible(P);
+        const bool persist = use_persist && persist_eligible(P);
         Twiddles ptw;
         if (persist && (rc = get_tables(dev, P, &ptw))) return rc;
         std::vector<BlockIO> io;
@@ -1444,7 +1464,7 @@ int pa_plan_digits(uint64_t n, uint64_t m, uint32_t* width) {
 }
 
 int pa_batch_mode(int mode) {
-    if (mode < 0 || mode > 1) return fail(PA_EINVAL, "pa_batch_mode: mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(PA_EINVAL, "pa_batch_mode: mode must be 0, 1 or 2");
     std::lock_guard<std::mutex> lk(g_mu);
     int prev = g_batch_mode;
     g_batch_mode = mode;

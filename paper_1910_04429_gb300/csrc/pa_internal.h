@@ -131,8 +131,9 @@ cudaError_t read_fallback_status(u32* out, bool clear);
 // Persistent batched transforms (pa_persist.cu): the products of many blocks in
 // one cooperative launch. A block's plan must be persist_eligible: one or two
 // strided passes with the odd radix first (the second, if any, radix 64), its
-// digit sources 16-byte aligned. barriers: one zeroed word per launch (at most
-// one launch per job). The carry steps follow separately.
+// digit sources 16-byte aligned. scratch: PERSIST_SCRATCH_WORDS per job, zeroed
+// (each launch's ticket and per-block tile counters). The carry steps follow
+// separately.
 struct PersistJob {
     u64* buf_x;
     u64* buf_a;
@@ -143,8 +144,9 @@ struct PersistJob {
     Geom G;        // the plan of its first product
     Twiddles tw;   // G's tables (get_tables)
 };
+constexpr u32 PERSIST_SCRATCH_WORDS = 6;
 bool persist_eligible(const Geom& G);
-cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* barriers, cudaStream_t st, u32* status);
+cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* scratch, cudaStream_t st, u32* status);
 cudaError_t read_persist_status(u32* out, bool clear);
 
 // Inter-pass twiddle tables of a strided pass (M = sub-problem size, S =

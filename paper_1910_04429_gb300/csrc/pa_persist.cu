@@ -11,18 +11,20 @@
 //       product, the first inverse pass),
 //   I2  the radix-64 inverse pass where present,
 //   I1  every block's last inverse pass (digits below L kept),
-// with a bounded grid-wide barrier between phases. Every phase's work items
-// are the tiles of the blocks taking part (4096 words in the tile pass and the
-// radix-64 passes; R_0 rows of the radix table's column count in the R_0 passes,
-// 3072 or 2560 words for the odd radices), handed to CTAs round robin over the
-// concatenated tile ranges; a CTA finds an item's block by binary search over
-// the blocks' first-tile offsets, kept in shared memory. Blocks of different
+// as one stream of work items, the tiles of every phase in that order (4096
+// words in the tile pass and the radix-64 passes; R_0 rows of the radix
+// table's column count in the R_0 passes, 3072 or 2560 words for the odd
+// radices). A CTA takes the next item from an atomic ticket, finds its block
+// by binary search over the blocks' first-tile offsets (kept in shared
+// memory), waits until that block has finished the phase before (per-block
+// tile counters, a bounded wait), runs the tile and counts it done. No grid-
+// wide barrier: one block's tile pass runs while other blocks are still in
+// their first pass, so the phases' tails overlap. Blocks of different
 // transform lengths and digit widths mix freely: each block names a class (its
 // length's geometry and twiddle tables) and its own digit width. The carry step
 // of every block follows as the usual batched carry launch.
 #include <mutex>
 
-#include "grid_sync.cuh"
 #include "ntt_kernels.cuh"
 
 namespace pa {
@@ -59,7 +61,8 @@ struct PkBlock {
 struct PkBatch {
     int nblocks;
     u32 spin_limit;
-    u32* barrier;  // zeroed word: the grid barrier's counter
+    u32* ticket;   // zeroed word: the next work item
+    u32* done;     // zeroed words: done[5 b + phase], the phase's finished tiles of block b
     u32* status;   // the launching stream's status word, or null
     PkClass cls[PK_CLASSES];
     PkBlock blk[PK_BLOCKS];
@@ -84,22 +87,36 @@ __device__ __forceinline__ int pk_find(const u32* pre, int nb, u32 t) {
     return lo;
 }
 
-template <typename F>
-__device__ __forceinline__ void pk_phase(const u32* pre, int nb, F&& item) {
-    const u32 total = pre[nb];
-    for (u32 t = blockIdx.x; t < total; t += gridDim.x) {
-        const int b = pk_find(pre, nb, t);
-        item(b, (u64)(t - pre[b]));
-        __syncthreads();  // shared memory free for the next item
-    }
+// Each pass body is its own (not inlined) function, register-allocated on its
+// own as in its per-pass kernel; the call costs once per tile.
+template <int RA, int RB, int C, bool WIDE>
+__device__ __noinline__ void pk_fwd_first_body(const StridedGeom& g, const BlockIO& io, const Twiddles& tw, u64 tile,
+                                               u64* dsm) {
+    fwd_strided_tile<RA, RB, C, true, true, 2, WIDE>(g, io, tw, tile, dsm);
+}
+template <int RA, int RB, int C>
+__device__ __noinline__ void pk_inv_last_body(const StridedGeom& g, const BlockIO& io, const Twiddles& tw, u64 tile,
+                                              u64* dsm) {
+    inv_strided_tile<RA, RB, C, true, true>(g, io, tw, tile, dsm);
+}
+__device__ __noinline__ void pk_fwd64_body(const StridedGeom& g, const BlockIO& io, const Twiddles& tw, u64 tile,
+                                           u64* dsm) {
+    fwd_strided_tile<8, 8, 64, false, true, 2, false>(g, io, tw, tile, dsm);
+}
+__device__ __noinline__ void pk_inv64_body(const StridedGeom& g, const BlockIO& io, const Twiddles& tw, u64 tile,
+                                           u64* dsm) {
+    inv_strided_tile<8, 8, 64, false, true>(g, io, tw, tile, dsm);
+}
+__device__ __noinline__ void pk_tile_body(const BlockIO& io, u64 ninv, const Twiddles& tw, u64 tile, u64* dsm) {
+    contig_both_tile<false>(io, ninv, tw, tile, dsm);
 }
 
 __device__ __forceinline__ void pk_fwd_first(const PkClass& c, const BlockIO& io, bool wide, u64 tile, u64* dsm) {
     switch (c.R0) {
-#define PK_FWD(r, a, b, cc)                                                              \
-    case r:                                                                              \
-        if (wide) fwd_strided_tile<a, b, cc, true, true, 2, true>(c.g0, io, c.tw, tile, dsm); \
-        else fwd_strided_tile<a, b, cc, true, true, 2, false>(c.g0, io, c.tw, tile, dsm);     \
+#define PK_FWD(r, a, b, cc)                                                     \
+    case r:                                                                     \
+        if (wide) pk_fwd_first_body<a, b, cc, true>(c.g0, io, c.tw, tile, dsm); \
+        else pk_fwd_first_body<a, b, cc, false>(c.g0, io, c.tw, tile, dsm);     \
         break;
         PA_RADIX_TABLE(PK_FWD)
 #undef PK_FWD
@@ -110,17 +127,27 @@ __device__ __forceinline__ void pk_inv_last(const PkClass& c, const BlockIO& io,
     switch (c.R0) {
 #define PK_INV(r, a, b, cc) \
     case r:                 \
-        inv_strided_tile<a, b, cc, true, true>(c.g0, io, c.tw, tile, dsm); \
+        pk_inv_last_body<a, b, cc>(c.g0, io, c.tw, tile, dsm); \
         break;
         PA_RADIX_TABLE(PK_INV)
 #undef PK_INV
     }
 }
 
+// phases in the order their items are handed out
+enum : int { PK_F1 = 0, PK_F2 = 1, PK_T = 2, PK_I2 = 3, PK_I1 = 4 };
+
+// Items are taken from one ticket in phase-major order (all F1 tiles, then F2,
+// T, I2, I1). An item waits, bounded, until its own block has finished the
+// phase before it (per-block counters), not for the whole grid: every tile it
+// waits for has a lower ticket, so it was taken earlier by a resident CTA that
+// waits only on still earlier tiles, and every wait ends.
 __global__ void __launch_bounds__(NT, 2) k_persist(const __grid_constant__ PkBatch pb) {
     extern __shared__ __align__(16) u64 dsm[];
     // first-tile offsets: R_0 passes, tile pass, radix-64 passes
     __shared__ u32 pre_r0[PK_BLOCKS + 1], pre_all[PK_BLOCKS + 1], pre_two[PK_BLOCKS + 1];
+    __shared__ u32 item_sh;
+    __shared__ BlockIO io_sh;  // the item's block, built once per item (not held in registers)
     const int nb = pb.nblocks;
     if (threadIdx.x == 0) {
         u32 r = 0, a = 0, b2 = 0;
@@ -137,39 +164,59 @@ __global__ void __launch_bounds__(NT, 2) k_persist(const __grid_constant__ PkBat
         pre_two[nb] = b2;
     }
     __syncthreads();
-    GridBarrier bar{pb.barrier, gridDim.x, 0, pb.spin_limit, &g_pk_status, pb.status};
-    const bool two = pre_two[nb] != 0;  // the same in every CTA
-    pk_phase(pre_r0, nb, [&](int b, u64 tile) {  // F1
-        const PkBlock& k = pb.blk[b];
-        pk_fwd_first(pb.cls[k.cls], pk_io(k), k.w > 16, tile, dsm);
-    });
-    grid_sync(bar);
-    if (two) {
-        pk_phase(pre_two, nb, [&](int b, u64 tile) {  // F2
-            const PkBlock& k = pb.blk[b];
-            const PkClass& c = pb.cls[k.cls];
-            fwd_strided_tile<8, 8, 64, false, true, 2, false>(c.g1, pk_io(k), c.tw, tile, dsm);
-        });
-        grid_sync(bar);
-    }
-    pk_phase(pre_all, nb, [&](int b, u64 tile) {  // T
+    const u32 s_f2 = pre_r0[nb], s_t = s_f2 + pre_two[nb], s_i2 = s_t + pre_all[nb], s_i1 = s_i2 + pre_two[nb],
+              s_end = s_i1 + pre_r0[nb];
+    while (true) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(pb.ticket, 1u);
+        __syncthreads();
+        const u32 t = item_sh;
+        if (t >= s_end) break;
+        int phase;
+        const u32* pre;
+        u32 local;
+        if (t < s_f2) phase = PK_F1, pre = pre_r0, local = t;
+        else if (t < s_t) phase = PK_F2, pre = pre_two, local = t - s_f2;
+        else if (t < s_i2) phase = PK_T, pre = pre_all, local = t - s_t;
+        else if (t < s_i1) phase = PK_I2, pre = pre_two, local = t - s_i2;
+        else phase = PK_I1, pre = pre_r0, local = t - s_i1;
+        const int b = pk_find(pre, nb, local);
+        const u64 tile = local - pre[b];
         const PkBlock& k = pb.blk[b];
         const PkClass& c = pb.cls[k.cls];
-        contig_both_tile<false>(pk_io(k), c.ninv, c.tw, tile, dsm);
-    });
-    grid_sync(bar);
-    if (two) {
-        pk_phase(pre_two, nb, [&](int b, u64 tile) {  // I2
-            const PkBlock& k = pb.blk[b];
-            const PkClass& c = pb.cls[k.cls];
-            inv_strided_tile<8, 8, 64, false, true>(c.g1, pk_io(k), c.tw, tile, dsm);
-        });
-        grid_sync(bar);
+        if (threadIdx.x == 0) io_sh = pk_io(k);
+        if (threadIdx.x == 0 && phase != PK_F1) {
+            // the phase before this one for block b: its counter and tile count
+            int dep = phase - 1;
+            if (c.nstr == 1 && (phase == PK_T || phase == PK_I1)) dep = phase - 2;
+            const u32 need = dep == PK_F1 ? k.tiles0 : k.tiles;
+            const u32* ctr = pb.done + 5 * b + dep;
+            u32 v, spins = 0;
+            while (true) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+                if (v >= need) break;
+                if (++spins > pb.spin_limit) {
+                    atomicOr(&g_pk_status, PA_STATUS_TIMEOUT);
+                    if (pb.status) atomicOr(pb.status, PA_STATUS_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        const BlockIO& io = io_sh;
+        switch (phase) {
+        case PK_F1: pk_fwd_first(c, io, k.w > 16, tile, dsm); break;
+        case PK_F2: pk_fwd64_body(c.g1, io, c.tw, tile, dsm); break;
+        case PK_T: pk_tile_body(io, c.ninv, c.tw, tile, dsm); break;
+        case PK_I2: pk_inv64_body(c.g1, io, c.tw, tile, dsm); break;
+        default: pk_inv_last(c, io, tile, dsm); break;
+        }
+        __syncthreads();  // the tile's writes done; shared memory free for the next item
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(pb.done + 5 * b + phase, 1u);
+        }
     }
-    pk_phase(pre_r0, nb, [&](int b, u64 tile) {  // I1
-        const PkBlock& k = pb.blk[b];
-        pk_inv_last(pb.cls[k.cls], pk_io(k), tile, dsm);
-    });
 }
 
 // ---------------------------------------------------------------------------
@@ -213,14 +260,14 @@ static cudaError_t pk_launch(const PkBatch& pb, int grid, cudaStream_t st) {
     return e;
 }
 
-cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* barriers, cudaStream_t st, u32* status) {
+cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* scratch, cudaStream_t st, u32* status) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const int grid = pk_grid(dev);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     static PkBatch pb;  // about 19 KB: kept off the stack (the library lock serialises callers)
-    int launches = 0;
+    u64 off = 0;  // words of scratch taken: a ticket and 5 counters per block, per launch
     pb.nblocks = 0;
     int ncls = 0;
     u64 clsN[PK_CLASSES];
@@ -233,7 +280,9 @@ cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* barriers, 
         // launch what is gathered when the batch ends or the next block does not fit
         if (pb.nblocks && (i == count || pb.nblocks == PK_BLOCKS || (c < 0 && ncls == PK_CLASSES))) {
             pb.spin_limit = PK_SPIN_LIMIT;
-            pb.barrier = barriers + launches++;
+            pb.ticket = scratch + off;
+            pb.done = scratch + off + 1;
+            off += 1 + 5 * (u64)pb.nblocks;
             pb.status = status;
             if ((e = pk_launch(pb, grid, st)) != cudaSuccess) return e;
             pb.nblocks = 0;

@@ -49,9 +49,10 @@ def test_shape_of_the_workload(batch):
     assert len(lens) >= 4
 
 
-@pytest.mark.parametrize("mode", [1, 0])
+@pytest.mark.parametrize("mode", [2, 1, 0])
 def test_batched_call_matches_oracle(batch, mode):
-    """Mode 1: the persistent kernel; mode 0: launches by size class."""
+    """Mode 1: the persistent kernel; mode 0: launches by size class; mode 2
+    (default): chosen by the batch's tile count (by size class here)."""
     import torch
 
     blks, t, want = batch

@@ -119,3 +119,22 @@ def test_both_modes_agree():
     for a, b in zip(got1, got0):
         np.testing.assert_array_equal(a, b)
     _check(blks[:16], got1[:16])
+
+
+def test_automatic_mode_takes_the_persistent_kernel_for_small_batches():
+    """Mode 2 (default): 16 blocks of 1e6 .. 2e6 bits (under 8 tiles per SM)
+    run in the persistent kernel; the 256-block workload's tiles do not."""
+    binding.batch_mode(2)
+    blks = inputs.make_batch(16, 1_000_000, 2_000_000, seed=11)
+    binding.profile(True)
+    got = _run(blks)
+    binding.profile(False)
+    names = binding.profile_collect()
+    assert "ntt_persistent" in names, names
+    _check(blks, got)
+    big = inputs.make_batch(64, 1_000_000, 10_000_000, seed=1)
+    binding.profile(True)
+    _run(big)
+    binding.profile(False)
+    names = binding.profile_collect()
+    assert "ntt_persistent" not in names and "ntt_contig_both" in names, names
