@@ -231,15 +231,15 @@ def hash_bytes(n: int, m: int) -> int:
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
 # launch at n = 10^8), valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 158.0e6, "src_sha": "ad02c353e006f01e",
+TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 109.8e6, "src_sha": "93d8de3f1228a586",
            "profile": "profiles/k_contig_both_n1e8.md"}
 
 
 # The sources that define the hash's kernels and their launch sequence (the
 # profiled code); host-only files (API, serving, adapters) are not part of it.
 KERNEL_SOURCES = ["gl.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "cp_async.cuh", "pdl.cuh", "plan.h",
-                  "pa_internal.h", "carry.cuh", "pa_ntt.cu", "pa_ntt_batch.cu", "pa_carry.cu",
-                  "pa_fallback.cu"]
+                  "pa_internal.h", "carry.cuh", "grid_sync.cuh", "pa_ntt.cu", "pa_ntt_batch.cu", "pa_carry.cu",
+                  "pa_fallback.cu", "pa_persist.cu"]
 
 
 def kernel_src_sha() -> str:
