@@ -61,11 +61,16 @@ __device__ __forceinline__ void stage_digits(uint16_t* stage, const Digits& dig,
 // Wider digits (width > 16): each row's 16-byte limb chunks, from the chunk that
 // holds the row's first digit bit, into its slot of wide_row_chunks(C) chunks;
 // chunks past the end of the limbs are zero-filled (never read from memory).
+// After the chunks, per row: x = its first digit's bit offset in the slot
+// (w P mod 128) | (its live digits, min(L - P, C) or 0) << 7, y = the column of
+// digit L - 1 if the row holds it, else C (the reads then need no 64-bit
+// position arithmetic per digit).
 template <int R, int C>
 __device__ __forceinline__ void stage_wide(u64* stage, const Digits& dig, const StridedGeom& g,
                                            const TilePos& tp, bool upper_zero) {
     constexpr int CHR = wide_row_chunks(C);
-    const int CH = (upper_zero ? R / 2 : R) * CHR;
+    const int rows = upper_zero ? R / 2 : R;
+    const int CH = rows * CHR;
     const u64 bytes = dig.nlimbs * 8;
     const char* src = reinterpret_cast<const char*>(dig.src);
     for (int ch = threadIdx.x; ch < CH; ch += NT) {
@@ -75,13 +80,22 @@ __device__ __forceinline__ void stage_wide(u64* stage, const Digits& dig, const 
         int live = off >= bytes ? 0 : (bytes - off >= 16 ? 16 : (int)(bytes - off));
         cp_async16(reinterpret_cast<char*>(stage) + (size_t)ch * 16, live ? src + off : src, live);
     }
+    uint2* rinfo = reinterpret_cast<uint2*>(stage + R * CHR * 2);
+    for (int d = threadIdx.x; d < rows; d += NT) {
+        const u64 P = tp.base + g.S * (u64)d;
+        const u64 live = P >= dig.L ? 0 : (dig.L - P < (u64)C ? dig.L - P : (u64)C);
+        const u64 top = dig.L - 1 - P;  // wraps (no match) when the row starts past L - 1
+        rinfo[d] = make_uint2((u32)((P * dig.width) & 127) | ((u32)live << 7), top < (u64)C ? (u32)top : (u32)C);
+    }
 }
 
 template <int R, int C, bool PACK, bool WIDE = false>
 struct StageSize {
     // one staged tile, in 8-byte words: a [R][C] tile of words, of 16-bit digits,
-    // or (WIDE) R rows of limb chunks
-    static constexpr int WORDS = !PACK ? R * C : WIDE ? R * wide_row_chunks(C) * 2 : R * C / 4;
+    // or (WIDE) R rows of limb chunks and a word of row facts per row; even, so
+    // that the second operand's tile stays 16-byte aligned for cp.async
+    static constexpr int WORDS = !PACK ? R * C : WIDE ? (R * wide_row_chunks(C) * 2 + R + 1) & ~1 : R * C / 4;
+    static_assert(WORDS % 2 == 0, "staged tiles must keep 16-byte alignment");
     static constexpr size_t BYTES = (size_t)(TILE + 2 * WORDS) * sizeof(u64);
 };
 

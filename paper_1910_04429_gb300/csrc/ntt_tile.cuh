@@ -202,11 +202,12 @@ struct Strided {
                 if (tp.base + c + g.S * (u64)d == dig.L - 1) x &= (uint16_t)dig.top_mask;
                 v[j1] = x;
             } else if (PACK) {
-                const u64 P = tp.base + g.S * (u64)d, pos = P + c;
+                // the row's bit offset and live digits, worked out once when it was staged
+                const uint2 ri = reinterpret_cast<const uint2*>(st64 + R * wide_row_chunks(C) * 2)[d];
                 const u32* row = reinterpret_cast<const u32*>(st64) + d * wide_row_chunks(C) * 4;
-                u64 x = wide_digit(row, (u32)((P * dig.width) & 127), dig.width, c);
-                if (pos >= dig.L) x = 0;
-                else if (pos == dig.L - 1) x &= dig.top_mask;
+                u64 x = wide_digit(row, ri.x & 127u, dig.width, c);
+                if ((u32)c >= (ri.x >> 7)) x = 0;
+                else if ((u32)c == ri.y) x &= dig.top_mask;
                 v[j1] = x;
             } else {
                 v[j1] = st64[d * C + c];
