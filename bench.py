@@ -88,6 +88,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--plan-variant", type=int, default=None,
+                   help="force this plan variant (PA_PLAN_* bits) for the workload's transform length")
     p.add_argument("--no-small", action="store_true", help="skip the 10^6-bit block measurement")
     p.add_argument("--no-toeplitz", action="store_true", help="skip the Toeplitz-hash measurement")
     p.add_argument("--no-forms", action="store_true",
@@ -238,7 +240,7 @@ TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 109.8e6, "src_sha": "93d8de3f12
 # The sources that define the hash's kernels and their launch sequence (the
 # profiled code); host-only files (API, serving, adapters) are not part of it.
 KERNEL_SOURCES = ["gl.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "cp_async.cuh", "pdl.cuh", "plan.h",
-                  "pa_internal.h", "carry.cuh", "grid_sync.cuh", "pa_ntt.cu", "pa_ntt_batch.cu", "pa_carry.cu",
+                  "pa_internal.h", "carry.cuh", "grid_sync.cuh", "bulk_copy.cuh", "pa_ntt.cu", "pa_ntt_batch.cu", "pa_carry.cu",
                   "pa_fallback.cu", "pa_persist.cu"]
 
 
@@ -293,6 +295,9 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     binding.prepare(n)
     variant = None if args.no_autotune else binding.autotune(n, reps=5)
+    if args.plan_variant is not None:
+        binding.plan_override_length(binding.plan_info(n, m)["first"], args.plan_variant)
+        variant = args.plan_variant
 
     def step(i):
         x, a, b = dblocks[i % ROTATE]

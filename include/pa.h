@@ -286,8 +286,10 @@ int pa_prepare(uint64_t n);
  * bits: the odd first radix run last instead of first; forward or inverse
  * strided passes loading their tiles directly instead of staging them with
  * asynchronous copies; for transforms of at most 64 tiles with one strided
- * pass, single-block tiles of a quarter of the columns, four times the CTAs).
- * Variants are 0 .. 15. pa_autotune times the applicable plans for the
+ * pass, single-block tiles of a quarter of the columns, four times the CTAs;
+ * for single blocks, the staged word tiles of the strided passes copied by one
+ * bulk copy per tile row (cp.async.bulk completing on an mbarrier) instead of
+ * per-thread 16-byte asynchronous copies). Variants are 0 .. 31. pa_autotune times the applicable plans for the
  * transform length that keys of n bits use (the fastest of three runs of reps
  * hashes each, on synthetic data, synchronous; it allocates with cudaMalloc)
  * and keeps the fastest for
@@ -302,6 +304,7 @@ int pa_prepare(uint64_t n);
 #define PA_PLAN_DIRECT_FWD 2
 #define PA_PLAN_DIRECT_INV 4
 #define PA_PLAN_NARROW 8
+#define PA_PLAN_BULK 16
 int pa_autotune(uint64_t n, int reps, int* variant_out);
 int pa_plan_override(uint64_t n, int variant);
 /* pa_plan_override_length: the same for the transform length N itself (a length

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libpa_gb300.so")
 SOURCES = ["pa_ntt.cu", "pa_ntt_batch.cu", "pa_api.cu", "pa_carry.cu", "pa_fallback.cu", "pa_noalloc.cu",
            "pa_serve.cu", "pa_bits.cu", "pa_toeplitz.cu", "pa_persist.cu"]
 HEADERS = ["gl.cuh", "ntt_tile.cuh", "ntt_kernels.cuh", "plan.h", "pa_internal.h", "cp_async.cuh", "pdl.cuh",
-           "carry.cuh", "grid_sync.cuh"]
+           "carry.cuh", "grid_sync.cuh", "bulk_copy.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <unordered_set>
 
+#include "bulk_copy.cuh"
 #include "cp_async.cuh"
 #include "pdl.cuh"
 #include "pa_internal.h"
@@ -89,6 +90,25 @@ __device__ __forceinline__ void stage_wide(u64* stage, const Digits& dig, const 
     }
 }
 
+// Plan variant PLAN_BULK: a tile's R rows of C words by one bulk copy each,
+// issued by warp 0 and completing on `bar` (armed here with the tile's bytes).
+// Row d starts at word base + S d: bases and strides are even and the rows
+// C >= 16 words long, so every copy is 16-byte aligned and sized.
+template <int R, int C>
+__device__ __forceinline__ void stage_rows_bulk(u64* stage, const u64* buf, const StridedGeom& g,
+                                                const TilePos& tp, uint64_t* bar) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_arrive_expect(bar, (uint32_t)(R * C * sizeof(u64)));
+    __syncwarp();
+    for (int d = lane; d < R; d += 32)
+        bulk_g2s(stage + d * C, buf + tp.base + g.S * (u64)d, (uint32_t)(C * sizeof(u64)), bar);
+}
+
+// polls of a bulk copy's barrier before the kernel gives up on it (seconds)
+constexpr uint32_t BULK_WAIT_LIMIT = 1u << 22;
+// sticky: a bulk-copy wait ran out (this translation unit's kernels; pa_device_status)
+static __device__ u32 g_bulk_status;
+
 template <int R, int C, bool PACK, bool WIDE = false>
 struct StageSize {
     // one staged tile, in 8-byte words: a [R][C] tile of words, of 16-bit digits,
@@ -105,15 +125,23 @@ struct StageSize {
 // shared memory asynchronously first, so a's loads overlap x's arithmetic.
 // (the body: one tile of block io, dynamic shared memory dsm; the kernel below
 // and the persistent batched kernel run it)
-template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS, bool WIDE>
+template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS, bool WIDE, bool BULK = false>
 __device__ __forceinline__ void fwd_strided_tile(const StridedGeom& g, const BlockIO& io, const Twiddles& tw,
                                                  u64 tile, u64* dsm) {
     using S = Strided<RA, RB, C>;
     using SZ = StageSize<S::R, C, PACK, WIDE>;
+    constexpr bool BULK_ROWS = STAGED && BULK && !PACK;  // words staged by bulk copies
     u64* sm = dsm;
     u64* st[2] = {dsm + TILE, dsm + TILE + SZ::WORDS};
     TilePos tp = S::tile(g, tile);
-    if (STAGED) {
+    __shared__ __align__(8) uint64_t bars[BULK_ROWS ? 2 : 1];
+    if (BULK_ROWS) {
+        if (threadIdx.x == 0)
+            for (int op = 0; op < OPS; op++) mbar_init(&bars[op]);
+        __syncthreads();
+        if (threadIdx.x < 32)
+            for (int op = 0; op < OPS; op++) stage_rows_bulk<S::R, C>(st[op], op ? io.buf_a : io.buf_x, g, tp, &bars[op]);
+    } else if (STAGED) {
 #pragma unroll
         for (int op = 0; op < OPS; op++) {
             if (PACK) {
@@ -136,7 +164,9 @@ __device__ __forceinline__ void fwd_strided_tile(const StridedGeom& g, const Blo
     for (int op = 0; op < OPS; op++) {
         u64* buf = op ? io.buf_a : io.buf_x;
         const Digits& d = op ? io.da : io.dx;
-        if (STAGED) {
+        if (BULK_ROWS) {
+            if (!mbar_wait(&bars[op], 0, BULK_WAIT_LIMIT)) atomicOr(&g_bulk_status, PA_STATUS_TIMEOUT);
+        } else if (STAGED) {
             if (op || OPS == 1) cp_async_wait<0>();
             else cp_async_wait<1>();
         }
@@ -160,13 +190,13 @@ __device__ __forceinline__ void fwd_strided_tile(const StridedGeom& g, const Blo
     }
 }
 
-template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS, bool WIDE = false>
+template <int RA, int RB, int C, bool PACK, int B, bool STAGED, int OPS, bool WIDE = false, bool BULK = false>
 __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     pdl_begin();
     clear_states(nb, NT);
     extern __shared__ __align__(16) u64 dsm[];
-    fwd_strided_tile<RA, RB, C, PACK, STAGED, OPS, WIDE>(g, nb.io[blockIdx.y], tw, blockIdx.x, dsm);
+    fwd_strided_tile<RA, RB, C, PACK, STAGED, OPS, WIDE, BULK>(g, nb.io[blockIdx.y], tw, blockIdx.x, dsm);
 }
 
 // Inverse strided pass over one tile. STAGED: the tile is copied into shared
@@ -174,23 +204,34 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_strided(StridedGeom g, const __gr
 // first phase loads it directly (the autotuner picks per transform length).
 // Three CTAs per SM (40 registers): the extra warps hide the global-load latency
 // this one-operand pass is exposed to.
-template <int RA, int RB, int C, bool LAST, bool STAGED>
+template <int RA, int RB, int C, bool LAST, bool STAGED, bool BULK = false>
 __device__ __forceinline__ void inv_strided_tile(const StridedGeom& g, const BlockIO& io, const Twiddles& tw,
                                                  u64 tile, u64* dsm) {
     using S = Strided<RA, RB, C>;
     u64* sm = dsm;
     u64* st = dsm + TILE;
     TilePos tp = S::tile(g, tile);
+    __shared__ __align__(8) uint64_t bar;
     if (STAGED) {
-        stage_words<S::R, C>(st, io.buf_x, g, tp);
-        cp_async_commit();
+        if (BULK) {
+            if (threadIdx.x == 0) mbar_init(&bar);
+            __syncthreads();
+            if (threadIdx.x < 32) stage_rows_bulk<S::R, C>(st, io.buf_x, g, tp, &bar);
+        } else {
+            stage_words<S::R, C>(st, io.buf_x, g, tp);
+            cp_async_commit();
+        }
         u64 w[S::ITEMS_B][RA];
 #pragma unroll
         for (int i = 0; i < S::ITEMS_B; i++) {
             int it = threadIdx.x + i * NT;
             if (S::NB % NT == 0 || it < S::NB) S::inv_twiddles(g, tp, it, tw, w[i]);
         }
-        cp_async_wait<0>();
+        if (BULK) {
+            if (!mbar_wait(&bar, 0, BULK_WAIT_LIMIT)) atomicOr(&g_bulk_status, PA_STATUS_TIMEOUT);
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < S::ITEMS_B; i++) {
@@ -212,12 +253,12 @@ __device__ __forceinline__ void inv_strided_tile(const StridedGeom& g, const Blo
     }
 }
 
-template <int RA, int RB, int C, bool LAST, int B, bool STAGED>
+template <int RA, int RB, int C, bool LAST, int B, bool STAGED, bool BULK = false>
 __global__ void __launch_bounds__(NT, 3) k_inv_strided(StridedGeom g, const __grid_constant__ NttBatch<B> nb,
                                                        Twiddles tw) {
     pdl_begin();
     extern __shared__ __align__(16) u64 dsm[];
-    inv_strided_tile<RA, RB, C, LAST, STAGED>(g, nb.io[blockIdx.y], tw, blockIdx.x, dsm);
+    inv_strided_tile<RA, RB, C, LAST, STAGED, BULK>(g, nb.io[blockIdx.y], tw, blockIdx.x, dsm);
 }
 
 // Forward contiguous pass of one tile; leaves the spectrum in registers.
@@ -426,11 +467,11 @@ struct Launcher {
 
     int ops;               // 2: transform x and a; 1: x only (a's spectrum reused)
 
-    template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS, bool WIDE = false>
+    template <int RA, int RB, int C, bool PACK, bool STAGED, int OPS, bool WIDE = false, bool BULK = false>
     void fwd_k() const {
         dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
         size_t smem = STAGED ? StageSize<RA * RB, C, PACK, WIDE>::BYTES : TILE * sizeof(u64);
-        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS, WIDE>;
+        auto k = k_fwd_strided<RA, RB, C, PACK, B, STAGED, OPS, WIDE, BULK>;
         allow_smem(k, smem);
         launch_pdl(k, grid, dim3(NT), smem, st, *g, *nb, *tw);
     }
@@ -439,6 +480,9 @@ struct Launcher {
     template <int RA, int RB, int C, int OPS>
     void fwd_ops(bool pack) const {
         if (!pack) {
+            if constexpr (B == 1) {
+                if (stage_fwd && bulk) return fwd_k<RA, RB, C, false, true, OPS, false, true>();
+            }
             if (stage_fwd) return fwd_k<RA, RB, C, false, true, OPS>();
             return fwd_k<RA, RB, C, false, false, OPS>();
         }
@@ -451,16 +495,22 @@ struct Launcher {
         if (ops == 1) return fwd_ops<RA, RB, C, 1>(pack);
         fwd_ops<RA, RB, C, 2>(pack);
     }
-    template <int RA, int RB, int C, bool LAST, bool STAGED>
+    template <int RA, int RB, int C, bool LAST, bool STAGED, bool BULK = false>
     void inv_k() const {
         dim3 grid((unsigned)(g->N / (RA * RB * C)), (unsigned)nb->count);
         size_t smem = (TILE + (STAGED ? RA * RB * C : 0)) * sizeof(u64);
-        auto k = k_inv_strided<RA, RB, C, LAST, B, STAGED>;
+        auto k = k_inv_strided<RA, RB, C, LAST, B, STAGED, BULK>;
         allow_smem(k, smem);
         launch_pdl(k, grid, dim3(NT), smem, st, *g, *nb, *tw);
     }
     template <int RA, int RB, int C>
     void inv(bool last) const {
+        if constexpr (B == 1) {
+            if (stage_inv && bulk) {
+                if (last) return inv_k<RA, RB, C, true, true, true>();
+                return inv_k<RA, RB, C, false, true, true>();
+            }
+        }
         if (last) {
             if (stage_inv) return inv_k<RA, RB, C, true, true>();
             return inv_k<RA, RB, C, true, false>();
@@ -474,6 +524,8 @@ struct Launcher {
     // digits wider than 16 bits (every digit source then 16-byte aligned: the
     // wide first pass always stages its rows)
     bool wide = false;
+    // plan variant PLAN_BULK (single blocks): staged word tiles by bulk row copies
+    bool bulk = false;
     template <int RA, int RB, int C>
     void fwd_narrow() const {  // the only strided pass: digits in
         if (wide) {
@@ -489,6 +541,7 @@ struct Launcher {
     }
     template <int RA, int RB, int C>
     void inv_narrow() const {  // the only strided pass: digits out
+        if (stage_inv && bulk) return inv_k<RA, RB, C, true, true, true>();
         if (stage_inv) return inv_k<RA, RB, C, true, true>();
         inv_k<RA, RB, C, true, false>();
     }
@@ -536,6 +589,7 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
                                 cudaStream_t st, int ops = 2) {
     bool stage_fwd = !(G.variant & PLAN_DIRECT_FWD), stage_inv = !(G.variant & PLAN_DIRECT_INV);
     bool narrow = narrow_plan<B>(G);
+    const bool bulk = B == 1 && (G.variant & PLAN_BULK);
     bool aligned = true;
     for (int i = 0; i < nb.count; i++)
         aligned = aligned && ((uintptr_t)nb.io[i].dx.src % 16 == 0) && ((uintptr_t)nb.io[i].da.src % 16 == 0) &&
@@ -554,8 +608,8 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = 0; p < G.nstrided; p++) {
         StridedGeom g = strided_geom(G, tw, p, narrow);
         prof_begin(st, p == 0 ? "ntt_fwd_strided_first" : "ntt_fwd_strided_r64");
-        Launcher<B>{&g, cur, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow, wide}.dispatch_fwd(G.pass[p].R,
-                                                                                                     p == 0);
+        Launcher<B>{&g, cur, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow, wide, bulk}.dispatch_fwd(
+            G.pass[p].R, p == 0);
         prof_end(st);
         cur = &later;
     }
@@ -597,7 +651,8 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     for (int p = G.nstrided - 1; p >= 0; p--) {
         StridedGeom g = strided_geom(G, tw, p, narrow);
         prof_begin(st, p == 0 ? "ntt_inv_strided_last" : "ntt_inv_strided_r64");
-        Launcher<B>{&g, &later, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow}.dispatch_inv(G.pass[p].R, p == 0);
+        Launcher<B>{&g, &later, &tw, st, aligned, ops, stage_fwd, stage_inv, narrow, wide, bulk}.dispatch_inv(
+            G.pass[p].R, p == 0);
         prof_end(st);
     }
     return cudaGetLastError();

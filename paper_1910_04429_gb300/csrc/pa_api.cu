@@ -175,7 +175,7 @@ int applicable_variants(const Geom& g) {
     if (g.nstrided == 0) return 0;
     int R0 = g.odd << ((g.logN - LOG_TILE) % 6);
     return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV |
-           (g.nstrided == 1 && g.N / TILE <= 64 ? PLAN_NARROW : 0);
+           (g.nstrided == 1 && g.N / TILE <= 64 ? PLAN_NARROW : 0) | PLAN_BULK;
 }
 
 // The plan for a transform length on device dev: base's length, with the
@@ -1313,7 +1313,7 @@ int pa_seed_destroy(pa_seed seed) {
 
 int pa_plan_override(uint64_t n, int variant) {
     if (n < 1 || n > PA_MAX_BITS || variant < -1 || variant >= PLAN_VARIANTS)
-        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 16");
+        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 32");
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
     cudaMemPool_t pool;
@@ -1328,7 +1328,7 @@ int pa_plan_override(uint64_t n, int variant) {
 
 int pa_plan_override_length(uint64_t N, int variant) {
     if (variant < -1 || variant >= PLAN_VARIANTS)
-        return fail(PA_EINVAL, "pa_plan_override_length: need -1 <= variant < 16");
+        return fail(PA_EINVAL, "pa_plan_override_length: need -1 <= variant < 32");
     if (N < 4096 || N > (1ull << MAX_LOGN) || choose_geom_len(N).N != N)
         return fail(PA_EINVAL, "pa_plan_override_length: not a transform length of the library");
     std::lock_guard<std::mutex> lk(g_mu);
@@ -1538,6 +1538,9 @@ int pa_device_status(int clear) {
     u32 fst = 0, pst = 0;
     if ((e = read_fallback_status(&fst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
     if ((e = read_persist_status(&pst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
+    u32 bst = 0;
+    if ((e = read_bulk_status(&bst, clear != 0)) != cudaSuccess) return cuda_fail(e, "device status");
+    if (bst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (bulk tile copy)");
     if (pst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (persistent transforms)");
     if (st & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (carry look-back)");
     if (fst & PA_STATUS_TIMEOUT) return fail(PA_ETIMEOUT, "a bounded device wait ran out (recomputation barrier)");

@@ -148,6 +148,9 @@ constexpr u32 PERSIST_SCRATCH_WORDS = 6;
 bool persist_eligible(const Geom& G);
 cudaError_t launch_persistent(const PersistJob* jobs, int count, u32* scratch, cudaStream_t st, u32* status);
 cudaError_t read_persist_status(u32* out, bool clear);
+// Sticky status of the single-block transform kernels' bulk-copy waits
+// (plan variant PLAN_BULK); synchronous.
+cudaError_t read_bulk_status(u32* out, bool clear);
 
 // Inter-pass twiddle tables of a strided pass (M = sub-problem size, S =
 // stride): out[0 .. M) = w_M^(j k) at k S + j, out[M .. 2M) = w_M^-(j k).

@@ -23,6 +23,16 @@ cudaError_t launch_pass_twiddles(const Twiddles& tw, u64 N, u64 M, u64 S, u64* o
     return cudaGetLastError();
 }
 
+// the sticky status of this file's kernels' bulk-copy waits (ntt_kernels.cuh)
+cudaError_t read_bulk_status(u32* out, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_bulk_status, sizeof(u32));
+    if (e == cudaSuccess && clear) {
+        u32 zero = 0;
+        e = cudaMemcpyToSymbol(g_bulk_status, &zero, sizeof(u32));
+    }
+    return e;
+}
+
 cudaError_t launch_convolution(const NttJob& j, cudaStream_t st) {
     NttBatch<1> nb;
     nb.count = 1;

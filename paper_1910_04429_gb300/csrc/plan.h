@@ -33,7 +33,8 @@ constexpr int PLAN_R0_LAST = 1;     // the odd radix R_0 runs last among the str
 constexpr int PLAN_DIRECT_FWD = 2;  // forward strided passes load their tiles directly
 constexpr int PLAN_DIRECT_INV = 4;  // inverse strided passes load their tiles directly
 constexpr int PLAN_NARROW = 8;      // single-pass plans, single blocks: tiles of a quarter of the columns
-constexpr int PLAN_VARIANTS = 16;
+constexpr int PLAN_BULK = 16;       // single blocks: staged word tiles by one bulk copy per row (cp.async.bulk)
+constexpr int PLAN_VARIANTS = 32;
 
 // N = R_0 * 64^q * 4096 with N = odd * 2^logN and R_0 = odd * 2^((logN-12) mod 6)
 // (omitted when 1; at most 48 for odd = 3, 40 for odd = 5): one strided pass of

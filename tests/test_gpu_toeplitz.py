@@ -125,7 +125,7 @@ def test_toeplitz_autotune_keeps_exact():
     torch = _need_gpu()
     n, m = 300_000, 120_000
     v = binding.toeplitz_autotune(n, m, reps=2)
-    assert 0 <= v < 16
+    assert 0 <= v < 32
     blk = inputs.make_toeplitz_block(n, m, seed=21)
     got = binding.toeplitz(dev(blk.x), dev(blk.s), n, m)
     torch.cuda.synchronize()
