@@ -289,7 +289,10 @@ int pa_prepare(uint64_t n);
  * pass, single-block tiles of a quarter of the columns, four times the CTAs;
  * for single blocks, the staged word tiles of the strided passes copied by one
  * bulk copy per tile row (cp.async.bulk completing on an mbarrier) instead of
- * per-thread 16-byte asynchronous copies). Variants are 0 .. 31. pa_autotune times the applicable plans for the
+ * per-thread 16-byte asynchronous copies; for single blocks whose transform
+ * has at most 64 tiles of 4096 words, each tile's pass run by a cluster of four
+ * CTAs on four SMs, exchanging the tile's rows and columns through distributed
+ * shared memory, instead of by one CTA). Variants are 0 .. 63. pa_autotune times the applicable plans for the
  * transform length that keys of n bits use (the fastest of three runs of reps
  * hashes each, on synthetic data, synchronous; it allocates with cudaMalloc)
  * and keeps the fastest for
@@ -305,6 +308,7 @@ int pa_prepare(uint64_t n);
 #define PA_PLAN_DIRECT_INV 4
 #define PA_PLAN_NARROW 8
 #define PA_PLAN_BULK 16
+#define PA_PLAN_CLUSTER 32
 int pa_autotune(uint64_t n, int reps, int* variant_out);
 int pa_plan_override(uint64_t n, int variant);
 /* pa_plan_override_length: the same for the transform length N itself (a length

@@ -123,6 +123,9 @@ def library_path() -> str:
 def load(build_if_missing: bool = True):
     """Load the CUDA library (building it from csrc/ if it is absent or stale)."""
     global _lib
+    lib = _lib
+    if lib is not None:  # loaded: no lock on the per-call path
+        return lib
     with _lock:
         if _lib is None:
             path = _build.LIB
@@ -144,24 +147,34 @@ def _check(rc: int, what: str):
         raise PaError(rc, f"{what}: {load().pa_last_error().decode()}")
 
 
-def _dev_ptr(t, limbs: int, name: str):
-    import torch
+_LIMB_DTYPES = None  # (torch.int64, torch.uint64), set on first use
 
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+
+def _dev_ptr(t, limbs: int, name: str):
+    global _LIMB_DTYPES
+    if _LIMB_DTYPES is None:
+        import torch
+
+        _LIMB_DTYPES = (torch.int64, torch.uint64)
+    try:
+        cuda, dtype = t.is_cuda, t.dtype
+    except AttributeError:
+        raise TypeError(f"{name} must be a CUDA tensor") from None
+    if not cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+    if dtype not in _LIMB_DTYPES or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous int64/uint64 tensor")
     if t.numel() < limbs:
         raise ValueError(f"{name} has {t.numel()} limbs, needs {limbs}")
-    return ctypes.c_void_p(t.data_ptr())
+    return t.data_ptr()  # a plain int: the c_void_p argtype converts it
 
 
 def _stream_ptr(stream):
-    import torch
-
     if stream is None:
+        import torch
+
         stream = torch.cuda.current_stream()
-    return ctypes.c_void_p(stream.cuda_stream)
+    return stream.cuda_stream
 
 
 def limbs(bits: int) -> int:
@@ -337,8 +350,8 @@ def hash_batched(blocks, stream=None):
     arr = (PaBlock * len(blocks))()
     for i, (k, a, b, n, m, o) in enumerate(blocks):
         L = limbs(n)
-        arr[i] = PaBlock(_dev_ptr(k, L, "key").value, _dev_ptr(a, L, "seed_a").value,
-                         _dev_ptr(b, L, "seed_b").value, n, m, _dev_ptr(o, limbs(m), "out").value)
+        arr[i] = PaBlock(_dev_ptr(k, L, "key"), _dev_ptr(a, L, "seed_a"),
+                         _dev_ptr(b, L, "seed_b"), n, m, _dev_ptr(o, limbs(m), "out"))
     _check(load().pa_hash_batched(arr, len(blocks), _stream_ptr(stream)), "pa_hash_batched")
 
 
@@ -352,8 +365,8 @@ def serve_init(device: int = -1, max_batch: int = 0, streams: int = 0, max_pendi
 def submit(key, seed_a, seed_b, n: int, m: int, out) -> int:
     """Queue one block (CUDA tensors that must stay alive until it completes)."""
     L = limbs(n)
-    blk = PaBlock(_dev_ptr(key, L, "key").value, _dev_ptr(seed_a, L, "seed_a").value,
-                  _dev_ptr(seed_b, L, "seed_b").value, n, m, _dev_ptr(out, limbs(m), "out").value)
+    blk = PaBlock(_dev_ptr(key, L, "key"), _dev_ptr(seed_a, L, "seed_a"),
+                  _dev_ptr(seed_b, L, "seed_b"), n, m, _dev_ptr(out, limbs(m), "out"))
     t = ctypes.c_uint64(0)
     rc = load().pa_submit(ctypes.byref(blk), ctypes.byref(t))
     if rc != PA_OK:
@@ -424,8 +437,8 @@ class Batch:
         arr = (PaBlock * len(blocks))()
         for i, (k, a, b, n, m, o) in enumerate(blocks):
             L = limbs(n)
-            arr[i] = PaBlock(_dev_ptr(k, L, "key").value, _dev_ptr(a, L, "seed_a").value,
-                             _dev_ptr(b, L, "seed_b").value, n, m, _dev_ptr(o, limbs(m), "out").value)
+            arr[i] = PaBlock(_dev_ptr(k, L, "key"), _dev_ptr(a, L, "seed_a"),
+                             _dev_ptr(b, L, "seed_b"), n, m, _dev_ptr(o, limbs(m), "out"))
         h = ctypes.c_void_p(0)
         _check(load().pa_batch_create(arr, len(blocks), ctypes.byref(h)), "pa_batch_create")
         self.handle = h
@@ -445,6 +458,11 @@ def autotune(n: int, reps: int = 5) -> int:
     v = ctypes.c_int(0)
     _check(load().pa_autotune(n, reps, ctypes.byref(v)), "pa_autotune")
     return int(v.value)
+
+
+# plan variant bits (include/pa.h PA_PLAN_*); variants are 0 .. PLAN_VARIANTS - 1
+PLAN_R0_LAST, PLAN_DIRECT_FWD, PLAN_DIRECT_INV, PLAN_NARROW, PLAN_BULK, PLAN_CLUSTER = 1, 2, 4, 8, 16, 32
+PLAN_VARIANTS = 64
 
 
 def plan_override(n: int, variant: int):

@@ -8,6 +8,8 @@
 // geometry: blockIdx.x is the tile, blockIdx.y the block, and the per-block
 // buffers and digit sources arrive in a __grid_constant__ parameter array.
 #pragma once
+#include <cooperative_groups.h>
+
 #include <mutex>
 #include <unordered_set>
 
@@ -430,6 +432,143 @@ static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_c
 }
 
 // ---------------------------------------------------------------------------
+// The tile pass on a cluster of four CTAs per tile (plan variant PLAN_CLUSTER:
+// single blocks of at most CLUSTER_MAX_TILES tiles, both operands), the same
+// arithmetic as contig_both_tile spread over four SMs. CTA q of the cluster
+// takes tile columns 16q .. 16q + 15 for the column half of a's and x's
+// forward transforms, tile rows 16q .. 16q + 15 for the row half, the product
+// and the row half of the inverse, and its columns again for the column half
+// of the inverse. The two transposes between the halves store into the owning
+// CTA's shared memory through the cluster (distributed shared memory), each
+// followed by a cluster barrier. Thread (warp u, lane): lanes 0-15 are a's
+// columns or rows, lanes 16-31 x's; after the product only x is transformed.
+// ---------------------------------------------------------------------------
+constexpr int CL_Q = 4;                          // CTAs per tile
+constexpr int CL_THREADS = 256;                  // 8 warps: u = warp
+constexpr int CL_LINES = 64 / CL_Q;              // columns (rows) per CTA
+constexpr int CL_CP = CL_LINES + 1;              // column-buffer pitch: a lane's row access hits 16 banks
+constexpr int CL_COLBUF = 64 * CL_CP;            // one operand's 64 rows x 16 columns
+constexpr int CL_ROWBUF = CL_LINES * TILE_PITCH; // one operand's 16 rows x 64 columns
+
+template <bool PACK>
+__global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
+    k_contig_cluster(const __grid_constant__ NttBatch<1> nb, u64 ninv, Twiddles tw) {
+    namespace cg = cooperative_groups;
+    pdl_begin();
+    clear_states(nb, CL_THREADS);
+    __shared__ u64 colbuf[2 * CL_COLBUF];
+    __shared__ u64 rowbuf[2 * CL_ROWBUF];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const BlockIO& io = nb.io[0];
+    const u64 base = (u64)(blockIdx.x / CL_Q) * TILE;
+    const int u = threadIdx.x >> 5, lane = threadIdx.x & 31, op = lane >> 4, li = lane & 15;
+    const int c = CL_LINES * q + li;  // the thread's tile column in the column halves
+    const bool scaled = tw.w4096s != nullptr;
+    u64 v[8];
+
+    // forward column half of operand op, column c (as c_fwd_col_a / c_fwd_col_b)
+    {
+        u64* cb = colbuf + op * CL_COLBUF;
+        const u64* src = (op ? io.buf_x : io.buf_a) + base;
+#pragma unroll
+        for (int j1 = 0; j1 < 8; j1++) {
+            int off = (u + 8 * j1) * 64 + c;
+            v[j1] = PACK ? digit_at(op ? io.dx : io.da, base + off) : src[off];
+        }
+        gl::dft<8, false>(v);
+        gl::RowRoots<64, false, 8, 8>::apply(v, u);
+#pragma unroll
+        for (int kr = 0; kr < 8; kr++) cb[(kr * 8 + u) * CL_CP + li] = v[kr];
+        __syncthreads();
+#pragma unroll
+        for (int j0 = 0; j0 < 8; j0++) v[j0] = cb[(u * 8 + j0) * CL_CP + li];
+        gl::dft<8, false>(v);
+        const u64* w = (op == 0 && scaled) ? tw.w4096s : tw.w4096;
+#pragma unroll
+        for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(v[ks], w[c * (8 * ks + u)]);
+    }
+    // tile row k = 8 ks + u, column c, into the row buffer of the CTA owning row
+    // k (rank k / 16 = ks / 2, local row 8 (ks & 1) + u)
+    {
+        u64* rb[CL_Q];
+#pragma unroll
+        for (int r = 0; r < CL_Q; r++) rb[r] = cluster.map_shared_rank(rowbuf + op * CL_ROWBUF, r);
+#pragma unroll
+        for (int ks = 0; ks < 8; ks++) rb[ks >> 1][(8 * (ks & 1) + u) * TILE_PITCH + c] = v[ks];
+    }
+    cluster.sync();
+
+    // forward row half of operand op, tile row 16 q + li (as c_fwd_row_a / c_fwd_row_b);
+    // each thread rewrites only the words it read before the barrier
+    u64* row = rowbuf + op * CL_ROWBUF + li * TILE_PITCH;
+#pragma unroll
+    for (int j1 = 0; j1 < 8; j1++) v[j1] = row[u + 8 * j1];
+    gl::dft<8, false>(v);
+    gl::RowRoots<64, false, 8, 8>::apply(v, u);
+#pragma unroll
+    for (int kr = 0; kr < 8; kr++) row[kr * 8 + u] = v[kr];
+    __syncthreads();
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0++) v[j0] = row[u * 8 + j0];
+    gl::dft<8, false>(v);  // v[ks]: the spectrum at (row 16 q + li, column 8 ks + u)
+    // the product (Algorithm 1 step 4) in x's lanes, a's spectrum from lane - 16
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        u64 av = __shfl_xor_sync(0xffffffffu, v[k], 16);
+        if (op) v[k] = gl::mul(v[k], scaled ? av : gl::mul(av, ninv));
+    }
+    // inverse row half of x (as c_inv_row_b_store / c_inv_row_a_load)
+    if (op) {
+        gl::dft<8, true>(v);
+#pragma unroll
+        for (int j0 = 0; j0 < 8; j0++) row[u * 8 + j0] = v[j0];  // the words this thread read last
+    }
+    __syncthreads();
+    if (op) {
+#pragma unroll
+        for (int kr = 0; kr < 8; kr++) v[kr] = row[kr * 8 + u];
+        gl::RowRoots<64, true, 8, 8>::apply(v, u);
+        gl::dft<8, true>(v);
+        // v[j1]: row 16 q + li, column u + 8 j1, to the CTA owning that column
+        // (rank j1 / 2, local column u + 8 (j1 & 1)), in x's column buffer
+        u64* cbx[CL_Q];
+#pragma unroll
+        for (int r = 0; r < CL_Q; r++) cbx[r] = cluster.map_shared_rank(colbuf + CL_COLBUF, r);
+#pragma unroll
+        for (int j1 = 0; j1 < 8; j1++)
+            cbx[j1 >> 1][(CL_LINES * q + li) * CL_CP + u + 8 * (j1 & 1)] = v[j1];
+    }
+    cluster.sync();
+
+    // inverse column half of x, column c, in lanes 0-15 (as c_inv_col_b, c_inv_col_a)
+    u64* xc = colbuf + CL_COLBUF;
+    if (!op) {
+#pragma unroll
+        for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(xc[(8 * ks + u) * CL_CP + li], tw.w4096i[c * (8 * ks + u)]);
+        gl::dft<8, true>(v);
+    }
+    __syncthreads();
+    if (!op) {
+#pragma unroll
+        for (int j0 = 0; j0 < 8; j0++) xc[(u * 8 + j0) * CL_CP + li] = v[j0];
+    }
+    __syncthreads();
+    if (!op) {
+#pragma unroll
+        for (int kr = 0; kr < 8; kr++) v[kr] = xc[(kr * 8 + u) * CL_CP + li];
+        gl::RowRoots<64, true, 8, 8>::apply(v, u);
+        gl::dft<8, true>(v);
+#pragma unroll
+        for (int j1 = 0; j1 < 8; j1++) {
+            const u64 p = base + (u64)((u + 8 * j1) * 64 + c);
+            if (!PACK) io.buf_x[p] = v[j1];
+            else if (p < io.L) io.buf_x[p] = gl::canon(v[j1]);  // the transform's last pass: exact digits
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
 
@@ -618,7 +757,15 @@ static cudaError_t launch_batch(const Geom& G, const Twiddles& tw, const NttBatc
     u64 ninv = n_inverse(G.logN, G.odd);
     bool paired = false;
     if constexpr (B == 1) {
-        if (ops == 2 && narrow && !pack) {
+        if (ops == 2 && (G.variant & PLAN_CLUSTER) && G.N / TILE <= CLUSTER_MAX_TILES) {
+            // each tile's pass on a four-CTA cluster
+            dim3 cgrid((unsigned)(CL_Q * (G.N / TILE)), 1);
+            prof_begin(st, "ntt_contig_both");
+            if (pack) launch_pdl(k_contig_cluster<true>, cgrid, dim3(CL_THREADS), 0, st, *cur, ninv, tw);
+            else launch_pdl(k_contig_cluster<false>, cgrid, dim3(CL_THREADS), 0, st, *cur, ninv, tw);
+            prof_end(st);
+            paired = true;
+        } else if (ops == 2 && narrow && !pack) {
             // few tiles: the two operands' forward tile passes side by side
             constexpr size_t smem = (2 * TILE_SM + TILE) * sizeof(u64);
             prof_begin(st, "ntt_contig_both");

@@ -172,10 +172,11 @@ Geom geom_for_bits(uint64_t n) { return choose_geom((n + 15) / 16); }
 
 // Plan variants that change anything for this transform length.
 int applicable_variants(const Geom& g) {
-    if (g.nstrided == 0) return 0;
+    const int cluster = g.N / TILE <= CLUSTER_MAX_TILES ? PLAN_CLUSTER : 0;
+    if (g.nstrided == 0) return cluster;
     int R0 = g.odd << ((g.logN - LOG_TILE) % 6);
     return (R0 > 1 && g.nstrided > 1 ? PLAN_R0_LAST : 0) | PLAN_DIRECT_FWD | PLAN_DIRECT_INV |
-           (g.nstrided == 1 && g.N / TILE <= 64 ? PLAN_NARROW : 0) | PLAN_BULK;
+           (g.nstrided == 1 && g.N / TILE <= 64 ? PLAN_NARROW : 0) | PLAN_BULK | cluster;
 }
 
 // The plan for a transform length on device dev: base's length, with the
@@ -1313,7 +1314,7 @@ int pa_seed_destroy(pa_seed seed) {
 
 int pa_plan_override(uint64_t n, int variant) {
     if (n < 1 || n > PA_MAX_BITS || variant < -1 || variant >= PLAN_VARIANTS)
-        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 32");
+        return fail(PA_EINVAL, "pa_plan_override: need 1 <= n <= PA_MAX_BITS, -1 <= variant < 64");
     std::lock_guard<std::mutex> lk(g_mu);
     int dev;
     cudaMemPool_t pool;
@@ -1328,7 +1329,7 @@ int pa_plan_override(uint64_t n, int variant) {
 
 int pa_plan_override_length(uint64_t N, int variant) {
     if (variant < -1 || variant >= PLAN_VARIANTS)
-        return fail(PA_EINVAL, "pa_plan_override_length: need -1 <= variant < 32");
+        return fail(PA_EINVAL, "pa_plan_override_length: need -1 <= variant < 64");
     if (N < 4096 || N > (1ull << MAX_LOGN) || choose_geom_len(N).N != N)
         return fail(PA_EINVAL, "pa_plan_override_length: not a transform length of the library");
     std::lock_guard<std::mutex> lk(g_mu);

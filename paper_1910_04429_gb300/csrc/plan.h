@@ -34,7 +34,9 @@ constexpr int PLAN_DIRECT_FWD = 2;  // forward strided passes load their tiles d
 constexpr int PLAN_DIRECT_INV = 4;  // inverse strided passes load their tiles directly
 constexpr int PLAN_NARROW = 8;      // single-pass plans, single blocks: tiles of a quarter of the columns
 constexpr int PLAN_BULK = 16;       // single blocks: staged word tiles by one bulk copy per row (cp.async.bulk)
-constexpr int PLAN_VARIANTS = 32;
+constexpr int PLAN_CLUSTER = 32;    // single blocks of at most 64 tiles: the tile pass on four-CTA clusters
+constexpr int PLAN_VARIANTS = 64;
+constexpr uint64_t CLUSTER_MAX_TILES = 64;  // PLAN_CLUSTER: transforms of at most this many tiles
 
 // N = R_0 * 64^q * 4096 with N = odd * 2^logN and R_0 = odd * 2^((logN-12) mod 6)
 // (omitted when 1; at most 48 for odd = 3, 40 for odd = 5): one strided pass of

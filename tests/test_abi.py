@@ -107,8 +107,8 @@ def test_argument_checks_without_gpu():
     assert lib.pa_prepare(0) == binding.PA_EINVAL
     assert lib.pa_fault_inject(99) == binding.PA_EINVAL
     assert lib.pa_plan_override(0, 0) == binding.PA_EINVAL
-    assert lib.pa_plan_override(1000, 32) == binding.PA_EINVAL
-    assert lib.pa_plan_override_length(4096, 32) == binding.PA_EINVAL
+    assert lib.pa_plan_override(1000, binding.PLAN_VARIANTS) == binding.PA_EINVAL
+    assert lib.pa_plan_override_length(4096, binding.PLAN_VARIANTS) == binding.PA_EINVAL
     assert lib.pa_plan_override_length(4097, 0) == binding.PA_EINVAL  # not a transform length
     assert lib.pa_autotune(0, 1, None) == binding.PA_EINVAL
     h = ctypes.c_void_p(0)
