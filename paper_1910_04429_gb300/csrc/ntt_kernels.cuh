@@ -433,22 +433,77 @@ static __global__ void __launch_bounds__(2 * NT, 1) k_contig_pair(const __grid_c
 
 // ---------------------------------------------------------------------------
 // The tile pass on a cluster of four CTAs per tile (plan variant PLAN_CLUSTER:
-// single blocks of at most CLUSTER_MAX_TILES tiles, both operands), the same
-// arithmetic as contig_both_tile spread over four SMs. CTA q of the cluster
+// single blocks of at most CLUSTER_MAX_TILES tiles, both operands): the
+// arithmetic of contig_both_tile spread over four SMs. CTA q of the cluster
 // takes tile columns 16q .. 16q + 15 for the column half of a's and x's
 // forward transforms, tile rows 16q .. 16q + 15 for the row half, the product
 // and the row half of the inverse, and its columns again for the column half
 // of the inverse. The two transposes between the halves store into the owning
 // CTA's shared memory through the cluster (distributed shared memory), each
-// followed by a cluster barrier. Thread (warp u, lane): lanes 0-15 are a's
-// columns or rows, lanes 16-31 x's; after the product only x is transformed.
+// followed by a cluster barrier. Every 64-point DFT runs as three radix-4
+// steps on 16 threads (one per warp, 4 values each), so that a thread's chain
+// of dependent instructions is short: a small transform is bound by that
+// latency, not by throughput. Lanes 0-15 hold a's columns or rows, lanes
+// 16-31 x's; after the product the a lanes run the inverse steps on their own
+// (dead) data, so that no warp diverges, and store nothing.
 // ---------------------------------------------------------------------------
 constexpr int CL_Q = 4;                          // CTAs per tile
-constexpr int CL_THREADS = 256;                  // 8 warps: u = warp
+constexpr int CL_THREADS = 512;                  // 16 warps: w = warp
 constexpr int CL_LINES = 64 / CL_Q;              // columns (rows) per CTA
-constexpr int CL_CP = CL_LINES + 1;              // column-buffer pitch: a lane's row access hits 16 banks
+constexpr int CL_CP = CL_LINES + 1;              // column-buffer pitch: lanes on 16 rows hit 16 banks
 constexpr int CL_COLBUF = 64 * CL_CP;            // one operand's 64 rows x 16 columns
 constexpr int CL_ROWBUF = CL_LINES * TILE_PITCH; // one operand's 16 rows x 64 columns
+
+// Forward length-64 DFT over the 16 warps of a CTA, 4 values a thread, for
+// one line per lane, with b (the line's 64 words at stride s) for the two
+// exchanges. In: warp w holds x[w + 16 j] in v[j]. Out: warp w = 4 kh + th
+// holds X[kh + 4 th + 16 t] in v[t]. Position p of the line is 64 = 4 x 16
+// (p = r + 16 j), then 16 = 4 x 4 (r = sl + 4 sh): a DFT over j with roots
+// w_64^(r kh), a DFT over sh with roots w_16^(sl th), a DFT over sl. The
+// stores in the first step go to the words the thread's own loads came from,
+// if they came from b.
+__device__ __forceinline__ void dft64_fwd_r4(u64* v, u64* b, int s, int w) {
+    gl::dft<4, false>(v);
+    gl::RowRoots<64, false, 4, 16>::apply(v, w);
+#pragma unroll
+    for (int kh = 0; kh < 4; kh++) b[(16 * kh + w) * s] = v[kh];
+    __syncthreads();
+    const int kh = w >> 2, sl = w & 3;
+#pragma unroll
+    for (int sh = 0; sh < 4; sh++) v[sh] = b[(16 * kh + sl + 4 * sh) * s];
+    gl::dft<4, false>(v);
+    gl::RowRoots<16, false, 4, 4>::apply(v, sl);
+#pragma unroll
+    for (int th = 0; th < 4; th++) b[(16 * kh + 4 * th + sl) * s] = v[th];  // the words it read
+    __syncthreads();
+    const int th = w & 3;
+#pragma unroll
+    for (int i = 0; i < 4; i++) v[i] = b[(16 * kh + 4 * th + i) * s];
+    gl::dft<4, false>(v);
+}
+
+// The inverse of dft64_fwd_r4 (without the 1/64): in, warp w = 4 kh + th holds
+// Y[kh + 4 th + 16 t] in v[t]; out, warp w holds 64 x[w + 16 j] in v[j]. The
+// first stores go to the words dft64_fwd_r4's last loads read in this thread.
+__device__ __forceinline__ void dft64_inv_r4(u64* v, u64* b, int s, int w) {
+    const int kh = w >> 2, th = w & 3;
+    gl::dft<4, true>(v);
+#pragma unroll
+    for (int i = 0; i < 4; i++) b[(16 * kh + 4 * th + i) * s] = v[i];
+    __syncthreads();
+    const int sl = w & 3;
+#pragma unroll
+    for (int t = 0; t < 4; t++) v[t] = b[(16 * kh + 4 * t + sl) * s];
+    gl::RowRoots<16, true, 4, 4>::apply(v, sl);
+    gl::dft<4, true>(v);
+#pragma unroll
+    for (int sh = 0; sh < 4; sh++) b[(16 * kh + sl + 4 * sh) * s] = v[sh];  // the words it read
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = b[(16 * k + w) * s];
+    gl::RowRoots<64, true, 4, 16>::apply(v, w);
+    gl::dft<4, true>(v);
+}
 
 template <bool PACK>
 __global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
@@ -462,112 +517,72 @@ __global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
     const int q = (int)cluster.block_rank();
     const BlockIO& io = nb.io[0];
     const u64 base = (u64)(blockIdx.x / CL_Q) * TILE;
-    const int u = threadIdx.x >> 5, lane = threadIdx.x & 31, op = lane >> 4, li = lane & 15;
-    const int c = CL_LINES * q + li;  // the thread's tile column in the column halves
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, op = lane >> 4, li = lane & 15;
+    const int c = CL_LINES * q + li;        // the lane's tile column in the column halves
+    const int kk = (w >> 2) + 4 * (w & 3);  // the frequencies kk + 16 t the warp ends with
     const bool scaled = tw.w4096s != nullptr;
-    u64 v[8];
+    u64* cb = colbuf + op * CL_COLBUF + li;               // column c of operand op, stride CL_CP
+    u64* rb = rowbuf + op * CL_ROWBUF + li * TILE_PITCH;  // row 16 q + li of operand op
+    u64 v[4];
 
-    // forward column half of operand op, column c (as c_fwd_col_a / c_fwd_col_b)
-    {
-        u64* cb = colbuf + op * CL_COLBUF;
-        const u64* src = (op ? io.buf_x : io.buf_a) + base;
+    // forward column half of operand op, column c: rows w + 16 j in
 #pragma unroll
-        for (int j1 = 0; j1 < 8; j1++) {
-            int off = (u + 8 * j1) * 64 + c;
-            v[j1] = PACK ? digit_at(op ? io.dx : io.da, base + off) : src[off];
-        }
-        gl::dft<8, false>(v);
-        gl::RowRoots<64, false, 8, 8>::apply(v, u);
-#pragma unroll
-        for (int kr = 0; kr < 8; kr++) cb[(kr * 8 + u) * CL_CP + li] = v[kr];
-        __syncthreads();
-#pragma unroll
-        for (int j0 = 0; j0 < 8; j0++) v[j0] = cb[(u * 8 + j0) * CL_CP + li];
-        gl::dft<8, false>(v);
-        const u64* w = (op == 0 && scaled) ? tw.w4096s : tw.w4096;
-#pragma unroll
-        for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(v[ks], w[c * (8 * ks + u)]);
+    for (int j = 0; j < 4; j++) {
+        const int off = (w + 16 * j) * 64 + c;
+        v[j] = PACK ? digit_at(op ? io.dx : io.da, base + off) : (op ? io.buf_x : io.buf_a)[base + off];
     }
-    // tile row k = 8 ks + u, column c, into the row buffer of the CTA owning row
-    // k (rank k / 16 = ks / 2, local row 8 (ks & 1) + u)
+    dft64_fwd_r4(v, cb, CL_CP, w);
     {
-        u64* rb[CL_Q];
+        // times w_4096^(c k) (a's times N^-1 too when the table has it), then
+        // row k = kk + 16 t to the CTA that owns it (rank t, local row kk)
+        const u64* tws = (op == 0 && scaled) ? tw.w4096s : tw.w4096;
 #pragma unroll
-        for (int r = 0; r < CL_Q; r++) rb[r] = cluster.map_shared_rank(rowbuf + op * CL_ROWBUF, r);
-#pragma unroll
-        for (int ks = 0; ks < 8; ks++) rb[ks >> 1][(8 * (ks & 1) + u) * TILE_PITCH + c] = v[ks];
+        for (int t = 0; t < 4; t++) {
+            u64* dst = cluster.map_shared_rank(rowbuf + op * CL_ROWBUF, t);
+            dst[kk * TILE_PITCH + c] = gl::mul(v[t], tws[c * (kk + 16 * t)]);
+        }
     }
     cluster.sync();
 
-    // forward row half of operand op, tile row 16 q + li (as c_fwd_row_a / c_fwd_row_b);
-    // each thread rewrites only the words it read before the barrier
-    u64* row = rowbuf + op * CL_ROWBUF + li * TILE_PITCH;
+    // forward row half of operand op, tile row 16 q + li
 #pragma unroll
-    for (int j1 = 0; j1 < 8; j1++) v[j1] = row[u + 8 * j1];
-    gl::dft<8, false>(v);
-    gl::RowRoots<64, false, 8, 8>::apply(v, u);
-#pragma unroll
-    for (int kr = 0; kr < 8; kr++) row[kr * 8 + u] = v[kr];
-    __syncthreads();
-#pragma unroll
-    for (int j0 = 0; j0 < 8; j0++) v[j0] = row[u * 8 + j0];
-    gl::dft<8, false>(v);  // v[ks]: the spectrum at (row 16 q + li, column 8 ks + u)
+    for (int j = 0; j < 4; j++) v[j] = rb[w + 16 * j];
+    dft64_fwd_r4(v, rb, 1, w);  // v[t]: the spectrum at (row 16 q + li, column kk + 16 t)
     // the product (Algorithm 1 step 4) in x's lanes, a's spectrum from lane - 16
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        u64 av = __shfl_xor_sync(0xffffffffu, v[k], 16);
-        if (op) v[k] = gl::mul(v[k], scaled ? av : gl::mul(av, ninv));
+    for (int t = 0; t < 4; t++) {
+        const u64 av = __shfl_xor_sync(0xffffffffu, v[t], 16);
+        if (op) v[t] = gl::mul(v[t], scaled ? av : gl::mul(av, ninv));
     }
-    // inverse row half of x (as c_inv_row_b_store / c_inv_row_a_load)
+    // inverse row half (x; the a lanes transform their own row and drop it)
+    dft64_inv_r4(v, rb, 1, w);  // v[j]: row 16 q + li, column w + 16 j
     if (op) {
-        gl::dft<8, true>(v);
+        // to the CTA owning column w + 16 j (rank j, local column w), x's column buffer
 #pragma unroll
-        for (int j0 = 0; j0 < 8; j0++) row[u * 8 + j0] = v[j0];  // the words this thread read last
-    }
-    __syncthreads();
-    if (op) {
-#pragma unroll
-        for (int kr = 0; kr < 8; kr++) v[kr] = row[kr * 8 + u];
-        gl::RowRoots<64, true, 8, 8>::apply(v, u);
-        gl::dft<8, true>(v);
-        // v[j1]: row 16 q + li, column u + 8 j1, to the CTA owning that column
-        // (rank j1 / 2, local column u + 8 (j1 & 1)), in x's column buffer
-        u64* cbx[CL_Q];
-#pragma unroll
-        for (int r = 0; r < CL_Q; r++) cbx[r] = cluster.map_shared_rank(colbuf + CL_COLBUF, r);
-#pragma unroll
-        for (int j1 = 0; j1 < 8; j1++)
-            cbx[j1 >> 1][(CL_LINES * q + li) * CL_CP + u + 8 * (j1 & 1)] = v[j1];
+        for (int j = 0; j < 4; j++) {
+            u64* dst = cluster.map_shared_rank(colbuf + CL_COLBUF, j);
+            dst[(CL_LINES * q + li) * CL_CP + w] = v[j];
+        }
     }
     cluster.sync();
 
-    // inverse column half of x, column c, in lanes 0-15 (as c_inv_col_b, c_inv_col_a)
-    u64* xc = colbuf + CL_COLBUF;
-    if (!op) {
+    // inverse column half of x, column c (the a lanes again on dead data)
 #pragma unroll
-        for (int ks = 0; ks < 8; ks++) v[ks] = gl::mul(xc[(8 * ks + u) * CL_CP + li], tw.w4096i[c * (8 * ks + u)]);
-        gl::dft<8, true>(v);
+    for (int t = 0; t < 4; t++) {
+        const int k = kk + 16 * t;
+        v[t] = gl::mul(cb[k * CL_CP], tw.w4096i[c * k]);
     }
-    __syncthreads();
-    if (!op) {
+    __syncthreads();  // every thread has read its rows before the buffer is reused
+    dft64_inv_r4(v, cb, CL_CP, w);  // v[j]: row w + 16 j, column c
+    if (op) {
 #pragma unroll
-        for (int j0 = 0; j0 < 8; j0++) xc[(u * 8 + j0) * CL_CP + li] = v[j0];
-    }
-    __syncthreads();
-    if (!op) {
-#pragma unroll
-        for (int kr = 0; kr < 8; kr++) v[kr] = xc[(kr * 8 + u) * CL_CP + li];
-        gl::RowRoots<64, true, 8, 8>::apply(v, u);
-        gl::dft<8, true>(v);
-#pragma unroll
-        for (int j1 = 0; j1 < 8; j1++) {
-            const u64 p = base + (u64)((u + 8 * j1) * 64 + c);
-            if (!PACK) io.buf_x[p] = v[j1];
-            else if (p < io.L) io.buf_x[p] = gl::canon(v[j1]);  // the transform's last pass: exact digits
+        for (int j = 0; j < 4; j++) {
+            const u64 p = base + (u64)((w + 16 * j) * 64 + c);
+            if (!PACK) io.buf_x[p] = v[j];
+            else if (p < io.L) io.buf_x[p] = gl::canon(v[j]);  // the transform's last pass: exact digits
         }
     }
 }
-
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
