@@ -574,13 +574,27 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(launches)]
-    for i, (a0, a1) in enumerate(evs):
+
+    def lone(fn):
+        for i, (a0, a1) in enumerate(evs):
+            torch.cuda.synchronize()
+            a0.record(stream)
+            fn(i)
+            a1.record(stream)
         torch.cuda.synchronize()
-        a0.record(stream)
-        step(i)
-        a1.record(stream)
-    torch.cuda.synchronize()
-    alone = sorted(a0.elapsed_time(a1) * 1e3 for a0, a1 in evs)
+        return sorted(a0.elapsed_time(a1) * 1e3 for a0, a1 in evs)
+
+    alone = lone(step)
+    # the same through the C ABI alone (arguments converted once, outside the timed calls)
+    lib = binding.load()
+    raw = [tuple(t.data_ptr() for t in (*dv[j], outs[j])) for j in range(rotate)]
+    sp = stream.cuda_stream
+
+    def step_c(i):
+        x, a, b, o = raw[i % rotate]
+        lib.pa_hash(x, a, b, n, m, o, sp)
+
+    alone_c = lone(step_c)
 
     binding.profile(True)
     for i in range(launches):
@@ -599,6 +613,7 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
     e1.record(stream)
     torch.cuda.synchronize()
     graph_ms = e0.elapsed_time(e1) / launches
+    alone_g = lone(lambda i: graphs[i % rotate].run(stream))
     for g in graphs:
         g.close()
     N = binding.plan_info(n, m)["first"]
@@ -608,7 +623,12 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
             "note": f"plain launches back to back, {launches} steps",
             "plain_single_launch_median_us": round(alone[len(alone) // 2], 2),
             "plain_single_launch_p99_us": round(alone[min(len(alone) - 1, int(0.99 * len(alone)))], 2),
+            "c_abi_single_launch_median_us": round(alone_c[len(alone_c) // 2], 2),
+            "c_abi_single_launch_p99_us": round(alone_c[min(len(alone_c) - 1, int(0.99 * len(alone_c)))], 2),
+            "single_launch_note": "events around one call each, synchronised between calls: through the "
+                                  "Python binding (argument checks included), and pa_hash called directly",
             "captured_graph_value": round(n / graph_ms / 1e3, 1),
+            "captured_graph_single_median_us": round(alone_g[len(alone_g) // 2], 2),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kstats.items()},
             "roofline": kernel_roofline(kstats, N)}
 

@@ -1,6 +1,7 @@
 """Seeded random sizes against the oracle, bit for bit: key lengths log-uniform
 from 1 bit to 3e6 bits with any output length, each under a random plan
-variant; random Toeplitz sizes; random mixed batches."""
+variant; small keys with the tile pass forced onto four-CTA clusters, full and
+wrapped; random Toeplitz sizes; random mixed batches."""
 import math
 
 import numpy as np
@@ -19,7 +20,7 @@ def _sizes(seed, count, n_max):
     for i in range(count):
         n = max(1, int(math.exp(float(u[3 * i]) * math.log(n_max))))
         m = 1 + int(float(u[3 * i + 1]) * n) if n > 1 else 1
-        out.append((n, min(m, n), int(float(u[3 * i + 2]) * 16)))
+        out.append((n, min(m, n), int(float(u[3 * i + 2]) * binding.PLAN_VARIANTS)))
     return out
 
 
@@ -34,6 +35,30 @@ def test_random_sizes_and_plans(chunk):
             binding.plan_override(n, -1)
         want = oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads())
         np.testing.assert_array_equal(got, want, err_msg=f"n={n} m={m} variant={variant}")
+
+
+@pytest.mark.parametrize("wrap", [1, 2])
+def test_random_small_sizes_on_clusters(wrap):
+    """Keys up to 2.1e6 bits (transforms of at most 64 tiles, the single tile
+    included) with the cluster bit set and the other bits random; wrap mode 2
+    wraps wherever a shorter length certifies."""
+    prev = binding.wrap_mode(wrap)
+    try:
+        for n, m, variant in _sizes(2000 + wrap, 16, 2_100_000):
+            v = variant | binding.PLAN_CLUSTER
+            blk = inputs.make_block(n, m, seed=3 * n + m)
+            info = binding.plan_info(n, m)
+            for N in {info["first"], info["full"]}:
+                binding.plan_override_length(N, v)
+            try:
+                got = gpu_hash(binding, blk.x, blk.a, blk.b, n, m)
+            finally:
+                for N in {info["first"], info["full"]}:
+                    binding.plan_override_length(N, -1)
+            want = oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads())
+            np.testing.assert_array_equal(got, want, err_msg=f"n={n} m={m} variant={v} wrap={wrap}")
+    finally:
+        binding.wrap_mode(prev)
 
 
 def test_random_toeplitz_sizes():
