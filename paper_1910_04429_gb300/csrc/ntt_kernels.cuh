@@ -156,6 +156,33 @@ __device__ __forceinline__ void fwd_strided_tile(const StridedGeom& g, const Blo
             cp_async_commit();
         }
     }
+    if constexpr (OPS == 2 && 2 * S::NA <= NT && 2 * S::NB <= NT && 2 * S::R * C <= TILE) {
+        // few columns per tile (narrow tiles): x in threads [0, NT/2), a in
+        // [NT/2, NT), both operands at once, each half with its own twiddles
+        // and its own [R][C] exchange area
+        const int op = threadIdx.x >= NT / 2 ? 1 : 0;
+        const int it = (int)threadIdx.x - op * (NT / 2);
+        u64* buf = op ? io.buf_a : io.buf_x;
+        const Digits& d = op ? io.da : io.dx;
+        u64* smo = sm + op * (S::R * C);
+        u64* sto = dsm + TILE + op * SZ::WORDS;  // st[op], without indexing an array at run time
+        u64 wv[RA];
+        if (it < S::NB) S::twiddles(g, tp, it, tw, wv);
+        if (BULK_ROWS) {
+            for (int o = 0; o < 2; o++)
+                if (!mbar_wait(&bars[o], 0, BULK_WAIT_LIMIT)) atomicOr(&g_bulk_status, PA_STATUS_TIMEOUT);
+        } else if (STAGED) {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // both staged tiles complete
+        if (it < S::NA) {
+            if (STAGED) S::template fwd_a_staged<PACK, WIDE>(g, tp, it, sto, (const uint16_t*)sto, d, smo);
+            else S::template fwd_a<PACK, WIDE>(g, tp, it, buf, d, smo);
+        }
+        __syncthreads();
+        if (it < S::NB) S::fwd_b(g, tp, it, buf, smo, wv);
+        return;
+    }
     u64 w[S::ITEMS_B][RA];
 #pragma unroll
     for (int i = 0; i < S::ITEMS_B; i++) {
