@@ -536,8 +536,6 @@ template <bool PACK>
 __global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
     k_contig_cluster(const __grid_constant__ NttBatch<1> nb, u64 ninv, Twiddles tw) {
     namespace cg = cooperative_groups;
-    pdl_begin();
-    clear_states(nb, CL_THREADS);
     __shared__ u64 colbuf[2 * CL_COLBUF];
     __shared__ u64 rowbuf[2 * CL_ROWBUF];
     cg::cluster_group cluster = cg::this_cluster();
@@ -550,6 +548,21 @@ __global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
     const bool scaled = tw.w4096s != nullptr;
     u64* cb = colbuf + op * CL_COLBUF + li;               // column c of operand op, stride CL_CP
     u64* rb = rowbuf + op * CL_ROWBUF + li * TILE_PITCH;  // row 16 q + li of operand op
+    // the twiddles w_4096^(+-c k) of the column halves, k = kk + 16 t (a's forward
+    // ones times N^-1 when the table has them): read before the wait for the
+    // previous kernel (the tables never change once built), so that no read of
+    // them sits behind a barrier
+    u64 twf[4], twi[4];
+    {
+        const u64* tws = (op == 0 && scaled) ? tw.w4096s : tw.w4096;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            twf[t] = tws[c * (kk + 16 * t)];
+            twi[t] = tw.w4096i[c * (kk + 16 * t)];
+        }
+    }
+    pdl_begin();
+    clear_states(nb, CL_THREADS);
     u64 v[4];
 
     // forward column half of operand op, column c: rows w + 16 j in
@@ -559,15 +572,11 @@ __global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
         v[j] = PACK ? digit_at(op ? io.dx : io.da, base + off) : (op ? io.buf_x : io.buf_a)[base + off];
     }
     dft64_fwd_r4(v, cb, CL_CP, w);
-    {
-        // times w_4096^(c k) (a's times N^-1 too when the table has it), then
-        // row k = kk + 16 t to the CTA that owns it (rank t, local row kk)
-        const u64* tws = (op == 0 && scaled) ? tw.w4096s : tw.w4096;
+    // times w_4096^(c k), then row k = kk + 16 t to the CTA that owns it (rank t, local row kk)
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-            u64* dst = cluster.map_shared_rank(rowbuf + op * CL_ROWBUF, t);
-            dst[kk * TILE_PITCH + c] = gl::mul(v[t], tws[c * (kk + 16 * t)]);
-        }
+    for (int t = 0; t < 4; t++) {
+        u64* dst = cluster.map_shared_rank(rowbuf + op * CL_ROWBUF, t);
+        dst[kk * TILE_PITCH + c] = gl::mul(v[t], twf[t]);
     }
     cluster.sync();
 
@@ -595,10 +604,7 @@ __global__ void __cluster_dims__(CL_Q, 1, 1) __launch_bounds__(CL_THREADS)
 
     // inverse column half of x, column c (the a lanes again on dead data)
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-        const int k = kk + 16 * t;
-        v[t] = gl::mul(cb[k * CL_CP], tw.w4096i[c * k]);
-    }
+    for (int t = 0; t < 4; t++) v[t] = gl::mul(cb[(kk + 16 * t) * CL_CP], twi[t]);
     __syncthreads();  // every thread has read its rows before the buffer is reused
     dft64_inv_r4(v, cb, CL_CP, w);  // v[j]: row w + 16 j, column c
     if (op) {
