@@ -173,13 +173,31 @@ __device__ __forceinline__ void stage_pairs(u64* dst, const u64* src, long long 
 // Digits [k0, k0 + SM_COEF) and limbs [J0, J0 + SM_LIMBS) of tile tt (tile_base)
 // into cs / bs; positions outside the operands read 0. (SM_COEF covers the
 // digits of SM_LIMBS limbs for every width W >= 16, plus the rounding of k0.)
+// The b limbs of a tile alone (VEC: issued as their own group of async copies,
+// not waited for).
 template <bool VEC, int W>
-__device__ __forceinline__ TileBase stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs) {
+__device__ __forceinline__ void stage_b(const CarryJob& c, u64 Ly, long long tt, u64* bs) {
+    const long long J0 = tile_base<W>(tt).J0;
+    if (VEC) {
+        stage_pairs(bs, c.b, J0, SM_LIMBS_PAD / 2, Ly);
+        cp_async_commit();
+    } else {
+        for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
+            long long j = J0 + i;
+            bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
+        }
+    }
+}
+
+// The digits of a tile, and its b limbs unless have_b (staged by stage_b);
+// returns with everything staged in shared memory by this thread complete.
+template <bool VEC, int W>
+__device__ __forceinline__ TileBase stage_tile(const CarryJob& c, u64 Ly, long long tt, u64* cs, u64* bs,
+                                               bool have_b = false) {
     const TileBase tb = tile_base<W>(tt);
-    const long long J0 = tb.J0;
     if (VEC) {
         stage_pairs(cs, c.coef, tb.k0, SM_COEF / 2, c.L, c.lo);
-        stage_pairs(bs, c.b, J0, SM_LIMBS_PAD / 2, Ly);
+        if (!have_b) stage_pairs(bs, c.b, tb.J0, SM_LIMBS_PAD / 2, Ly);
         cp_async_commit();
         cp_async_wait<0>();
     } else {
@@ -187,10 +205,7 @@ __device__ __forceinline__ TileBase stage_tile(const CarryJob& c, u64 Ly, long l
             long long k = tb.k0 + i;
             cs[i] = (k >= (long long)c.lo && (u64)k < c.L) ? c.coef[k] : 0;
         }
-        for (int i = threadIdx.x; i < SM_LIMBS; i += CARRY_THREADS) {
-            long long j = J0 + i;
-            bs[i] = (j >= 0 && (u64)j < Ly) ? c.b[j] : 0;
-        }
+        if (!have_b) stage_b<false, W>(c, Ly, tt, bs);
     }
     return tb;
 }

@@ -76,6 +76,7 @@ constexpr int CARRY_LIMBS = 2;  // limbs per thread (4 measured slower: longer p
 // (tiles of 256 limbs: 128 x 2 measured ahead of 256 x 2 and 256 x 1)
 constexpr u64 CARRY_TILE_LIMBS = (u64)CARRY_THREADS * CARRY_LIMBS;
 constexpr u32 CARRY_SPIN_LIMIT = 1u << 20;  // polls of a predecessor tile before giving up (~0.1-1 s)
+constexpr u64 CARRY_FIXED_MAX_CTAS = 256;   // carry grids up to this size take their tiles by block index
 constexpr u32 PA_STATUS_TIMEOUT = 1u;       // device status bit: a bounded wait ran out
 GL_HD u64 carry_tiles(u64 n) { return ((n + 63) / 64 + CARRY_TILE_LIMBS - 1) / CARRY_TILE_LIMBS; }
 // tile states, the ticket counter, the wrapped product's flag
