@@ -45,35 +45,37 @@ __device__ unsigned long long g_flags;  // carry launches that set their wrapped
 // carry_tiles(n) - first_out_tile(n, m) CTAs per block (the widest block's
 // count along x). ticket_start > 0 (fault injection) leaves the first output
 // tiles unprocessed and makes every tile take the look-back path, so that the
-// wait on them runs out. fixed (grids small enough to be resident at once, no
+// wait on them runs out. FIXED (grids small enough to be resident at once, no
 // fault injection): CTA x takes output tile x, with no ticket, and stages its
 // b limbs before the wait for the previous kernel (b is the caller's input,
 // which no kernel of this hash writes), two memory round trips off the
 // critical path of a small hash.
-template <int B, bool VEC, int W>
+template <int B, bool VEC, int W, bool FIXED>
 __global__ void __launch_bounds__(CARRY_THREADS) k_carry(const __grid_constant__ CarryBatch<B> cb,
-                                                         u32 ticket_start, u32 spin_limit, u32 fixed) {
+                                                         u32 ticket_start, u32 spin_limit) {
     __shared__ __align__(16) u64 cs[SM_COEF];
     __shared__ __align__(16) u64 bs[SM_LIMBS_PAD];
     __shared__ u32 tile_sh;
     __shared__ int decided_sh, carry_in_sh;
+    if constexpr (FIXED) {
+        const CarryJob& c = cb.job[blockIdx.y];
+        const u64 t = first_out_tile(c.n, c.m, c.flag != nullptr) + blockIdx.x;
+        if (t >= carry_tiles(c.n)) return;
+        stage_b<VEC, W>(c, (c.n + 63) / 64, (long long)t, bs);
+    }
+    pdl_begin();
     const CarryJob& c = cb.job[blockIdx.y];
     const u64 Ly = (c.n + 63) / 64, tiles = carry_tiles(c.n);
     const u64 t0 = first_out_tile(c.n, c.m, c.flag != nullptr);
     u32* state = c.state;  // tiles words, then the ticket counter
-    if (fixed) {
-        if (t0 + blockIdx.x >= tiles) return;
-        stage_b<VEC, W>(c, Ly, (long long)(t0 + blockIdx.x), bs);
-    }
-    pdl_begin();
-    if (!fixed) {
+    if constexpr (!FIXED) {
         if (threadIdx.x == 0) tile_sh = atomicAdd(&state[tiles], 1u) + ticket_start;
         __syncthreads();
     }
-    const u64 t = t0 + (fixed ? blockIdx.x : tile_sh);
+    const u64 t = t0 + (FIXED ? blockIdx.x : tile_sh);
     if (t >= tiles) return;
 
-    const TileBase tb = stage_tile<VEC, W>(c, Ly, (long long)t, cs, bs, fixed != 0);
+    const TileBase tb = stage_tile<VEC, W>(c, Ly, (long long)t, cs, bs, FIXED);
     __syncthreads();
 
     const int l0 = HALO_LO + CARRY_LIMBS * threadIdx.x;  // shared position of the thread's first limb
@@ -220,7 +222,7 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     u32 start = g_inject_ticket.exchange(0);
     u32 limit = start ? 1000u : CARRY_SPIN_LIMIT;
     // a grid this small is resident at once: fixed tiles need no ticket
-    const u32 fixed = start == 0 && tiles * (u64)cb.count <= CARRY_FIXED_MAX_CTAS ? 1u : 0u;
+    const bool fixed = start == 0 && tiles * (u64)cb.count <= CARRY_FIXED_MAX_CTAS;
     bool vec = true;
     for (int i = 0; i < cb.count; i++)
         vec = vec && (uintptr_t)cb.job[i].coef % 16 == 0 && (uintptr_t)cb.job[i].b % 16 == 0 &&
@@ -231,8 +233,10 @@ static cudaError_t launch_carry_b(const CarryBatch<B>& cb, cudaStream_t st) {
     switch (cb.job[0].width) {  // every job of a launch has the same digit width
 #define PA_CARRY_W(w)                                                                                    \
     case w:                                                                                              \
-        e = vec ? launch_pdl(k_carry<B, true, w>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit, fixed)   \
-                : launch_pdl(k_carry<B, false, w>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit, fixed); \
+        e = fixed ? (vec ? launch_pdl(k_carry<B, true, w, true>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)   \
+                         : launch_pdl(k_carry<B, false, w, true>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)) \
+                  : (vec ? launch_pdl(k_carry<B, true, w, false>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)  \
+                         : launch_pdl(k_carry<B, false, w, false>, grid, dim3(CARRY_THREADS), 0, st, cb, start, limit)); \
         break;
         PA_CARRY_W(16) PA_CARRY_W(17) PA_CARRY_W(18) PA_CARRY_W(19) PA_CARRY_W(20)
 #undef PA_CARRY_W
