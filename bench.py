@@ -233,7 +233,7 @@ def hash_bytes(n: int, m: int) -> int:
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram bytes per
 # launch at n = 10^8), valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 110.0e6, "src_sha": "85377fc70ed3a578",
+TRAFFIC = {"kernel": "ntt_contig_both", "bytes": 110.0e6, "src_sha": "10aac03709b1b0b9",
            "profile": "profiles/k_contig_both_n1e8.md"}
 
 
