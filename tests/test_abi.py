@@ -75,6 +75,26 @@ def test_status_constants_match_header():
         assert int(m.group(1)) == getattr(binding, name)
 
 
+def test_plan_bits_match_header():
+    """The binding's plan-variant bits are the header's PA_PLAN_* values, and
+    the variants are exactly the combinations of those bits."""
+    text = _header_text()
+    bits = {}
+    for name in ("R0_LAST", "DIRECT_FWD", "DIRECT_INV", "NARROW", "BULK", "CLUSTER"):
+        m = re.search(rf"#define PA_PLAN_{name} (\d+)", text)
+        assert m, name
+        bits[name] = int(m.group(1))
+        assert bits[name] == getattr(binding, "PLAN_" + name)
+    assert sorted(bits.values()) == [1 << i for i in range(len(bits))]
+    assert binding.PLAN_VARIANTS == 1 << len(bits)
+    # the last variant passes the argument check (without a GPU the call then
+    # fails on the device; with one it sets an override, cleared again)
+    lib = binding.raw()
+    rc = lib.pa_plan_override(1000, binding.PLAN_VARIANTS - 1)
+    assert rc != binding.PA_EINVAL or b"variant" not in lib.pa_last_error()
+    lib.pa_plan_override(1000, -1)
+
+
 def test_argument_checks_without_gpu():
     lib = binding.raw()
     z = np.zeros(4, dtype=np.uint64)
