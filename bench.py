@@ -616,6 +616,32 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
     alone_g = lone(lambda i: graphs[i % rotate].run(stream))
     for g in graphs:
         g.close()
+    # end to end from pinned host buffers (pa_hash_host_async back to back, the
+    # median of three runs of `launches` calls; and the synchronous pa_hash_host),
+    # each result read back equal to the device path's
+    hx, ha, hb = ([torch.from_numpy(getattr(b, f).view(np.int64)).pin_memory() for b in blks] for f in "xab")
+    hout = [torch.empty(Mo, dtype=torch.int64).pin_memory() for _ in blks]
+
+    def e2e(sync):
+        f = binding.hash_host if sync else binding.hash_host_async
+        runs = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(launches):
+                j = i % rotate
+                f(hx[j], ha[j], hb[j], n, m, hout[j], stream=stream)
+            torch.cuda.synchronize()
+            runs.append((time.perf_counter() - t0) * 1e3 / launches)
+        return statistics.median(runs)
+
+    e2e(False)  # warm-up
+    e2e_ms, e2e_sync_ms = e2e(False), e2e(True)
+    for j in range(rotate):
+        step(j)
+    torch.cuda.synchronize()
+    if not all(np.array_equal(hout[j].numpy(), outs[j].cpu().numpy()) for j in range(rotate)):
+        raise RuntimeError("host-buffer results differ from device-buffer results at n = 10^6")
     N = binding.plan_info(n, m)["first"]
     return {"workload": f"G_cd hash, one key of n={n} bits, m={m}, {rotate} rotating blocks, "
                         f"L2-resident", "plan_variant": tuned, "transform": N,
@@ -627,6 +653,11 @@ def run_small(dev, stream, n=1_000_000, m=250_000, launches=500, rotate=8):
             "c_abi_single_launch_p99_us": round(alone_c[min(len(alone_c) - 1, int(0.99 * len(alone_c)))], 2),
             "single_launch_note": "events around one call each, synchronised between calls: through the "
                                   "Python binding (argument checks included), and pa_hash called directly",
+            "e2e": {"value": round(n / e2e_ms / 1e3, 1), "unit": UNIT,
+                    "sync_value": round(n / e2e_sync_ms / 1e3, 1),
+                    "h2d_bytes_per_step": 3 * L * 8, "d2h_bytes_per_step": Mo * 8,
+                    "api": "pa_hash_host_async back to back on pinned buffers, host clock to the final sync "
+                           f"(median of 3 runs of {launches} calls); sync_value: pa_hash_host"},
             "captured_graph_value": round(n / graph_ms / 1e3, 1),
             "captured_graph_single_median_us": round(alone_g[len(alone_g) // 2], 2),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kstats.items()},
