@@ -92,7 +92,10 @@ int pa_hash(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b,
  * seed_b behind them, so b's copy overlaps the transforms; the hash waits on
  * each copy with an event; the result is copied back on `stream`. Pinned
  * (page-locked) buffers make the copies asynchronous; pageable memory also
- * works.
+ * works. For n <= 2^21 with all four buffers in page-locked host memory that
+ * the device can address (mapped: cudaHostAlloc'd or registered), there are no
+ * copies: the kernels read the inputs and write `out` in place over the
+ * host link, which saves the copy path's host work on blocks this small.
  *
  * pa_hash_host_async: the same, returning once everything is queued. The
  * copy stream runs at most two calls ahead of the hashes (staging memory is

@@ -688,15 +688,45 @@ int status_slot_of(int dev, cudaStream_t st) {
 // on the device's copy stream (two calls at most ahead of the hashes, so the
 // next call's copies overlap this call's transforms), b behind them, the hash
 // runs on st after each copy's event, and the result is copied back on st.
+// Host-buffer hashes of at most this many bits run in place on mapped memory.
+constexpr u64 ZERO_COPY_MAX_BITS = 1ull << 21;
+
+// The device address of host buffer [p, p + bytes) when all of it is host
+// memory the device can address (page-locked and mapped: its first and last
+// bytes both mapped, at device addresses bytes - 1 apart), else null.
+const void* mapped_host(const void* p, size_t bytes) {
+    cudaPointerAttributes a0, a1;
+    const char* last = (const char*)p + bytes - 1;
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered pointer is not an error here
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    if ((const char*)a1.devicePointer - (const char*)a0.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+    return a0.devicePointer;
+}
+
 int queue_hash_host(const uint64_t* key, const uint64_t* seed_a, const uint64_t* seed_b, uint64_t n,
                     uint64_t m, uint64_t* out, cudaStream_t st, bool queued) {
     std::lock_guard<std::mutex> lk(g_mu);
     int dev, rc;
     cudaMemPool_t pool;
     if ((rc = setup(&dev, &pool))) return rc;
-    if ((rc = side_streams(dev))) return rc;
     Device& d = g_dev[dev];
     size_t in_bytes = ((n + 63) / 64) * sizeof(u64), out_bytes = ((m + 63) / 64) * sizeof(u64);
+    if (n <= ZERO_COPY_MAX_BITS) {
+        // Small blocks in mapped page-locked memory: the kernels read the inputs
+        // and write the result in place over the host link. The copy path's
+        // staging, copies and events cost more host time than such a hash
+        // takes on the device.
+        const void* kx = mapped_host(key, in_bytes);
+        const void* ka = kx ? mapped_host(seed_a, in_bytes) : nullptr;
+        const void* kb = ka ? mapped_host(seed_b, in_bytes) : nullptr;
+        void* ko = kb ? (void*)mapped_host(out, out_bytes) : nullptr;
+        if (ko) return hash_device((const u64*)kx, (const u64*)ka, (const u64*)kb, n, m, (u64*)ko, st, dev, pool);
+    }
+    if ((rc = side_streams(dev))) return rc;
     cudaEvent_t done = d.done[d.host_calls & 1];  // recorded by the call two before this one
     cudaError_t e = cudaSuccess;
     if (d.host_calls >= 2) e = cudaStreamWaitEvent(d.copy, done, 0);

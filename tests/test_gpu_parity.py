@@ -239,6 +239,35 @@ def test_hash_host_pinned(n, m):
         np.testing.assert_array_equal(out.numpy().view(np.uint64), want)
 
 
+def test_hash_host_small_mixed_buffers():
+    """Small blocks run in place on mapped page-locked buffers; any buffer that
+    is not (a pageable output here) sends the call through the copy path. Views
+    one limb into larger pinned tensors (8-byte aligned) take 16-bit digits. All
+    against the oracle, synchronous and queued."""
+    import torch
+
+    n, m = 500_001, 120_007
+    blk = inputs.make_block(n, m, seed=21)
+    want = oracle.pa_hash(blk.x, blk.a, blk.b, n, m, threads=oracle.default_threads())
+    L, Mo = (n + 63) // 64, (m + 63) // 64
+    pins = [torch.from_numpy(v.view(np.int64)).pin_memory() for v in (blk.x, blk.a, blk.b)]
+    # pinned inputs, pageable output: the copy path
+    np.testing.assert_array_equal(binding.hash_host(*pins, n, m), want)
+    # views one limb into larger pinned tensors, pinned output: in place
+    big = [torch.zeros(L + 1, dtype=torch.int64).pin_memory() for _ in range(3)]
+    for t, v in zip(big, pins):
+        t[1:].copy_(v)
+    for sync in (True, False):
+        out = torch.full((Mo + 1,), -1, dtype=torch.int64).pin_memory()
+        if sync:
+            binding.hash_host(big[0][1:], big[1][1:], big[2][1:], n, m, out[1:])
+        else:
+            binding.hash_host_async(big[0][1:], big[1][1:], big[2][1:], n, m, out[1:])
+            torch.cuda.synchronize()
+        np.testing.assert_array_equal(out[1:].numpy().view(np.uint64), want)
+        assert int(out[0]) == -1  # nothing written before the output
+
+
 def test_hash_host_async_pipeline():
     """Back-to-back pa_hash_host_async calls (pinned and pageable buffers, one
     stream and two alternating streams): every result equals the oracle's once
